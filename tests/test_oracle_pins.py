@@ -1,0 +1,395 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks a closed form, an invariant, a special case that reduces to a
+simpler operator, brute force on a tiny grid, or the paper's printed constants,
+so that a dropped term, a wrong sign or index, or a transposed table in the
+oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbinputs
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+STENCILS = ["D2Q9", "D3Q19", "D3Q27"]
+CS2 = 1.0 / 3.0
+
+
+def _golden_weights():
+    out = {}
+    with open(os.path.join(GOLDEN, "stencils.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, c2, count, frac = line.split()
+            num, den = frac.split("/")
+            out.setdefault(name, {})[int(c2)] = (int(count), float(num) / float(den))
+    return out
+
+
+# ----------------------------------------------------------------------------- stencils
+@pytest.mark.parametrize("name", STENCILS)
+def test_stencil_weights_match_textbook(name):
+    d, c, w, opp = oracle.stencil(name)
+    gold = _golden_weights()[name]
+    c2 = (c * c).sum(1)
+    for k, (count, weight) in gold.items():
+        sel = c2 == k
+        assert sel.sum() == count
+        np.testing.assert_allclose(w[sel], weight, rtol=0, atol=1e-16)
+    assert len(w) == sum(cnt for cnt, _ in gold.values())
+    # distinct velocities, each with its opposite
+    assert len({tuple(v) for v in c}) == len(w)
+    np.testing.assert_array_equal(c[opp], -c)
+    if d == 2:
+        assert np.all(c[:, 2] == 0)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_stencil_isotropy(name):
+    d, c, w, _ = oracle.stencil(name)
+    c = c[:, :d].astype(float)
+    I = np.eye(d)
+    assert abs(w.sum() - 1) < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia->a", w, c), 0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, c, c), CS2 * I, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0, atol=1e-16)
+    iso4 = CS2 ** 2 * (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+                       + np.einsum("ad,bc->abcd", I, I))
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso4, atol=1e-16)
+
+
+# ----------------------------------------------------------------------------- equilibrium
+@pytest.mark.parametrize("name", STENCILS)
+def test_equilibrium_moments_closed_form(name):
+    d, c, w, _ = oracle.stencil(name)
+    dims = (5, 4, 1) if d == 2 else (3, 4, 2)
+    rho, u = lbinputs.random_moments(dims, seed=1, u_amp=0.1)
+    f = oracle.init_eq(name, dims, rho, u)
+    cf = c[:, :d].astype(float)
+    np.testing.assert_allclose(f.sum(0), rho, rtol=1e-15)
+    np.testing.assert_allclose(np.einsum("ia,in->an", cf, f), rho * u, atol=1e-16)
+    P = np.einsum("ia,ib,in->abn", cf, cf, f)
+    expect = np.einsum("n,an,bn->abn", rho, u, u) + CS2 * rho[None, None, :] * np.eye(d)[:, :, None]
+    np.testing.assert_allclose(P, expect, atol=2e-16)
+    # the oracle's own moment routine returns the generating fields
+    r2, u2 = oracle.moments(name, dims, f)
+    np.testing.assert_allclose(r2, rho, rtol=1e-15)
+    np.testing.assert_allclose(u2, u, atol=1e-16)
+
+
+def _random_node(name, seed, eps=0.05):
+    d, c, w, _ = oracle.stencil(name)
+    return lbinputs.random_populations(w, 1, seed, eps)[:, 0]
+
+
+# ----------------------------------------------------------------------------- collision
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("coll", ["bgk", "regularized"])
+@pytest.mark.parametrize("tau", [0.51, 0.8, 1.7])
+def test_collision_conserves_mass_momentum(name, coll, tau):
+    d, c, w, _ = oracle.stencil(name)
+    f = _random_node(name, 3)
+    out = oracle.collide_node(name, tau, coll, f)
+    assert abs(out.sum() - f.sum()) < 1e-15
+    np.testing.assert_allclose(c.T @ out, c.T @ f, atol=1e-16)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("coll", ["bgk", "regularized"])
+def test_unit_relaxation_gives_equilibrium(name, coll):
+    d, c, w, _ = oracle.stencil(name)
+    f = _random_node(name, 4)
+    out = oracle.collide_node(name, 1.0, coll, f)
+    rho = f.sum()
+    u = (c[:, :d].T @ f) / rho
+    feq = oracle.init_eq(name, (1, 1, 1), [rho], u.reshape(d, 1))[:, 0]
+    np.testing.assert_allclose(out, feq, atol=1e-16)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_bgk_is_linear_relaxation(name):
+    # Eq. 2: f* - f^eq = (1 - 1/tau)(f - f^eq) component by component
+    d, c, w, _ = oracle.stencil(name)
+    f = _random_node(name, 5)
+    tau = 0.7
+    out = oracle.collide_node(name, tau, "bgk", f)
+    feq = oracle.collide_node(name, 1.0, "bgk", f)
+    np.testing.assert_allclose(out - feq, (1 - 1 / tau) * (f - feq), atol=1e-16)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_regularized_second_moment(name):
+    # f*'s second moment = rho u u + rho cs2 I + (1 - omega) Pi^neq (Latt & Chopard)
+    d, c, w, _ = oracle.stencil(name)
+    cf = c[:, :d].astype(float)
+    f = _random_node(name, 6)
+    tau = 0.6
+    out = oracle.collide_node(name, tau, "regularized", f)
+    rho = f.sum()
+    u = cf.T @ f / rho
+    eq2 = rho * np.outer(u, u) + rho * CS2 * np.eye(d)
+    pneq = np.einsum("ia,ib,i->ab", cf, cf, f) - eq2
+    np.testing.assert_allclose(np.einsum("ia,ib,i->ab", cf, cf, out), eq2 + (1 - 1 / tau) * pneq, atol=1e-16)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_regularized_discards_non_hydrodynamic_part(name):
+    # adding a vector with zero 0th, 1st and 2nd moments leaves the regularized f* unchanged
+    d, c, w, _ = oracle.stencil(name)
+    cf = c[:, :d].astype(float)
+    f = _random_node(name, 7)
+    # a direction with vanishing moments of order 0, 1 and 2: from the null space of
+    # the (1, c_a, c_a c_b) moment matrix
+    rows = [np.ones(len(w))] + [cf[:, a] for a in range(d)] + \
+        [cf[:, a] * cf[:, b] for a in range(d) for b in range(a, d)]
+    _, _, vt = np.linalg.svd(np.array(rows))
+    g = vt[-1] * 0.01
+    assert abs(g.sum()) < 1e-16
+    np.testing.assert_allclose(cf.T @ g, 0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("ia,ib,i->ab", cf, cf, g), 0, atol=1e-16)
+    a = oracle.collide_node(name, 0.6, "regularized", f)
+    b = oracle.collide_node(name, 0.6, "regularized", f + 0.3 * g)
+    np.testing.assert_allclose(a, b, atol=1e-16)
+    # whereas BGK keeps a (1 - omega) share of it
+    a = oracle.collide_node(name, 0.6, "bgk", f)
+    b = oracle.collide_node(name, 0.6, "bgk", f + 0.3 * g)
+    np.testing.assert_allclose(b - a, (1 - 1 / 0.6) * 0.3 * g, atol=1e-16)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_guo_source_moments(name):
+    # sum S = 0, sum c S = (1 - omega/2) F, sum c c S = (1 - omega/2)(u F + F u)
+    d, c, w, _ = oracle.stencil(name)
+    cf = c[:, :d].astype(float)
+    rng = np.random.default_rng(8)
+    u = rng.uniform(-0.1, 0.1, d)
+    F = rng.uniform(-1e-3, 1e-3, d)
+    tau = 0.8
+    S = oracle.guo_source(name, tau, u, F)
+    pre = 1 - 0.5 / tau
+    assert abs(S.sum()) < 1e-18
+    np.testing.assert_allclose(cf.T @ S, pre * F, atol=1e-18)
+    np.testing.assert_allclose(np.einsum("ia,ib,i->ab", cf, cf, S), pre * (np.outer(u, F) + np.outer(F, u)),
+                               atol=1e-18)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("coll", ["bgk", "regularized"])
+def test_forced_collision_adds_exactly_F(name, coll):
+    d, c, w, _ = oracle.stencil(name)
+    f = _random_node(name, 9)
+    F = np.array([1e-3, -2e-3, 5e-4][:d])
+    out = oracle.collide_node(name, 0.7, coll, f, F=F)
+    assert abs(out.sum() - f.sum()) < 1e-15
+    np.testing.assert_allclose(c[:, :d].T @ out, c[:, :d].T @ f + F, atol=1e-16)
+
+
+# ----------------------------------------------------------------------------- learned (Eq. 5)
+def _bgk_mlp(tau, seed=11, ghost_tau=None):
+    """Network whose output is the constant ln(ghost_tau - 1/2) (hidden layers random)."""
+    gt = tau if ghost_tau is None else ghost_tau
+    th = lbinputs.random_mlp_params(seed, out_bias=math.log(gt - 0.5), out_scale=0.0)
+    return np.concatenate([th, np.zeros(6), np.ones(6)])
+
+
+def test_learned_with_shear_rate_ghosts_is_bgk():
+    tau = 0.62
+    for seed in range(5):
+        f = _random_node("D2Q9", 20 + seed, eps=0.2)
+        a = oracle.collide_node("D2Q9", tau, "learned", f, mlp=_bgk_mlp(tau))
+        b = oracle.collide_node("D2Q9", tau, "bgk", f)
+        np.testing.assert_allclose(a, b, atol=1e-16)
+
+
+def test_learned_with_unit_ghost_rate_is_regularized():
+    tau = 0.62
+    for seed in range(5):
+        f = _random_node("D2Q9", 30 + seed, eps=0.2)
+        a = oracle.collide_node("D2Q9", tau, "learned", f, mlp=_bgk_mlp(tau, ghost_tau=1.0))
+        b = oracle.collide_node("D2Q9", tau, "regularized", f)
+        np.testing.assert_allclose(a, b, atol=1e-16)
+
+
+def _d2q9_rotation():
+    d, c, w, _ = oracle.stencil("D2Q9")
+    # rotation by 90 degrees: (cx, cy) -> (-cy, cx); perm[i] = index of R c_i
+    rc = np.stack([-c[:, 1], c[:, 0], c[:, 2]], 1)
+    return np.array([np.where((c == v).all(1))[0][0] for v in rc])
+
+
+def test_learned_invariants_and_collision_are_rotation_equivariant():
+    perm = _d2q9_rotation()
+    mlp = np.concatenate([lbinputs.random_mlp_params(3, out_bias=0.1, out_scale=1.0), np.zeros(6), 50 * np.ones(6)])
+    for seed in range(4):
+        f = _random_node("D2Q9", 40 + seed, eps=0.3)
+        fr = np.empty_like(f)
+        fr[perm] = f  # population of direction i moves to direction R c_i
+        np.testing.assert_allclose(oracle.invariants(fr), oracle.invariants(f), rtol=1e-12, atol=1e-18)
+        a = oracle.collide_node("D2Q9", 0.6, "learned", f, mlp=mlp)
+        b = oracle.collide_node("D2Q9", 0.6, "learned", fr, mlp=mlp)
+        np.testing.assert_allclose(b[perm], a, atol=1e-16)
+        assert abs(a.sum() - f.sum()) < 1e-15
+
+
+def test_learned_rate_in_open_interval_and_paper_offset():
+    const = {}
+    with open(os.path.join(GOLDEN, "paper_constants.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                const[k] = float(v)
+    off = const["higher_moment_tau_offset"]
+    for z in [-30.0, -2.0, 0.0, 3.0, 30.0]:
+        mlp = _bgk_mlp(0.6)
+        mlp[792] = z  # output bias
+        om = oracle.mlp_omega(mlp, np.zeros(6))
+        assert 0.0 < om < 2.0
+        assert abs(om - 1.0 / (math.exp(z) + off)) < 1e-15
+
+
+# ----------------------------------------------------------------------------- streaming
+@pytest.mark.parametrize("name,dims", [("D2Q9", (5, 4, 1)), ("D2Q9", (7, 3, 1)), ("D3Q19", (5, 4, 3)),
+                                       ("D3Q27", (7, 6, 5)), ("D3Q27", (3, 1, 2))])
+@pytest.mark.parametrize("n", [1, 3])
+def test_streaming_brute_force(name, dims, n):
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    f0 = lbinputs.random_populations(w, N, seed=12)
+    fn = oracle.step(name, dims, 0.8, "none", f0, nsteps=n)
+    nx, ny, nz = dims
+    for i in range(len(w)):
+        grid = f0[i].reshape(nz, ny, nx)
+        # f^n_i(x) = f^0_i(x - n c_i)
+        expect = np.roll(grid, shift=(n * c[i, 2], n * c[i, 1], n * c[i, 0]), axis=(0, 1, 2))
+        np.testing.assert_array_equal(fn[i].reshape(nz, ny, nx), expect)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_global_mass_and_momentum_over_steps(name):
+    d, c, w, _ = oracle.stencil(name)
+    dims = (6, 5, 1) if d == 2 else (4, 3, 5)
+    rho, u = lbinputs.random_moments(dims, seed=13)
+    f0 = oracle.init_eq(name, dims, rho, u)
+    F = lbinputs.random_field((d, oracle.n_nodes(dims)), seed=14, amp=1e-4)
+    for coll in ["bgk", "regularized"]:
+        r0 = oracle.reduce(name, dims, f0)
+        f5 = oracle.step(name, dims, 0.7, coll, f0, nsteps=5)
+        r5 = oracle.reduce(name, dims, f5)
+        np.testing.assert_allclose(r5[:4], r0[:4], atol=1e-12)
+        # with a force, total momentum grows by exactly 5 * sum F (reduce reports sum(j + F/2))
+        f5 = oracle.step(name, dims, 0.7, coll, f0, nsteps=5, F=F)
+        j0 = np.einsum("ia,in->a", c[:, :d], f0)
+        j5 = np.einsum("ia,in->a", c[:, :d], f5)
+        np.testing.assert_allclose(j5 - j0, 5 * F.sum(1), atol=1e-13)
+
+
+def _transpose_xy(f, perm, dims):
+    nx, ny, nz = dims
+    out = np.empty_like(f)
+    for i in range(f.shape[0]):
+        out[perm[i]] = f[i].reshape(nz, ny, nx).transpose(0, 2, 1).ravel()
+    return out
+
+
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("coll", ["bgk", "regularized"])
+def test_step_commutes_with_axis_swap(name, coll):
+    # reflecting the grid across x = y maps the method onto itself
+    d, c, w, _ = oracle.stencil(name)
+    sw = np.stack([c[:, 1], c[:, 0], c[:, 2]], 1)
+    perm = np.array([np.where((c == v).all(1))[0][0] for v in sw])
+    dims = (5, 5, 1) if d == 2 else (4, 4, 3)
+    rho, u = lbinputs.random_moments(dims, seed=15, u_amp=0.08)
+    f0 = oracle.init_eq(name, dims, rho, u) + 1e-3 * lbinputs.random_populations(w, oracle.n_nodes(dims), 16)
+    a = _transpose_xy(oracle.step(name, dims, 0.66, coll, f0, nsteps=3), perm, dims)
+    b = oracle.step(name, dims, 0.66, coll, _transpose_xy(f0, perm, dims), nsteps=3)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- whole scheme
+def _tgv_decay_slope(n, tau, steps, t0):
+    dims, rho, u = lbinputs.taylor_green_2d(n, u0=0.05)
+    f = oracle.init_eq("D2Q9", dims, rho, u)
+    ts, Es = [], []
+    chunk = max(1, steps // 50)
+    t = 0
+    while t <= steps:
+        if t >= t0:
+            ts.append(t)
+            Es.append(oracle.reduce("D2Q9", dims, f)[4])
+        f = oracle.step("D2Q9", dims, tau, "bgk", f, nsteps=chunk)
+        t += chunk
+    slope = np.polyfit(np.array(ts, float), np.log(np.array(Es)), 1)[0]
+    return slope
+
+
+def test_taylor_green_decay_rate_matches_viscosity():
+    # TGV energy decays as exp(-4 nu k^2 t) with nu = c_s^2 (tau - 1/2) (Sec. 2.1 BGK viscosity)
+    tau, n = 0.8, 64
+    nu = CS2 * (tau - 0.5)
+    k = 2 * math.pi / n
+    slope = _tgv_decay_slope(n, tau, 1000, 100)
+    assert abs(slope / (-4 * nu * k * k) - 1) < 0.01
+
+
+def test_taylor_green_decay_error_is_second_order():
+    tau = 0.8
+    nu = CS2 * (tau - 0.5)
+    errs = []
+    for n, steps in [(16, 100), (32, 400), (64, 1600)]:
+        k = 2 * math.pi / n
+        errs.append(abs(_tgv_decay_slope(n, tau, steps, steps // 10) / (-4 * nu * k * k) - 1))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.0 < r1 < 5.5 and 3.0 < r2 < 5.5, errs
+
+
+# ----------------------------------------------------------------------------- moments / reduce
+def test_moments_with_force_carry_half_shift():
+    dims = (4, 3, 1)
+    rho, u = lbinputs.random_moments(dims, seed=17)
+    F = lbinputs.random_field((2, 12), seed=18, amp=1e-3)
+    f = oracle.init_eq("D2Q9", dims, rho, u)
+    r, uu = oracle.moments("D2Q9", dims, f, F=F)
+    np.testing.assert_allclose(uu, u + F / (2 * rho), atol=1e-17)
+
+
+def test_reduce_energy_of_known_field():
+    dims, rho, u = lbinputs.taylor_green_2d(16, u0=0.05)
+    f = oracle.init_eq("D2Q9", dims, rho, u)
+    out = oracle.reduce("D2Q9", dims, f)
+    N = 256
+    assert abs(out[0] - rho.sum()) < 1e-12
+    assert abs(out[4] - 0.5 * (u * u).sum() / N) < 1e-16
+    assert abs(out[5] - 0.5 * (rho * (u * u).sum(0)).sum() / N) < 1e-16
+    # TGV: zero net momentum
+    np.testing.assert_allclose(out[1:4], 0, atol=1e-15)
+
+
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("forced", [False, True])
+def test_regularized_equals_bgk_for_hydrodynamic_nonequilibrium(name, forced):
+    # if f - f^eq lies in the span of the Hermite polynomials of order <= 2, projecting
+    # it changes nothing, so the regularized operator must coincide with BGK
+    d, c, w, _ = oracle.stencil(name)
+    cf = c[:, :d].astype(float)
+    rng = np.random.default_rng(19)
+    rho, u = 1.02, rng.uniform(-0.05, 0.05, d)
+    F = rng.uniform(-1e-3, 1e-3, d) if forced else None
+    # f^neq = w_i [c_i . a1 / cs2 + (c_i c_i - cs2 I) : P / (2 cs2^2)] with a1 = -F/2 (zero unforced)
+    P = rng.uniform(-1e-3, 1e-3, (d, d))
+    P = P + P.T
+    a1 = -0.5 * F if forced else np.zeros(d)
+    Q = np.einsum("ia,ib->iab", cf, cf) - CS2 * np.eye(d)[None]
+    fneq = w * (cf @ a1 / CS2 + np.einsum("iab,ab->i", Q, P) / (2 * CS2 * CS2))
+    # the moments of f: u here is the shifted (physical) velocity, so j = rho u - F/2
+    feq = oracle.init_eq(name, (1, 1, 1), [rho], u.reshape(d, 1))[:, 0]
+    f = feq + fneq
+    a = oracle.collide_node(name, 0.58, "regularized", f, F=F)
+    b = oracle.collide_node(name, 0.58, "bgk", f, F=F)
+    np.testing.assert_allclose(a, b, atol=1e-17)
