@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the fused lattice Boltzmann stream-collide step on one GB300.
+
+Workload (one "step" = one lattice update of the whole grid through the C ABI):
+D3Q19, BGK, FP32 populations in the two-buffer pull layout, 256^3 periodic 3D
+Taylor-Green vortex at Re 1600 and Ma 0.1 (u0 = 0.1 c_s), tau from Re. Prints one
+JSON line with GLUPS, the HBM roofline of the stream-collide kernel, an end-to-end
+number through host buffers, the oracle's CPU baseline, and side measurements
+(AA layout, half-precision storage, the adjoint/forward step-time ratio).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method needs no data exchange between replicas); the time is the maximum
+over ranks and the value is the total of lattice updates over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbinputs  # noqa: E402
+
+METRIC = "GLUPS & % HBM roofline, fused stream-collide; adjoint/forward step time ratio"
+UNIT = "GLUPS"
+N_GRID = 256
+U0 = 0.1 / math.sqrt(3.0)
+RE = 1600.0
+Q19 = 19
+BYTES_PER_LU = {  # algorithmic bytes per lattice update: read Q + write Q populations (+ force read)
+    ("D3Q19", "f32"): 2 * 19 * 4, ("D3Q19", "f16"): 2 * 19 * 2, ("D3Q19", "bf16"): 2 * 19 * 2,
+    ("D3Q19", "f64"): 2 * 19 * 8, ("D2Q9", "f32"): 2 * 9 * 4,
+}
+# DRAM traffic per launch of the D3Q19 FP32 AB stream-collide kernel at 256^3 from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
+# with the listed hash; the hash is recomputed at run time and the figure dropped if it differs.
+NCU_TRAFFIC = {"kernel_hash": None, "bytes_per_launch": None}
+KERNEL_SOURCES = ["lb_device.cuh", "lb_collide.cuh", "lb_kernels.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_12929_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.out = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            text, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            text, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in text.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_steps(lat, k: int, stream):
+    """Device time of k steps of lat (CUDA events on the context's stream), seconds."""
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    lat.step(k)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def tgv_workload(n=N_GRID):
+    tau = lbinputs.tau_from_reynolds(RE, U0, n)
+    dims, rho, u = lbinputs.taylor_green_3d(n, u0=U0)
+    return dims, tau, rho, u
+
+
+def run_ours(args):
+    import torch
+    from paper_2106_12929_gb300 import Lattice, build
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    build.build()
+    stream = torch.cuda.current_stream()
+    dims, tau, rho, u = tgv_workload()
+    N = int(np.prod(dims))
+    rho_d = torch.tensor(rho, device="cuda")
+    u_d = torch.tensor(u, device="cuda")
+
+    lat = Lattice("D3Q19", dims, tau, "bgk", storage="f32", layout="ab")
+    lat.init_from_moments(rho_d, u_d)
+    lat.step(args.warmup)
+    barrier(world)
+    sampler = ClockSampler(dev)
+    launches0 = lat.launch_count()
+    torch.cuda.synchronize()
+    barrier(world)
+    t = time_steps(lat, args.steps, stream)
+    barrier(world)
+    clocks = sampler.stop()
+    launches = lat.launch_count() - launches0
+    lat.check()
+    t_max = max_over_ranks(t, world)
+    glups = world * N * args.steps / t_max / 1e9
+
+    # roofline of the dominant kernel (one stream-collide launch per step)
+    per_launch = t / args.steps
+    alg_bytes = BYTES_PER_LU[("D3Q19", "f32")] * N
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / per_launch / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["kernel_hash"] == kernel_hash() else None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_update<D3Q19, float, BGK, AB>", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = side_measurements(lat, stream, dims, tau, rho_d, u_d, args, glups / world)
+    lat.close()
+
+    # end to end through the public API with host buffers: H2D of (rho, u), K steps, D2H of (rho, u)
+    rho_h = torch.tensor(rho).pin_memory()
+    u_h = torch.tensor(u).pin_memory()
+    lat = Lattice("D3Q19", dims, tau, "bgk", storage="f32", layout="ab")
+    lat.init_from_moments(rho_h, u_h)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    lat.init_from_moments(rho_h, u_h)
+    lat.step(args.steps)
+    r_out, u_out = lat.moments(torch.float64, "cpu")
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    barrier(world)
+    t_e2e = max_over_ranks(t_e2e, world)
+    lat.close()
+    e2e = {"value": round(world * N * args.steps / t_e2e / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int((rho_h.numel() + u_h.numel()) * 8 / args.steps),
+           "d2h_bytes_per_step": int((r_out.numel() + u_out.numel()) * 8 / args.steps),
+           "what": "lb_init_from_moments(host rho, u) + lb_step(K) + lb_moments(host), wall clock"}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": round(glups, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "D3Q19 BGK FP32 two-buffer pull stream-collide, 256^3 periodic 3D Taylor-Green "
+                               f"vortex, Re {RE:g}, Ma 0.1 (u0 = {U0:.6f}), tau = {tau:.6f}",
+                   "grid": list(dims), "nodes": N, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (two 1.27 GB population buffers per replica)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks, "extra": extra,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
+    """AA layout, half-precision storage and the adjoint/forward ratio (rank 0, not in `value`)."""
+    import torch
+    from paper_2106_12929_gb300 import Lattice
+    N = int(np.prod(dims))
+    k = max(50, args.steps // 2)
+    out = {"d3q19_f32_ab_glups": round(glups_ab, 3)}
+    for layout, storage in [("aa", "f32"), ("ab", "f16"), ("ab", "bf16"), ("aa", "f16")]:
+        lat = Lattice("D3Q19", dims, tau, "bgk", storage=storage, layout=layout)
+        lat.init_from_moments(rho_d, u_d)
+        lat.step(4)
+        t = time_steps(lat, k, stream)
+        g = N * k / t / 1e9
+        out[f"d3q19_{storage}_{layout}_glups"] = round(g, 3)
+        out[f"d3q19_{storage}_{layout}_hbm_frac"] = round(
+            g * BYTES_PER_LU[("D3Q19", storage)] / measured_peak_hbm()[0], 4)
+        lat.close()
+    out["f16_over_f32_glups"] = round(out["d3q19_f16_ab_glups"] / glups_ab, 3)
+    out.update(adjoint_ratio(stream))
+    return out
+
+
+def adjoint_ratio(stream, n=1024, steps=500, k=50):
+    """D2Q9 BGK + Guo force, FP32, 1024^2 shear layer, 500 steps, checkpoints every 50:
+    (recompute + adjoint) time over forward-with-recording time."""
+    import torch
+    from paper_2106_12929_gb300 import Lattice
+    dims, rho, u = lbinputs.shear_layer(n, u0=0.05)
+    N = n * n
+    F = torch.tensor(lbinputs.smooth_force(dims, 1e-5, seed=12929), dtype=torch.float32, device="cuda")
+    et = torch.full((N,), 1e-3, dtype=torch.float32, device="cuda")
+    lat = Lattice("D2Q9", dims, 0.51, "bgk", storage="f32", record_every=k)
+    lat.set_force(F)
+    rho_d = torch.tensor(rho, dtype=torch.float32, device="cuda")
+    u_d = torch.tensor(u, dtype=torch.float32, device="cuda")
+    res = {}
+    for rep in range(2):  # the first pass allocates checkpoints and recompute buffers
+        lat.init_from_moments(rho_d, u_d)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        gF = torch.zeros((2, N), dtype=torch.float32, device="cuda")
+        _, lamT = lat.loss_energy(et, grad_F=gF)
+        torch.cuda.synchronize()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record(stream)
+        lat.step_adjoint(lamT, steps, grad_F=gF, want_lambda0=False)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fwd = e0.elapsed_time(e1) / 1e3
+        bwd = e1b.elapsed_time(e2) / 1e3
+        res = {"adjoint_forward_ratio": round(bwd / fwd, 3), "adjoint_fwd_ms_per_step": round(fwd / steps * 1e3, 4),
+               "adjoint_bwd_ms_per_step": round(bwd / steps * 1e3, 4),
+               "adjoint_workload": "D2Q9 BGK+Guo FP32 1024^2 shear layer, 500 steps, checkpoint every 50"}
+    lat.close()
+    return res
+
+
+def cpu_baseline(sample_steps: int = 1):
+    """The FP64 CPU oracle on this host, on a bounded sample of the same workload: the full
+    256^3 D3Q19 grid for `sample_steps` step(s)."""
+    import oracle
+    dims, tau, rho, u = tgv_workload()
+    N = int(np.prod(dims))
+    f = oracle.init_eq("D3Q19", dims, rho, u)
+    t0 = time.perf_counter()
+    oracle.step("D3Q19", dims, tau, "bgk", f, nsteps=sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(N * sample_steps / dt / 1e9, 5), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"D3Q19 BGK FP64, 256^3 TGV, {sample_steps} step(s) ({dt:.1f} s wall)"}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores as the reference arm: each step is one lattice
+    update of a 64^3 periodic TGV at the same Re and Ma (a bounded sample of the workload)."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    n = 64
+    dims, tau, rho, u = tgv_workload(n)
+    N = n ** 3
+    f = oracle.init_eq("D3Q19", dims, rho, u)
+    f = oracle.step("D3Q19", dims, tau, "bgk", f, nsteps=args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.step("D3Q19", dims, tau, "bgk", f, nsteps=args.steps)
+    dt = time.perf_counter() - t0
+    value = N * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "D3Q19 BGK FP64 oracle (plain C, host cores), 64^3 periodic 3D Taylor-Green vortex, "
+                               "Re 1600, Ma 0.1: a bounded per-step sample of the 256^3 workload",
+                   "grid": list(dims), "nodes": N},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"64^3 D3Q19 grid, {args.steps} steps"},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * liblb — lattice Boltzmann stream-and-collide on one GB300 (sm_103a), C ABI.
+ *
+ * The library advances the particle populations f_i(x, t) of a periodic Cartesian
+ * grid by the lattice Boltzmann equation f_i(x + c_i, t + 1) = f_i(x, t) + Omega_i(f)
+ * (Bedrunka et al., arXiv 2106.12929, Sec. 2.1, Eq. 1) with
+ *   - the D2Q9, D3Q19 and D3Q27 velocity sets (Sec. 2.2, 3.1, 3.3),
+ *   - the second-order equilibrium (Eq. 3) and the moments rho, rho u (Eq. 4),
+ *   - BGK (Eq. 2), regularized (Sec. 2.1) or moment-space collision with a learned
+ *     higher-moment relaxation rate (Eq. 5, Sec. 3.1), and a Guo body force,
+ * plus the discrete adjoint of the time stepping (gradients through the solver,
+ * Sec. 3.2) and the Eq. 6 training loss.
+ *
+ * Conventions for every call
+ *   - Grid: dims = {nx, ny, nz}; 2D stencils need nz == 1. Node n = x + nx (y + ny z).
+ *     N = nx ny nz nodes, N < 2^31. Every direction is periodic.
+ *   - Arrays crossing the boundary are dense, component-major, x fastest:
+ *     populations f[Q][N], velocity u[d][N], force F[d][N], density rho[N].
+ *     Their element type and location are given by an lb_mem value; device pointers
+ *     must be on the context's device. The caller owns every buffer it passes; the
+ *     library copies in or out on the context's stream and keeps no pointer to it.
+ *   - The exposed state is always the PRE-collision state f^n of Eq. 1, whatever
+ *     the internal layout (two-buffer pull, or in-place AA) and storage type.
+ *   - Calls are asynchronous on the context's stream except where a result is
+ *     returned in host memory (those synchronise the stream before returning).
+ *   - Errors are returned as lb_status; nothing aborts, exits or traps. On an
+ *     argument error the context is unchanged. On a CUDA error the context is
+ *     marked failed and every later call returns LB_ERR_STATE. lb_last_error()
+ *     gives a message for the calling thread.
+ *   - A context is not thread safe; use one context per thread or lock around it.
+ */
+#ifndef LIBLB_LB_H
+#define LIBLB_LB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LB_API __attribute__((visibility("default")))
+#else
+#define LB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx; /* opaque, owned by the library */
+
+typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_stencil;
+
+/* Collision operator.
+ *   LB_BGK          Eq. 2: f* = f - (f - f^eq)/tau (+ Guo source).
+ *   LB_REGULARIZED  Latt & Chopard (Sec. 2.1): relax only the projection of f - f^eq
+ *                   onto the Hermite polynomials of order <= 2 (+ Guo source).
+ *   LB_LEARNED_MRT  Eq. 5 on D2Q9: Hermite moments; stress rows relax with 1/tau,
+ *                   the three higher rows with 1/(exp(z) + 1/2), z = a per-node
+ *                   6-24-24-1 tanh network of local moment invariants (Sec. 3.1).
+ *                   No body force.
+ *   LB_NONE         streaming only (f* = f); the force is ignored. For tests. */
+typedef enum { LB_BGK = 0, LB_REGULARIZED = 1, LB_LEARNED_MRT = 2, LB_NONE = 3 } lb_collision;
+
+/* Storage of the populations in device memory. Arithmetic is FP64 for LB_F64 and
+ * FP32 otherwise. The half types store the shifted value f_i - w_i, rounded to
+ * nearest even, and add w_i back on load. */
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16_SHIFTED = 2, LB_BF16_SHIFTED = 3 } lb_storage;
+
+/* LB_LAYOUT_AB: two population buffers, one fused pull-stream + collide launch per
+ *               step from one into the other.
+ * LB_LAYOUT_AA: one buffer updated in place, alternating even and odd steps
+ *               (half the memory of AB, the same bytes moved per step). */
+typedef enum { LB_LAYOUT_AB = 0, LB_LAYOUT_AA = 1 } lb_layout;
+
+/* Element type and location of an array argument. */
+typedef enum { LB_HOST_F64 = 0, LB_DEVICE_F64 = 1, LB_HOST_F32 = 2, LB_DEVICE_F32 = 3 } lb_mem;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,         /* bad argument; nothing was done */
+    LB_ERR_OOM = 2,         /* device allocation failed */
+    LB_ERR_CUDA = 3,        /* a CUDA call failed; the context is now failed */
+    LB_ERR_UNSTABLE = 4,    /* a node had a non-finite or non-positive density */
+    LB_ERR_STATE = 5,       /* call not valid in the current state (or context failed) */
+    LB_ERR_UNSUPPORTED = 6  /* valid but not provided (e.g. learned collision on D3Q19) */
+} lb_status;
+
+typedef struct {
+    lb_storage storage;   /* default LB_F32 */
+    lb_layout layout;     /* default LB_LAYOUT_AB */
+    void* cuda_stream;    /* cudaStream_t of all work; NULL = the legacy default stream */
+    int device;           /* CUDA device ordinal; -1 (default) = the current device */
+    int check_every;      /* >0: lb_step synchronises every check_every steps and at its end
+                             and returns LB_ERR_UNSTABLE if a node went bad; 0 (default) = never */
+    int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
+                             lb_step_adjoint can run backwards (AB layout only); 0 = off */
+} lb_options;
+
+/* Fill *opt with the defaults listed above. */
+LB_API void lb_default_options(lb_options* opt);
+
+/* Create a context: validate, allocate the population buffer(s) on opt->device and
+ * zero them. tau > 1/2 is the BGK relaxation time of Eq. 2 (viscosity
+ * nu = c_s^2 (tau - 1/2)); for LB_LEARNED_MRT it is the stress relaxation time
+ * tau_n of Sec. 3.1. opt may be NULL (defaults). On success *out owns the memory
+ * until lb_destroy. Errors: LB_ERR_ARG (dims, tau, enum values), LB_ERR_UNSUPPORTED
+ * (learned collision on a stencil other than D2Q9), LB_ERR_OOM, LB_ERR_CUDA. */
+LB_API lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau,
+                    lb_collision collision, const lb_options* opt);
+
+/* Release every device buffer of the context (synchronises its stream). NULL is a no-op. */
+LB_API void lb_destroy(lb_ctx* ctx);
+
+/* f_i = f_i^eq(rho, u) at every node (Eq. 3), as the pre-collision state f^0.
+ * rho[N], u[d][N]. The velocity is used as given (no force shift). Resets the
+ * step counter and any recording. */
+LB_API lb_status lb_init_from_moments(lb_ctx* ctx, const void* rho, const void* u, lb_mem mem);
+
+/* Set the body force F[d][N] (constant in time); NULL clears it. The velocity of a
+ * forced state is u = (sum_i c_i f_i + F/2)/rho and the Guo source
+ * S_i = (1 - omega/2) w_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F is added in
+ * the collision (Guo, Zheng & Shi 2002; the paper only mentions forcing, Sec. 2.2). */
+LB_API lb_status lb_set_force(lb_ctx* ctx, const void* F, lb_mem mem);
+
+/* Network of the learned collision (Sec. 3.1), n_params = 805 values:
+ * W1[24][6], b1[24], W2[24][24], b2[24], W3[24], b3 (793 trained parameters), then
+ * the fixed input shift[6] and scale[6] (input k is (I_k - shift_k) scale_k).
+ * Only valid for LB_LEARNED_MRT contexts. */
+LB_API lb_status lb_set_mlp(lb_ctx* ctx, const void* params, int64_t n_params, lb_mem mem);
+
+/* Advance n >= 0 steps of Eq. 1 (one fused kernel launch per step). */
+LB_API lb_status lb_step(lb_ctx* ctx, int64_t n);
+
+/* rho[N] and u[d][N] of the current pre-collision state (Eq. 4, with the force
+ * shift if a force is set). Either pointer may be NULL. */
+LB_API lb_status lb_moments(lb_ctx* ctx, void* rho, void* u, lb_mem mem);
+
+/* Global sums of the current state, accumulated in FP64 in a fixed order
+ * (deterministic): out[0] = sum rho, out[1..3] = sum rho u (x, y, z; z = 0 in 2D),
+ * out[4] = (1/2N) sum |u|^2 (incompressible kinetic energy), out[5] = (1/2N) sum rho |u|^2.
+ * out is host memory; the call synchronises the stream. */
+LB_API lb_status lb_reduce(lb_ctx* ctx, double out[6]);
+
+/* Copy the current pre-collision state out as f[Q][N] (natural layout, unshifted). */
+LB_API lb_status lb_get_populations(lb_ctx* ctx, void* f, lb_mem mem);
+
+/* Replace the state by f[Q][N] (pre-collision, natural layout). Resets the step
+ * counter and any recording. */
+LB_API lb_status lb_set_populations(lb_ctx* ctx, const void* f, lb_mem mem);
+
+/* Synchronise the stream and report LB_ERR_UNSTABLE if any node of any step since
+ * the last check had a non-finite or non-positive density (the flag is then cleared). */
+LB_API lb_status lb_check(lb_ctx* ctx);
+
+/* Steps taken since the last initialisation. */
+LB_API int64_t lb_steps_taken(const lb_ctx* ctx);
+
+/* ------------------------------------------------------------------ adjoint ---- */
+/* The discrete adjoint of f^{n+1} = S C(f^n; F), S the periodic shift along c_i
+ * (Sec. 3.2 takes such gradients by automatic differentiation; here they are
+ * written out): lambda^n = J_C(f^n; F)^T S^T lambda^{n+1}, dL/dF += (dC/dF)^T S^T lambda^{n+1}. */
+
+/* Seed from moment cotangents of the current state: given dL/drho[N] (may be NULL)
+ * and dL/du[d][N], write lambda = dL/df [Q][N] and add the force's direct part
+ * dL/du / (2 rho) to grad_F[d][N] (grad_F may be NULL). */
+LB_API lb_status lb_adjoint_seed_moments(lb_ctx* ctx, const void* grad_rho, const void* grad_u, void* lambda,
+                                  void* grad_F, lb_mem mem);
+
+/* Kinetic-energy-field loss L = sum_x (e(x) - e*(x))^2, e = rho |u|^2 / 2, of the
+ * current state: *loss (host, FP64), lambda = dL/df [Q][N], grad_F += dL/dF's direct
+ * part (may be NULL). e_target[N]. Synchronises the stream. */
+LB_API lb_status lb_loss_energy(lb_ctx* ctx, const void* e_target, double* loss, void* lambda, void* grad_F,
+                         lb_mem mem);
+
+/* Eq. 6 loss of the current D2Q9 state against targets u_ref[2][N], w_ref[N] (vorticity)
+ * and E_ref: L = 0.6 mean|u - u_ref|^2 + 0.2 mean(w - w_ref)^2 + 0.2 (E - E_ref)^2 with
+ * w by central differences and E = (1/2N) sum |u|^2. *loss (host, FP64) and
+ * lambda = dL/df [Q][N]. No force. Synchronises the stream. */
+LB_API lb_status lb_loss_eq6(lb_ctx* ctx, const void* u_ref, const void* w_ref, double E_ref, double* loss,
+                      void* lambda, lb_mem mem);
+
+/* Run the adjoint back over the n steps recorded since the last initialisation
+ * (n must equal lb_steps_taken and the context must have record_every > 0).
+ * lambda_T[Q][N] = dL/df^n of the current state. Outputs (each may be NULL):
+ * lambda_0[Q][N] = dL/df^0; grad_F[d][N] += dL/dF; grad_theta[793] += dL/dtheta
+ * (learned collision only). Recomputes each checkpoint segment forward once.
+ * The state is left at f^n. */
+LB_API lb_status lb_step_adjoint(lb_ctx* ctx, const void* lambda_T, int64_t n, void* lambda_0, void* grad_F,
+                          void* grad_theta, lb_mem mem);
+
+/* One Adam update of n parameters in device memory (FP32):
+ * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ * theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). t >= 1 is the step
+ * number. Runs on `stream` (NULL = legacy default stream). */
+LB_API lb_status lb_adam_update(float* theta, float* m, float* v, const float* grad, int64_t n, double lr, double b1,
+                         double b2, double eps, int64_t t, void* stream);
+
+/* ------------------------------------------------------------------ info ---- */
+LB_API int64_t lb_num_nodes(const lb_ctx* ctx);
+LB_API int lb_q(const lb_ctx* ctx);
+LB_API int lb_d(const lb_ctx* ctx);
+/* Kernel launches issued by this context since creation (for launch accounting). */
+LB_API int64_t lb_launch_count(const lb_ctx* ctx);
+LB_API const char* lb_status_string(lb_status s);
+/* Message of the last error on the calling thread ("" if none). */
+LB_API const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBLB_LB_H */

@@ -55,7 +55,7 @@ def _load():
             for name in ("ora_stencil", "ora_init_eq", "ora_step", "ora_collide_node", "ora_moments",
                          "ora_reduce", "ora_adjoint", "ora_seed_moments", "ora_loss_energy",
                          "ora_loss_eq6", "ora_vorticity", "ora_mlp_omega", "ora_invariants",
-                         "ora_guo_source"):
+                         "ora_guo_source", "ora_num_threads"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -252,3 +252,8 @@ def invariants(f):
     I = np.zeros(6)
     _check(_load().ora_invariants(_p(_arr(f, (9,))), _p(I)), "invariants")
     return I
+
+
+def num_threads() -> int:
+    """Threads the oracle's node loops run on (OpenMP)."""
+    return int(_load().ora_num_threads())

@@ -936,3 +936,11 @@ int ora_vorticity(const int64_t* dims, const double* f, double* w, double* E)
 
 int ora_num_mlp(void) { return NMLP; }
 int ora_num_theta(void) { return NTHETA; }
+
+/* number of threads the node loops of ora_step use */
+#ifdef _OPENMP
+#include <omp.h>
+int ora_num_threads(void) { return omp_get_max_threads(); }
+#else
+int ora_num_threads(void) { return 1; }
+#endif

@@ -1,0 +1,6 @@
+// D3Q19 kernels with __half population storage (every collision, force on/off, layout).
+#include "lb_kernels.cuh"
+
+namespace lb {
+cudaError_t run_op_d3q19_f16(const OpArgs& a) { return run_op_typed<D3Q19, __half>(a); }
+}  // namespace lb

@@ -1,0 +1,6 @@
+// D3Q19 kernels with float population storage (every collision, force on/off, layout).
+#include "lb_kernels.cuh"
+
+namespace lb {
+cudaError_t run_op_d3q19_f32(const OpArgs& a) { return run_op_typed<D3Q19, float>(a); }
+}  // namespace lb

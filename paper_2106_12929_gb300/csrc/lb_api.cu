@@ -1,0 +1,794 @@
+// C-ABI of liblb (declared in include/lb.h): context management, argument
+// checking, host/device staging, kernel dispatch, checkpointed adjoint driver.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb.h"
+#include "lb_ops.cuh"
+#include "lb_learned.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lb_status fail(lb_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+int storage_bytes(int s) { return s == LB_F64 ? 8 : (s == LB_F32 ? 4 : 2); }
+int real_bytes(int s) { return s == LB_F64 ? 8 : 4; }
+
+// Make the context's device current for the lifetime of the guard.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct lb_ctx {
+    int stencil = 0, Q = 9, D = 2;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t N = 0, plane = 0;
+    double tau = 1.0, omega = 1.0;
+    int coll = LB_BGK;
+    lb_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lb::Geom g{};
+
+    void* ab[2] = {nullptr, nullptr};  // AB ping-pong buffers (AA uses ab[0])
+    void* state = nullptr;             // buffer holding the current state
+    int aa_parity = 0;                 // AA: 0 natural (even), 1 odd
+    void* F = nullptr;                 // force [D][plane], arithmetic type
+    std::vector<double> net;           // learned network (805 values), passed to kernels by value
+    unsigned* status = nullptr;
+    double* partials = nullptr;
+    int64_t partials_cap = 0;
+    double* dsmall = nullptr;          // device scratch for small results (8 doubles)
+    int64_t steps = 0;
+    int64_t launches = 0;
+    bool failed = false;
+
+    // recording for the adjoint
+    bool recording = false;
+    std::vector<void*> ckpt;   // ckpt[s] represents f^{s k}
+    std::vector<void*> ring;   // k - 1 recompute buffers
+    void* lam[2] = {nullptr, nullptr};
+    void* gF = nullptr;        // force-gradient accumulator [D][plane]
+    void* gtheta = nullptr;    // learned: per-block parameter gradient partials
+    int64_t gtheta_cap = 0;
+};
+
+namespace {
+
+int64_t pop_bytes(const lb_ctx* c) { return (int64_t)c->Q * c->plane * storage_bytes(c->opt.storage); }
+int64_t real_pop_bytes(const lb_ctx* c) { return (int64_t)c->Q * c->plane * real_bytes(c->opt.storage); }
+
+lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* what)
+{
+    if (c) c->failed = true;
+    return fail(LB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LB_CUDA(ctx, call, what)                                  \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return cuda_fail((ctx), _e, what); \
+    } while (0)
+
+lb_status alloc(lb_ctx* c, void** p, int64_t bytes, const char* what)
+{
+    cudaError_t e = cudaMalloc(p, (size_t)bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "allocating %lld bytes for %s: %s", (long long)bytes, what, cudaGetErrorString(e));
+    }
+    (void)c;
+    return LB_OK;
+}
+
+bool mem_host(lb_mem m) { return m == LB_HOST_F64 || m == LB_HOST_F32; }
+int mem_f64(lb_mem m) { return (m == LB_HOST_F64 || m == LB_DEVICE_F64) ? 1 : 0; }
+bool mem_valid(int m) { return m >= 0 && m <= 3; }
+
+lb_status check_ctx(const lb_ctx* c)
+{
+    if (!c) return fail(LB_ERR_ARG, "null context");
+    if (c->failed) return fail(LB_ERR_STATE, "context failed after an earlier CUDA error");
+    return LB_OK;
+}
+
+lb::OpArgs base_args(lb_ctx* c, int op)
+{
+    lb::OpArgs a;
+    a.op = op;
+    a.storage = c->opt.storage;
+    a.coll = c->coll;
+    a.force = c->F != nullptr && c->coll != LB_NONE;
+    a.mode = c->opt.layout == LB_LAYOUT_AB ? lb::AB : (c->aa_parity ? lb::AA_ODD : lb::AA_EVEN);
+    a.src = c->state;
+    a.F = c->F;
+    a.g = c->g;
+    a.omega = c->omega;
+    a.status = c->status;
+    a.stream = c->stream;
+    return a;
+}
+
+lb_status launch(lb_ctx* c, const lb::OpArgs& a, const char* what)
+{
+    cudaError_t e;
+    if (a.coll == LB_LEARNED_MRT && (a.op == lb::OP_UPDATE || a.op == lb::OP_ADJ_STEP))
+        e = lb::run_learned_d2q9(a, c->net.data());
+    else
+        e = lb::run_op(c->stencil, a);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return LB_OK;
+}
+
+// Staging of caller arrays: device arrays are used in place; host arrays are
+// copied through a stream-ordered temporary device buffer.
+struct Staged {
+    lb_ctx* c = nullptr;
+    void* dev = nullptr;
+    void* tmp = nullptr;
+    int64_t bytes = 0;
+    ~Staged()
+    {
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+};
+
+lb_status stage_in(lb_ctx* c, Staged& s, const void* p, int64_t count, lb_mem m, const char* what)
+{
+    s.c = c;
+    s.bytes = count * (mem_f64(m) ? 8 : 4);
+    if (!mem_host(m)) {
+        s.dev = const_cast<void*>(p);
+        return LB_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&s.tmp, (size_t)s.bytes, c->stream);
+    if (e != cudaSuccess) {
+        s.tmp = nullptr;
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "staging %s: %s", what, cudaGetErrorString(e));
+    }
+    LB_CUDA(c, cudaMemcpyAsync(s.tmp, p, (size_t)s.bytes, cudaMemcpyHostToDevice, c->stream), what);
+    s.dev = s.tmp;
+    return LB_OK;
+}
+
+lb_status stage_out_alloc(lb_ctx* c, Staged& s, void* p, int64_t count, lb_mem m, bool copy_in, const char* what)
+{
+    s.c = c;
+    s.bytes = count * (mem_f64(m) ? 8 : 4);
+    if (!mem_host(m)) {
+        s.dev = p;
+        return LB_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&s.tmp, (size_t)s.bytes, c->stream);
+    if (e != cudaSuccess) {
+        s.tmp = nullptr;
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "staging %s: %s", what, cudaGetErrorString(e));
+    }
+    if (copy_in) LB_CUDA(c, cudaMemcpyAsync(s.tmp, p, (size_t)s.bytes, cudaMemcpyHostToDevice, c->stream), what);
+    s.dev = s.tmp;
+    return LB_OK;
+}
+
+lb_status stage_out_finish(lb_ctx* c, Staged& s, void* p, const char* what)
+{
+    if (!s.tmp) return LB_OK;
+    LB_CUDA(c, cudaMemcpyAsync(p, s.tmp, (size_t)s.bytes, cudaMemcpyDeviceToHost, c->stream), what);
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), what);
+    return LB_OK;
+}
+
+lb_status ensure_partials(lb_ctx* c, int64_t count)
+{
+    if (c->partials_cap >= count) return LB_OK;
+    if (c->partials) cudaFree(c->partials);
+    c->partials = nullptr;
+    c->partials_cap = 0;
+    lb_status s = alloc(c, (void**)&c->partials, count * 8, "reduction partials");
+    if (s == LB_OK) c->partials_cap = count;
+    return s;
+}
+
+void reset_recording(lb_ctx* c)
+{
+    c->recording = false;
+    c->steps = 0;
+}
+
+lb_status record_begin(lb_ctx* c)
+{
+    if (c->ckpt.empty()) {
+        void* p = nullptr;
+        lb_status s = alloc(c, &p, pop_bytes(c), "checkpoint");
+        if (s != LB_OK) return s;
+        c->ckpt.push_back(p);
+    }
+    LB_CUDA(c, cudaMemcpyAsync(c->ckpt[0], c->state, (size_t)pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream),
+            "checkpoint copy");
+    c->recording = true;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_default_options(lb_options* o)
+{
+    if (!o) return;
+    o->storage = LB_F32;
+    o->layout = LB_LAYOUT_AB;
+    o->cuda_stream = nullptr;
+    o->device = -1;
+    o->check_every = 0;
+    o->record_every = 0;
+}
+
+lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau, lb_collision coll,
+                    const lb_options* opt)
+{
+    if (!out) return fail(LB_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!dims) return fail(LB_ERR_ARG, "dims is null");
+    if ((int)stencil < 0 || (int)stencil > 2) return fail(LB_ERR_ARG, "unknown stencil %d", (int)stencil);
+    if ((int)coll < 0 || (int)coll > 3) return fail(LB_ERR_ARG, "unknown collision %d", (int)coll);
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_ERR_ARG, "tau must be a finite number > 1/2 (got %g)", tau);
+    lb_options o;
+    lb_default_options(&o);
+    if (opt) o = *opt;
+    if ((int)o.storage < 0 || (int)o.storage > 3) return fail(LB_ERR_ARG, "unknown storage %d", (int)o.storage);
+    if ((int)o.layout < 0 || (int)o.layout > 1) return fail(LB_ERR_ARG, "unknown layout %d", (int)o.layout);
+    if (o.check_every < 0 || o.record_every < 0) return fail(LB_ERR_ARG, "negative check_every / record_every");
+    const int D = stencil == LB_D2Q9 ? 2 : 3;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > 65535) return fail(LB_ERR_ARG, "dims[%d] = %lld out of [1, 65535]", a, (long long)dims[a]);
+    if (D == 2 && dims[2] != 1) return fail(LB_ERR_ARG, "2D stencil needs dims[2] == 1");
+    const int64_t N = dims[0] * dims[1] * dims[2];
+    if (N >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "grid of %lld nodes exceeds 2^31 - 1", (long long)N);
+    if (coll == LB_LEARNED_MRT && stencil != LB_D2Q9)
+        return fail(LB_ERR_UNSUPPORTED, "the learned collision is defined for D2Q9 only");
+    if (o.record_every > 0 && o.layout != LB_LAYOUT_AB)
+        return fail(LB_ERR_UNSUPPORTED, "recording for the adjoint needs the AB layout");
+
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(LB_ERR_CUDA, "no CUDA device");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) return fail(LB_ERR_ARG, "bad device %d", dev);
+    DeviceGuard guard(dev);
+    if (!guard.ok) return fail(LB_ERR_CUDA, "cannot select device %d", dev);
+
+    lb_ctx* c = new lb_ctx();
+    c->stencil = stencil;
+    c->Q = stencil == LB_D2Q9 ? 9 : (stencil == LB_D3Q19 ? 19 : 27);
+    c->D = D;
+    for (int a = 0; a < 3; ++a) c->dims[a] = dims[a];
+    c->N = N;
+    // pad each population plane to a multiple of 64 elements (128 B for half, 512 B for FP64)
+    c->plane = (N + 63) / 64 * 64;
+    c->tau = tau;
+    c->omega = 1.0 / tau;
+    c->coll = coll;
+    c->opt = o;
+    c->device = dev;
+    c->stream = (cudaStream_t)o.cuda_stream;
+    c->g.nx = (int)dims[0];
+    c->g.ny = (int)dims[1];
+    c->g.nz = (int)dims[2];
+    c->g.plane = c->plane;
+
+    lb_status s = LB_OK;
+    const int nbuf = o.layout == LB_LAYOUT_AB ? 2 : 1;
+    for (int b = 0; b < nbuf && s == LB_OK; ++b) s = alloc(c, &c->ab[b], pop_bytes(c), "population buffer");
+    if (s == LB_OK) s = alloc(c, (void**)&c->status, 64, "status word");
+    if (s == LB_OK) s = alloc(c, (void**)&c->dsmall, 64, "small results");
+    if (s != LB_OK) {
+        lb_destroy(c);
+        return s;
+    }
+    c->state = c->ab[0];
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < nbuf && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->ab[b], 0, (size_t)pop_bytes(c), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 64, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lb_destroy(c);
+        return fail(LB_ERR_CUDA, "initialising buffers: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    cudaStreamSynchronize(c->stream);
+    void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
+                    c->gF, c->gtheta};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (void* p : c->ckpt)
+        if (p) cudaFree(p);
+    for (void* p : c->ring)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+lb_status lb_init_from_moments(lb_ctx* c, const void* rho, const void* u, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!rho || !u || !mem_valid(m)) return fail(LB_ERR_ARG, "rho, u and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged sr, su;
+    if ((s = stage_in(c, sr, rho, c->N, m, "rho")) != LB_OK) return s;
+    if ((s = stage_in(c, su, u, c->N * c->D, m, "u")) != LB_OK) return s;
+    c->aa_parity = 0;
+    c->state = c->ab[0];
+    lb::OpArgs a = base_args(c, lb::OP_INIT_EQ);
+    a.dst = c->state;
+    a.in0 = sr.dev;
+    a.in1 = su.dev;
+    a.io_f64 = mem_f64(m);
+    if ((s = launch(c, a, "init_eq")) != LB_OK) return s;
+    reset_recording(c);
+    return LB_OK;
+}
+
+lb_status lb_set_force(lb_ctx* c, const void* F, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
+    if (F && c->coll == LB_LEARNED_MRT) return fail(LB_ERR_UNSUPPORTED, "the learned collision takes no force");
+    DeviceGuard guard(c->device);
+    if (!F) {
+        if (c->F) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->F);
+        }
+        c->F = nullptr;
+        return LB_OK;
+    }
+    if (!c->F) {
+        const int64_t bytes = (int64_t)c->D * c->plane * real_bytes(c->opt.storage);
+        if ((s = alloc(c, &c->F, bytes, "force")) != LB_OK) return s;
+        LB_CUDA(c, cudaMemsetAsync(c->F, 0, (size_t)bytes, c->stream), "force clear");
+    }
+    Staged sf;
+    if ((s = stage_in(c, sf, F, c->N * c->D, m, "force")) != LB_OK) return s;
+    LB_CUDA(c, lb::convert_copy(sf.dev, mem_f64(m), c->F, c->opt.storage == LB_F64, c->N, c->N, c->plane, c->D, 0,
+                                c->stream),
+            "force copy");
+    c->launches += 1;
+    return LB_OK;
+}
+
+lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (c->coll != LB_LEARNED_MRT) return fail(LB_ERR_STATE, "context does not use the learned collision");
+    if (!params || n != lb::kNetValues || !mem_valid(m))
+        return fail(LB_ERR_ARG, "need %d network values (got %lld)", lb::kNetValues, (long long)n);
+    DeviceGuard guard(c->device);
+    const int f64 = mem_f64(m);
+    std::vector<unsigned char> tmp((size_t)n * (f64 ? 8 : 4));
+    if (mem_host(m)) {
+        std::memcpy(tmp.data(), params, tmp.size());
+    } else {
+        // the values are passed to the kernels by value, so they come to the host
+        LB_CUDA(c, cudaMemcpyAsync(tmp.data(), params, tmp.size(), cudaMemcpyDeviceToHost, c->stream), "network read");
+        LB_CUDA(c, cudaStreamSynchronize(c->stream), "network read");
+    }
+    std::vector<double> v((size_t)n);
+    for (int64_t k = 0; k < n; ++k)
+        v[(size_t)k] = f64 ? ((const double*)tmp.data())[k] : (double)((const float*)tmp.data())[k];
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(LB_ERR_ARG, "network values must be finite");
+    c->net.swap(v);
+    return LB_OK;
+}
+
+static lb_status step_once(lb_ctx* c)
+{
+    const int k = c->opt.record_every;
+    lb::OpArgs a = base_args(c, lb::OP_UPDATE);
+    if (c->opt.layout == LB_LAYOUT_AA) {
+        a.dst = c->state;
+        lb_status s = launch(c, a, "stream-collide (AA)");
+        if (s != LB_OK) return s;
+        c->aa_parity ^= 1;
+        c->steps += 1;
+        return LB_OK;
+    }
+    void* dst = (c->state == c->ab[0]) ? c->ab[1] : c->ab[0];
+    if (k > 0 && (c->steps + 1) % k == 0) {
+        const size_t slot = (size_t)((c->steps + 1) / k);
+        while (c->ckpt.size() <= slot) {
+            void* p = nullptr;
+            lb_status s = alloc(c, &p, pop_bytes(c), "checkpoint");
+            if (s != LB_OK) return s;
+            c->ckpt.push_back(p);
+        }
+        dst = c->ckpt[slot];
+    }
+    a.dst = dst;
+    lb_status s = launch(c, a, "stream-collide");
+    if (s != LB_OK) return s;
+    c->state = dst;
+    c->steps += 1;
+    return LB_OK;
+}
+
+lb_status lb_check(lb_ctx* c)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    DeviceGuard guard(c->device);
+    unsigned h = 0;
+    LB_CUDA(c, cudaMemcpyAsync(&h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "status read");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "status sync");
+    if (h) {
+        LB_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream), "status clear");
+        return fail(LB_ERR_UNSTABLE, "a node had a non-finite or non-positive density");
+    }
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int64_t n)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (n < 0) return fail(LB_ERR_ARG, "negative step count");
+    if (c->coll == LB_LEARNED_MRT && c->net.empty()) return fail(LB_ERR_STATE, "network not set");
+    DeviceGuard guard(c->device);
+    if (c->opt.record_every > 0 && !c->recording && n > 0)
+        if ((s = record_begin(c)) != LB_OK) return s;
+    for (int64_t t = 0; t < n; ++t) {
+        if ((s = step_once(c)) != LB_OK) return s;
+        if (c->opt.check_every > 0 && (t + 1) % c->opt.check_every == 0)
+            if ((s = lb_check(c)) != LB_OK) return s;
+    }
+    if (c->opt.check_every > 0 && n % c->opt.check_every != 0) return lb_check(c);
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_ctx* c, void* rho, void* u, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
+    if (!rho && !u) return LB_OK;
+    DeviceGuard guard(c->device);
+    Staged sr, su;
+    if (rho && (s = stage_out_alloc(c, sr, rho, c->N, m, false, "rho")) != LB_OK) return s;
+    if (u && (s = stage_out_alloc(c, su, u, c->N * c->D, m, false, "u")) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_MOMENTS);
+    a.out0 = rho ? sr.dev : nullptr;
+    a.out1 = u ? su.dev : nullptr;
+    a.io_f64 = mem_f64(m);
+    if ((s = launch(c, a, "moments")) != LB_OK) return s;
+    if (rho && (s = stage_out_finish(c, sr, rho, "rho")) != LB_OK) return s;
+    if (u && (s = stage_out_finish(c, su, u, "u")) != LB_OK) return s;
+    return LB_OK;
+}
+
+lb_status lb_reduce(lb_ctx* c, double out[6])
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!out) return fail(LB_ERR_ARG, "out is null");
+    DeviceGuard guard(c->device);
+    const int64_t nb = lb::node_grid_blocks(c->g);
+    if ((s = ensure_partials(c, 6 * nb)) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_REDUCE_PARTIAL);
+    a.partials = c->partials;
+    if ((s = launch(c, a, "reduce")) != LB_OK) return s;
+    LB_CUDA(c, lb::reduce_final(c->partials, nb, 6, c->dsmall, c->stream), "reduce final");
+    c->launches += 1;
+    double h[6];
+    LB_CUDA(c, cudaMemcpyAsync(h, c->dsmall, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "reduce read");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "reduce sync");
+    const double invN = 1.0 / (double)c->N;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = h[3];
+    out[4] = 0.5 * h[4] * invN;
+    out[5] = 0.5 * h[5] * invN;
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx* c, void* f, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!f || !mem_valid(m)) return fail(LB_ERR_ARG, "f and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged sf;
+    if ((s = stage_out_alloc(c, sf, f, c->N * c->Q, m, false, "populations")) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_GET);
+    a.out0 = sf.dev;
+    a.io_f64 = mem_f64(m);
+    if ((s = launch(c, a, "get populations")) != LB_OK) return s;
+    return stage_out_finish(c, sf, f, "populations");
+}
+
+lb_status lb_set_populations(lb_ctx* c, const void* f, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!f || !mem_valid(m)) return fail(LB_ERR_ARG, "f and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged sf;
+    if ((s = stage_in(c, sf, f, c->N * c->Q, m, "populations")) != LB_OK) return s;
+    c->aa_parity = 0;
+    c->state = c->ab[0];
+    lb::OpArgs a = base_args(c, lb::OP_SET);
+    a.dst = c->state;
+    a.in0 = sf.dev;
+    a.io_f64 = mem_f64(m);
+    if ((s = launch(c, a, "set populations")) != LB_OK) return s;
+    reset_recording(c);
+    return LB_OK;
+}
+
+int64_t lb_steps_taken(const lb_ctx* c) { return c ? c->steps : -1; }
+
+lb_status lb_adjoint_seed_moments(lb_ctx* c, const void* grho, const void* gu, void* lam, void* gF, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!gu || !lam || !mem_valid(m)) return fail(LB_ERR_ARG, "grad_u, lambda and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged sr, su, sl, sg;
+    if (grho && (s = stage_in(c, sr, grho, c->N, m, "grad_rho")) != LB_OK) return s;
+    if ((s = stage_in(c, su, gu, c->N * c->D, m, "grad_u")) != LB_OK) return s;
+    if ((s = stage_out_alloc(c, sl, lam, c->N * c->Q, m, false, "lambda")) != LB_OK) return s;
+    const bool want_gF = gF && c->F;
+    if (want_gF && (s = stage_out_alloc(c, sg, gF, c->N * c->D, m, true, "grad_F")) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_ADJ_SEED);
+    a.in0 = grho ? sr.dev : nullptr;
+    a.in1 = su.dev;
+    a.out0 = sl.dev;
+    a.out1 = want_gF ? sg.dev : nullptr;
+    a.io_f64 = mem_f64(m);
+    if ((s = launch(c, a, "adjoint seed")) != LB_OK) return s;
+    if ((s = stage_out_finish(c, sl, lam, "lambda")) != LB_OK) return s;
+    if (want_gF && (s = stage_out_finish(c, sg, gF, "grad_F")) != LB_OK) return s;
+    return LB_OK;
+}
+
+lb_status lb_loss_energy(lb_ctx* c, const void* et, double* loss, void* lam, void* gF, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!et || !loss || !mem_valid(m)) return fail(LB_ERR_ARG, "e_target, loss and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged se, sl, sg;
+    if ((s = stage_in(c, se, et, c->N, m, "e_target")) != LB_OK) return s;
+    if (lam && (s = stage_out_alloc(c, sl, lam, c->N * c->Q, m, false, "lambda")) != LB_OK) return s;
+    const bool want_gF = gF && c->F;
+    if (want_gF && (s = stage_out_alloc(c, sg, gF, c->N * c->D, m, true, "grad_F")) != LB_OK) return s;
+    const int64_t nb = lb::node_grid_blocks(c->g);
+    if ((s = ensure_partials(c, nb)) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_LOSS_ENERGY);
+    a.in0 = se.dev;
+    a.out0 = lam ? sl.dev : nullptr;
+    a.out1 = want_gF ? sg.dev : nullptr;
+    a.io_f64 = mem_f64(m);
+    a.partials = c->partials;
+    if ((s = launch(c, a, "energy loss")) != LB_OK) return s;
+    LB_CUDA(c, lb::reduce_final(c->partials, nb, 1, c->dsmall, c->stream), "loss reduce");
+    c->launches += 1;
+    LB_CUDA(c, cudaMemcpyAsync(loss, c->dsmall, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss read");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "loss sync");
+    if (lam && (s = stage_out_finish(c, sl, lam, "lambda")) != LB_OK) return s;
+    if (want_gF && (s = stage_out_finish(c, sg, gF, "grad_F")) != LB_OK) return s;
+    return LB_OK;
+}
+
+lb_status lb_loss_eq6(lb_ctx* c, const void* uref, const void* wref, double Eref, double* loss, void* lam, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (c->stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "the Eq. 6 loss is defined for D2Q9");
+    if (c->F) return fail(LB_ERR_UNSUPPORTED, "the Eq. 6 loss takes no force");
+    if (!uref || !wref || !loss || !mem_valid(m)) return fail(LB_ERR_ARG, "u_ref, w_ref, loss and lb_mem required");
+    DeviceGuard guard(c->device);
+    Staged su, sw, sl;
+    if ((s = stage_in(c, su, uref, 2 * c->N, m, "u_ref")) != LB_OK) return s;
+    if ((s = stage_in(c, sw, wref, c->N, m, "w_ref")) != LB_OK) return s;
+    if (lam && (s = stage_out_alloc(c, sl, lam, c->N * c->Q, m, false, "lambda")) != LB_OK) return s;
+    const int64_t nb = lb::node_grid_blocks(c->g);
+    if ((s = ensure_partials(c, 3 * nb + 8)) != LB_OK) return s;
+    lb::LossEq6Args e;
+    e.a = base_args(c, lb::OP_LOSS_ENERGY);
+    e.uref = su.dev;
+    e.wref = sw.dev;
+    e.Eref = Eref;
+    e.lam = lam ? sl.dev : nullptr;
+    e.io_f64 = mem_f64(m);
+    e.partials = c->partials;
+    e.result = c->dsmall;
+    e.N = c->N;
+    Staged scr;
+    scr.c = c;
+    if (cudaMallocAsync(&scr.tmp, (size_t)(3 * c->plane * real_bytes(c->opt.storage)), c->stream) != cudaSuccess) {
+        scr.tmp = nullptr;
+        cudaGetLastError();
+        return fail(LB_ERR_OOM, "Eq. 6 scratch");
+    }
+    e.scratch = scr.tmp;
+    int launches = 0;
+    cudaError_t ce = lb::loss_eq6_d2q9(e, &launches);
+    c->launches += launches;
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "Eq. 6 loss");
+    LB_CUDA(c, cudaMemcpyAsync(loss, c->dsmall, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss read");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "loss sync");
+    if (lam && (s = stage_out_finish(c, sl, lam, "lambda")) != LB_OK) return s;
+    return LB_OK;
+}
+
+lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, void* gFout, void* gth, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!lamT || !mem_valid(m)) return fail(LB_ERR_ARG, "lambda_T and a valid lb_mem are required");
+    const int k = c->opt.record_every;
+    if (k <= 0) return fail(LB_ERR_STATE, "context was created with record_every = 0");
+    if (n != c->steps) return fail(LB_ERR_STATE, "n = %lld but %lld steps were recorded", (long long)n, (long long)c->steps);
+    if (n > 0 && !c->recording) return fail(LB_ERR_STATE, "no recorded run");
+    if (gth && c->coll != LB_LEARNED_MRT) return fail(LB_ERR_ARG, "grad_theta needs the learned collision");
+    DeviceGuard guard(c->device);
+    const int f64 = c->opt.storage == LB_F64;
+    const int64_t rb = real_pop_bytes(c);
+    for (int b = 0; b < 2; ++b)
+        if (!c->lam[b] && (s = alloc(c, &c->lam[b], rb, "adjoint buffer")) != LB_OK) return s;
+    const int64_t gFb = (int64_t)c->D * c->plane * real_bytes(c->opt.storage);
+    if (c->F && !c->gF && (s = alloc(c, &c->gF, gFb, "force gradient")) != LB_OK) return s;
+    while ((int64_t)c->ring.size() < k - 1) {
+        void* p = nullptr;
+        if ((s = alloc(c, &p, pop_bytes(c), "recompute buffer")) != LB_OK) return s;
+        c->ring.push_back(p);
+    }
+    int64_t nblk = 0;
+    if (c->coll == LB_LEARNED_MRT) {
+        nblk = lb::learned_adj_partial_count(c->g);
+        const int64_t need = nblk * 793;
+        if (c->gtheta_cap < need) {
+            if (c->gtheta) cudaFree(c->gtheta);
+            c->gtheta = nullptr;
+            c->gtheta_cap = 0;
+            if ((s = alloc(c, &c->gtheta, need * real_bytes(c->opt.storage), "parameter gradient")) != LB_OK) return s;
+            c->gtheta_cap = need;
+        }
+        LB_CUDA(c, cudaMemsetAsync(c->gtheta, 0, (size_t)(need * real_bytes(c->opt.storage)), c->stream), "gtheta clear");
+    }
+    // lambda^n from the caller
+    Staged sl;
+    if ((s = stage_in(c, sl, lamT, c->N * c->Q, m, "lambda_T")) != LB_OK) return s;
+    LB_CUDA(c, lb::convert_copy(sl.dev, mem_f64(m), c->lam[0], f64, c->N, c->N, c->plane, c->Q, 0, c->stream),
+            "lambda_T copy");
+    c->launches += 1;
+    if (c->gF) LB_CUDA(c, cudaMemsetAsync(c->gF, 0, (size_t)gFb, c->stream), "gF clear");
+    int cur = 0;
+    const int64_t nseg = (n + k - 1) / k;
+    std::vector<void*> states((size_t)k);
+    for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+        const int64_t start = seg * k;
+        const int64_t L = (n - start < k) ? n - start : k;
+        states[0] = c->ckpt[(size_t)seg];
+        for (int64_t j = 1; j < L; ++j) {
+            lb::OpArgs a = base_args(c, lb::OP_UPDATE);
+            a.mode = lb::AB;
+            a.src = states[(size_t)(j - 1)];
+            a.dst = c->ring[(size_t)(j - 1)];
+            if ((s = launch(c, a, "recompute")) != LB_OK) return s;
+            states[(size_t)j] = c->ring[(size_t)(j - 1)];
+        }
+        for (int64_t j = L - 1; j >= 0; --j) {
+            lb::OpArgs a = base_args(c, lb::OP_ADJ_STEP);
+            a.mode = lb::AB;
+            a.src = states[(size_t)j];
+            a.lam_in = c->lam[cur];
+            a.lam_out = c->lam[1 - cur];
+            a.gF = c->gF;
+            a.gth = c->gtheta;
+            if ((s = launch(c, a, "adjoint step")) != LB_OK) return s;
+            cur = 1 - cur;
+        }
+    }
+    if (lam0) {
+        Staged so;
+        if ((s = stage_out_alloc(c, so, lam0, c->N * c->Q, m, false, "lambda_0")) != LB_OK) return s;
+        LB_CUDA(c, lb::convert_copy(c->lam[cur], f64, so.dev, mem_f64(m), c->N, c->plane, c->N, c->Q, 0, c->stream),
+                "lambda_0 copy");
+        c->launches += 1;
+        if ((s = stage_out_finish(c, so, lam0, "lambda_0")) != LB_OK) return s;
+    }
+    if (gFout && c->gF) {
+        Staged so;
+        if ((s = stage_out_alloc(c, so, gFout, c->N * c->D, m, true, "grad_F")) != LB_OK) return s;
+        LB_CUDA(c, lb::convert_copy(c->gF, f64, so.dev, mem_f64(m), c->N, c->plane, c->N, c->D, 1, c->stream),
+                "grad_F copy");
+        c->launches += 1;
+        if ((s = stage_out_finish(c, so, gFout, "grad_F")) != LB_OK) return s;
+    }
+    if (gth) {
+        Staged so;
+        if ((s = stage_out_alloc(c, so, gth, 793, m, true, "grad_theta")) != LB_OK) return s;
+        LB_CUDA(c, lb::learned_reduce_theta(c->gtheta, nblk, f64, so.dev, mem_f64(m), c->stream), "grad_theta");
+        c->launches += 1;
+        if ((s = stage_out_finish(c, so, gth, "grad_theta")) != LB_OK) return s;
+    }
+    return LB_OK;
+}
+
+lb_status lb_adam_update(float* theta, float* mm, float* v, const float* g, int64_t n, double lr, double b1, double b2,
+                         double eps, int64_t t, void* stream)
+{
+    if (!theta || !mm || !v || !g || n < 0 || t < 1) return fail(LB_ERR_ARG, "bad Adam arguments");
+    const double c1 = 1.0 - std::pow(b1, (double)t), c2 = 1.0 - std::pow(b2, (double)t);
+    cudaError_t e = lb::adam_update(theta, mm, v, g, n, (float)lr, (float)b1, (float)b2, (float)eps, (float)c1,
+                                    (float)c2, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, "adam: %s", cudaGetErrorString(e));
+    return LB_OK;
+}
+
+int64_t lb_num_nodes(const lb_ctx* c) { return c ? c->N : -1; }
+int lb_q(const lb_ctx* c) { return c ? c->Q : -1; }
+int lb_d(const lb_ctx* c) { return c ? c->D : -1; }
+int64_t lb_launch_count(const lb_ctx* c) { return c ? c->launches : -1; }
+
+const char* lb_status_string(lb_status s)
+{
+    switch (s) {
+    case LB_OK: return "ok";
+    case LB_ERR_ARG: return "invalid argument";
+    case LB_ERR_OOM: return "out of device memory";
+    case LB_ERR_CUDA: return "CUDA error";
+    case LB_ERR_UNSTABLE: return "unstable (non-finite or non-positive density)";
+    case LB_ERR_STATE: return "invalid state";
+    case LB_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char* lb_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Device-side building blocks of liblb: velocity sets, storage conversion, and
+// the per-node load/store patterns of the two-buffer (AB) and in-place (AA)
+// layouts. Everything here is header-only and force-inlined into the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#define LB_DEV __device__ __forceinline__
+#define LB_HD __host__ __device__ __forceinline__
+
+namespace lb {
+
+// ----------------------------------------------------------------------------
+// Velocity sets (Sec. 2.2, 3.1, 3.3 name D2Q9, D3Q19, D3Q27; the tables are the
+// textbook ones). Order: rest, +/- axis pairs, +/- edge pairs (xy, xz, yz), +/-
+// corner pairs. D3Q19 is the first 19 entries of the D3Q27 table.
+// ----------------------------------------------------------------------------
+LB_HD constexpr int c3(int i, int a)
+{
+    constexpr int t[27][3] = {
+        {0, 0, 0},
+        {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+        {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+        {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+        {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1},
+        {1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1},
+        {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+    return t[i][a];
+}
+
+LB_HD constexpr int c2(int i, int a)
+{
+    constexpr int t[9][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+    return a < 2 ? t[i][a] : 0;
+}
+
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, ID = 0;
+    LB_HD static constexpr int c(int i, int a) { return c2(i, a); }
+    LB_HD static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+};
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, ID = 1;
+    LB_HD static constexpr int c(int i, int a) { return c3(i, a); }
+    LB_HD static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+};
+struct D3Q27 {
+    static constexpr int Q = 27, D = 3, ID = 2;
+    LB_HD static constexpr int c(int i, int a) { return c3(i, a); }
+    LB_HD static constexpr double w(int i)
+    {
+        return i == 0 ? 8.0 / 27.0 : (i < 7 ? 2.0 / 27.0 : (i < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+    }
+};
+
+// opposite direction: pairs are stored next to each other after the rest velocity
+LB_HD constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ----------------------------------------------------------------------------
+// Storage types. Real is the arithmetic type (FP64 only for FP64 storage).
+// Half types hold f_i - w_i.
+// ----------------------------------------------------------------------------
+template <class T> struct Store;
+template <> struct Store<double> {
+    using Real = double;
+    static constexpr bool shifted = false;
+    LB_DEV static double load(const double* p) { return *p; }
+    LB_DEV static void store(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    using Real = float;
+    static constexpr bool shifted = false;
+    LB_DEV static float load(const float* p) { return *p; }
+    LB_DEV static void store(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    using Real = float;
+    static constexpr bool shifted = true;
+    LB_DEV static float load(const __half* p) { return __half2float(*p); }
+    LB_DEV static void store(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using Real = float;
+    static constexpr bool shifted = true;
+    LB_DEV static float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    LB_DEV static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+template <class St, class T>
+LB_DEV typename Store<T>::Real load_pop(const T* p, int i)
+{
+    using R = typename Store<T>::Real;
+    R v = Store<T>::load(p);
+    if constexpr (Store<T>::shifted) v += R(St::w(i));
+    return v;
+}
+
+template <class St, class T>
+LB_DEV void store_pop(T* p, int i, typename Store<T>::Real v)
+{
+    using R = typename Store<T>::Real;
+    if constexpr (Store<T>::shifted) v -= R(St::w(i));
+    Store<T>::store(p, v);
+}
+
+// ----------------------------------------------------------------------------
+// Grid geometry and periodic neighbours of one node.
+// ----------------------------------------------------------------------------
+struct Geom {
+    int nx, ny, nz;
+    int64_t plane;  // element stride between population planes (>= N, padded)
+};
+
+// Node coordinates and the wrapped +/-1 neighbours along each axis.
+struct Nbr {
+    int x[3], y[3], z[3];  // index 0: coordinate - 1, 1: coordinate, 2: coordinate + 1 (wrapped)
+    LB_DEV int node(const Geom& g, int dx, int dy, int dz) const
+    {
+        return x[dx + 1] + g.nx * (y[dy + 1] + g.ny * z[dz + 1]);
+    }
+};
+
+LB_DEV Nbr make_nbr(const Geom& g, int x, int y, int z)
+{
+    Nbr n;
+    n.x[0] = x == 0 ? g.nx - 1 : x - 1; n.x[1] = x; n.x[2] = x == g.nx - 1 ? 0 : x + 1;
+    n.y[0] = y == 0 ? g.ny - 1 : y - 1; n.y[1] = y; n.y[2] = y == g.ny - 1 ? 0 : y + 1;
+    n.z[0] = z == 0 ? g.nz - 1 : z - 1; n.z[1] = z; n.z[2] = z == g.nz - 1 ? 0 : z + 1;
+    return n;
+}
+
+// ----------------------------------------------------------------------------
+// Access modes. The buffer content per mode, for the pre-collision state f^n:
+//   AB      : buf_i(x) = f*_i(x) of the previous step, so f^n_i(x) = buf_i(x - c_i)
+//             (pull). The next state is written unshifted: out_i(x) = f*_i(x).
+//   AA_EVEN : buf_i(x) = f^n_i(x) (natural). Collide writes f*_i(x) into slot opp(i)
+//             of the same node.
+//   AA_ODD  : slot opp(i) of x holds f*_i(x) of the previous step, so
+//             f^n_i(x) = buf_opp(i)(x - c_i). Collide writes f*_i(x) to slot i of
+//             x + c_i, which is the natural layout of the next state.
+// ----------------------------------------------------------------------------
+enum Mode { AB = 0, AA_EVEN = 1, AA_ODD = 2 };
+
+template <class St, int MODE, class T>
+LB_DEV void load_node(const T* buf, const Geom& g, const Nbr& nb, int n, typename Store<T>::Real* f)
+{
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        int src;
+        int slot = i;
+        if constexpr (MODE == AA_EVEN) {
+            src = n;
+        } else {
+            src = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
+            if constexpr (MODE == AA_ODD) slot = opp(i);
+        }
+        f[i] = load_pop<St>(buf + (int64_t)slot * g.plane + src, slot);
+    }
+}
+
+template <class St, int MODE, class T>
+LB_DEV void store_node(T* buf, const Geom& g, const Nbr& nb, int n, const typename Store<T>::Real* f)
+{
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        int dst = n;
+        int slot = i;
+        if constexpr (MODE == AA_EVEN) slot = opp(i);
+        if constexpr (MODE == AA_ODD) dst = nb.node(g, St::c(i, 0), St::c(i, 1), St::c(i, 2));
+        store_pop<St>(buf + (int64_t)slot * g.plane + dst, slot, f[i]);
+    }
+}
+
+}  // namespace lb

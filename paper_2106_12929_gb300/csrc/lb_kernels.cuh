@@ -1,0 +1,406 @@
+// Node kernels of liblb, templated on the velocity set and instantiated once per
+// set in fwd_<stencil>.cu. One thread owns one node; blocks tile x-rows; each
+// population plane is contiguous (structure of arrays, x fastest), so every
+// load and store of a warp touches 32 consecutive elements of one plane.
+#pragma once
+
+#include "lb_adjoint.cuh"
+#include "lb_collide.cuh"
+#include "lb_ops.cuh"
+
+namespace lb {
+
+template <class O> LB_DEV O to_io(double v) { return (O)v; }
+
+LB_DEV double io_load(const void* p, int f64, int64_t k)
+{
+    return f64 ? ((const double*)p)[k] : (double)((const float*)p)[k];
+}
+LB_DEV void io_store(void* p, int f64, int64_t k, double v)
+{
+    if (f64) ((double*)p)[k] = v;
+    else ((float*)p)[k] = (float)v;
+}
+LB_DEV void io_add(void* p, int f64, int64_t k, double v)
+{
+    if (f64) ((double*)p)[k] += v;
+    else ((float*)p)[k] += (float)v;
+}
+
+struct NodeIdx {
+    int x, y, z, n;
+    bool valid;
+};
+
+LB_DEV NodeIdx node_index(const Geom& g)
+{
+    NodeIdx r;
+    r.x = blockIdx.x * blockDim.x + threadIdx.x;
+    r.y = blockIdx.y;
+    r.z = blockIdx.z;
+    r.valid = r.x < g.nx;
+    r.n = r.x + g.nx * (r.y + g.ny * r.z);
+    return r;
+}
+
+template <class St, class R>
+LB_DEV void load_force(const R* F, const Geom& g, int n, R* Fl)
+{
+    Fl[0] = F[n];
+    Fl[1] = F[g.plane + n];
+    Fl[2] = St::D == 3 ? F[2 * g.plane + n] : R(0);
+}
+
+// ------------------------------------------------------------------ step (K1/K2)
+template <class St, class T, int COLL, bool FORCE, int MODE>
+__global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
+                                                typename Store<T>::Real omega, unsigned* status)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    R f[St::Q];
+    load_node<St, MODE>(src, g, nb, id.n, f);
+    R Fl[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+    bool ok = collide<St, COLL, FORCE>(f, Fl, omega);
+    store_node<St, MODE>(dst, g, nb, id.n, f);
+    if (!ok) atomicOr(status, 1u);
+}
+
+// Write a natural-layout state value set into the buffer for the given mode:
+// AB keeps f*_i(x) at x (the next pull reads it from x + c_i), so the state
+// f_i(x) goes to x - c_i; AA (even parity) stores it in place.
+template <class St, int MODE, class T>
+LB_DEV void store_state(T* buf, const Geom& g, const Nbr& nb, int n, const typename Store<T>::Real* f)
+{
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        int dst = n;
+        if constexpr (MODE == AB) dst = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
+        store_pop<St>(buf + (int64_t)i * g.plane + dst, i, f[i]);
+    }
+}
+
+// ------------------------------------------------------------------ init (K5)
+template <class St, class T, int MODE>
+__global__ void __launch_bounds__(128) k_init_eq(T* buf, Geom g, const void* rho, const void* u, int f64)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    NodeMoments<St, R> m;
+    m.rho = (R)io_load(rho, f64, id.n);
+    m.ux = (R)io_load(u, f64, id.n);
+    m.uy = (R)io_load(u, f64, N + id.n);
+    m.uz = St::D == 3 ? (R)io_load(u, f64, 2 * N + id.n) : R(0);
+    R f[St::Q];
+    equilibrium<St>(m, f);
+    store_state<St, MODE>(buf, g, nb, id.n, f);
+}
+
+// ------------------------------------------------------------------ set / get (K11)
+template <class St, class T, int MODE>
+__global__ void __launch_bounds__(128) k_set(T* buf, Geom g, const void* fin, int f64)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    R f[St::Q];
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) f[i] = (R)io_load(fin, f64, (int64_t)i * N + id.n);
+    store_state<St, MODE>(buf, g, nb, id.n, f);
+}
+
+template <class St, class T, int MODE>
+__global__ void __launch_bounds__(128) k_get(const T* buf, Geom g, void* fout, int f64)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    R f[St::Q];
+    load_node<St, MODE>(buf, g, nb, id.n, f);
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) io_store(fout, f64, (int64_t)i * N + id.n, (double)f[i]);
+}
+
+// ------------------------------------------------------------------ moments (K3)
+template <class St, class T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(128) k_moments(const T* buf, const typename Store<T>::Real* F, Geom g,
+                                                 void* rho, void* u, int f64)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    R f[St::Q];
+    load_node<St, MODE>(buf, g, nb, id.n, f);
+    R Fl[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+    NodeMoments<St, R> m = node_moments<St, FORCE>(f, Fl);
+    if (rho) io_store(rho, f64, id.n, (double)m.rho);
+    if (u) {
+        io_store(u, f64, id.n, (double)m.ux);
+        io_store(u, f64, N + id.n, (double)m.uy);
+        if (St::D == 3) io_store(u, f64, 2 * N + id.n, (double)m.uz);
+    }
+}
+
+// ------------------------------------------------------------------ global sums (K4, pass 1)
+// Each block writes the FP64 sums of its nodes in a fixed tree order; pass 2
+// (reduce_final) adds the block partials in block order, so results are
+// deterministic for a given grid.
+template <int W>
+LB_DEV void block_sum_store(double (&v)[W], double* out)
+{
+    __shared__ double sh[W][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0) sh[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            out[k] = s;
+        }
+    }
+}
+
+template <class St, class T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(128) k_reduce_partial(const T* buf, const typename Store<T>::Real* F, Geom g,
+                                                        double* partials)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (id.valid) {
+        Nbr nb = make_nbr(g, id.x, id.y, id.z);
+        R f[St::Q];
+        load_node<St, MODE>(buf, g, nb, id.n, f);
+        R Fl[3] = {R(0), R(0), R(0)};
+        if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+        NodeMoments<St, R> m = node_moments<St, FORCE>(f, Fl);
+        const double r = m.rho, ux = m.ux, uy = m.uy, uz = m.uz;
+        const double uu = ux * ux + uy * uy + uz * uz;
+        v[0] = r;
+        v[1] = r * ux;
+        v[2] = r * uy;
+        v[3] = r * uz;
+        v[4] = uu;
+        v[5] = r * uu;
+    }
+    const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_sum_store<6>(v, partials + 6 * b);
+}
+
+// ------------------------------------------------------------------ adjoint seeds (K7)
+template <class St, class T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(128) k_adj_seed(const T* buf, const typename Store<T>::Real* F, Geom g,
+                                                  const void* grho, const void* gu, void* lam, void* gF, int f64)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    R f[St::Q];
+    load_node<St, MODE>(buf, g, nb, id.n, f);
+    R Fl[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+    NodeMoments<St, R> m = node_moments<St, FORCE>(f, Fl);
+    const R gr = grho ? (R)io_load(grho, f64, id.n) : R(0);
+    const R gx = (R)io_load(gu, f64, id.n), gy = (R)io_load(gu, f64, N + id.n);
+    const R gz = St::D == 3 ? (R)io_load(gu, f64, 2 * N + id.n) : R(0);
+    const R inv = R(1) / m.rho;
+    const R gdotu = gx * m.ux + gy * m.uy + gz * m.uz;
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        // dL/df_i = dL/drho + dL/du . (c_i - u) / rho
+        R v = gr + (cdotu<St>(i, gx, gy, gz) - gdotu) * inv;
+        io_store(lam, f64, (int64_t)i * N + id.n, (double)v);
+    }
+    if (FORCE && gF) {
+        io_add(gF, f64, id.n, (double)(R(0.5) * gx * inv));
+        io_add(gF, f64, N + id.n, (double)(R(0.5) * gy * inv));
+        if (St::D == 3) io_add(gF, f64, 2 * N + id.n, (double)(R(0.5) * gz * inv));
+    }
+}
+
+// energy-field loss L = sum (rho |u|^2 / 2 - e*)^2: seed and per-block partial sums of L
+template <class St, class T, int MODE, bool FORCE>
+__global__ void __launch_bounds__(128) k_loss_energy(const T* buf, const typename Store<T>::Real* F, Geom g,
+                                                     const void* etarget, void* lam, void* gF, int f64,
+                                                     double* partials)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    double v[1] = {0.0};
+    if (id.valid) {
+        Nbr nb = make_nbr(g, id.x, id.y, id.z);
+        const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+        R f[St::Q];
+        load_node<St, MODE>(buf, g, nb, id.n, f);
+        R Fl[3] = {R(0), R(0), R(0)};
+        if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+        NodeMoments<St, R> m = node_moments<St, FORCE>(f, Fl);
+        const R uu = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+        const R diff = R(0.5) * m.rho * uu - (R)io_load(etarget, f64, id.n);
+        v[0] = (double)diff * (double)diff;
+        // dL/drho at fixed u = diff |u|^2, dL/du = 2 diff rho u
+        const R gr = diff * uu;
+        const R gx = R(2) * diff * m.rho * m.ux, gy = R(2) * diff * m.rho * m.uy, gz = R(2) * diff * m.rho * m.uz;
+        const R inv = R(1) / m.rho;
+        const R gdotu = gx * m.ux + gy * m.uy + gz * m.uz;
+        if (lam) {
+#pragma unroll
+            for (int i = 0; i < St::Q; ++i)
+                io_store(lam, f64, (int64_t)i * N + id.n, (double)(gr + (cdotu<St>(i, gx, gy, gz) - gdotu) * inv));
+        }
+        if (FORCE && gF) {
+            io_add(gF, f64, id.n, (double)(R(0.5) * gx * inv));
+            io_add(gF, f64, N + id.n, (double)(R(0.5) * gy * inv));
+            if (St::D == 3) io_add(gF, f64, 2 * N + id.n, (double)(R(0.5) * gz * inv));
+        }
+    }
+    const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    block_sum_store<1>(v, partials + b);
+}
+
+// ------------------------------------------------------------------ adjoint step (K6)
+// lambda^n(x) = J_C(f^n(x))^T mu(x), mu_i(x) = lambda^{n+1}_i(x + c_i); the state
+// buffer holds the previous step's post-collision values (AB layout), so f^n is
+// pulled exactly as the forward step pulls it.
+template <class St, class T, int COLL, bool FORCE>
+__global__ void __launch_bounds__(128) k_adj_step(const T* state, const typename Store<T>::Real* F,
+                                                  const typename Store<T>::Real* lam_in,
+                                                  typename Store<T>::Real* lam_out, typename Store<T>::Real* gF,
+                                                  Geom g, typename Store<T>::Real omega)
+{
+    using R = typename Store<T>::Real;
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    R f[St::Q], mu[St::Q];
+    load_node<St, AB>(state, g, nb, id.n, f);
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i)
+        mu[i] = lam_in[(int64_t)i * g.plane + nb.node(g, St::c(i, 0), St::c(i, 1), St::c(i, 2))];
+    R Fl[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
+    R gFl[3];
+    adjoint_node<St, COLL, FORCE>(f, Fl, mu, omega, gFl);
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) lam_out[(int64_t)i * g.plane + id.n] = mu[i];
+    if constexpr (FORCE) {
+        gF[id.n] += gFl[0];
+        gF[g.plane + id.n] += gFl[1];
+        if (St::D == 3) gF[2 * g.plane + id.n] += gFl[2];
+    }
+}
+
+// ------------------------------------------------------------------ dispatch
+template <class St, class T, int COLL, bool FORCE>
+cudaError_t launch_update(const OpArgs& a)
+{
+    using R = typename Store<T>::Real;
+    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
+    const T* src = (const T*)a.src;
+    T* dst = (T*)a.dst;
+    const R* F = (const R*)a.F;
+    if (a.mode == AB) k_update<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+    else if (a.mode == AA_EVEN)
+        k_update<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+    else k_update<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+    return cudaGetLastError();
+}
+
+template <class St, class T, int MODE, bool FORCE>
+cudaError_t launch_state_op(const OpArgs& a)
+{
+    using R = typename Store<T>::Real;
+    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
+    const R* F = (const R*)a.F;
+    switch (a.op) {
+    case OP_INIT_EQ:
+        if (MODE == AA_ODD) return cudaErrorInvalidValue;
+        k_init_eq<St, T, MODE><<<gr, bl, 0, a.stream>>>((T*)a.dst, a.g, a.in0, a.in1, a.io_f64);
+        break;
+    case OP_SET:
+        if (MODE == AA_ODD) return cudaErrorInvalidValue;
+        k_set<St, T, MODE><<<gr, bl, 0, a.stream>>>((T*)a.dst, a.g, a.in0, a.io_f64);
+        break;
+    case OP_GET: k_get<St, T, MODE><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.out0, a.io_f64); break;
+    case OP_MOMENTS:
+        k_moments<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.out0, a.out1, a.io_f64);
+        break;
+    case OP_REDUCE_PARTIAL:
+        k_reduce_partial<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.partials);
+        break;
+    case OP_ADJ_SEED:
+        k_adj_seed<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.in0, a.in1, a.out0,
+                                                                a.out1, a.io_f64);
+        break;
+    case OP_LOSS_ENERGY:
+        k_loss_energy<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.in0, a.out0, a.out1,
+                                                                   a.io_f64, a.partials);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class St, class T, int COLL>
+cudaError_t launch_adj(const OpArgs& a)
+{
+    using R = typename Store<T>::Real;
+    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
+    if (a.force)
+        k_adj_step<St, T, COLL, true><<<gr, bl, 0, a.stream>>>((const T*)a.src, (const R*)a.F, (const R*)a.lam_in,
+                                                               (R*)a.lam_out, (R*)a.gF, a.g, (R)a.omega);
+    else
+        k_adj_step<St, T, COLL, false><<<gr, bl, 0, a.stream>>>((const T*)a.src, nullptr, (const R*)a.lam_in,
+                                                                (R*)a.lam_out, nullptr, a.g, (R)a.omega);
+    return cudaGetLastError();
+}
+
+template <class St, class T>
+cudaError_t run_op_typed(const OpArgs& a)
+{
+    if (a.op == OP_UPDATE) {
+        switch (a.coll) {
+        case BGK: return a.force ? launch_update<St, T, BGK, true>(a) : launch_update<St, T, BGK, false>(a);
+        case REG: return a.force ? launch_update<St, T, REG, true>(a) : launch_update<St, T, REG, false>(a);
+        case NONE: return launch_update<St, T, NONE, false>(a);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (a.op == OP_ADJ_STEP) {
+        switch (a.coll) {
+        case BGK: return launch_adj<St, T, BGK>(a);
+        case REG: return launch_adj<St, T, REG>(a);
+        case NONE: return launch_adj<St, T, NONE>(a);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (a.mode == AB) return a.force ? launch_state_op<St, T, AB, true>(a) : launch_state_op<St, T, AB, false>(a);
+    if (a.mode == AA_EVEN)
+        return a.force ? launch_state_op<St, T, AA_EVEN, true>(a) : launch_state_op<St, T, AA_EVEN, false>(a);
+    return a.force ? launch_state_op<St, T, AA_ODD, true>(a) : launch_state_op<St, T, AA_ODD, false>(a);
+}
+
+}  // namespace lb

@@ -1,0 +1,554 @@
+// Learned moment-space collision on D2Q9 (Eq. 5, Sec. 3.1), its discrete adjoint
+// with the network-parameter gradient, and the Eq. 6 training loss.
+//
+// Moment basis (Hermite, orthogonal under the weights w_i): 1, cx, cy,
+// cx^2 - 1/3, cx cy, cy^2 - 1/3 (stress rows), (cx^2 - 1/3) cy, cx (cy^2 - 1/3),
+// (cx^2 - 1/3)(cy^2 - 1/3) (higher rows; their equilibria vanish for the
+// second-order f^eq). With d = f - f^eq, Pi = sum c c d and the higher moments
+// g = sum H d, the collision is
+//   f*_i = f^eq_i + (1 - w_s) 4.5 w_i (c_i c_i - I/3) : Pi
+//                 + (1 - w_g) w_i sum_g H_g(c_i) g_g / |H_g|^2_w,
+// w_s = 1/tau (stress rows), w_g = 1/(exp(z) + 1/2) from the per-node network
+// z = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 of the standardised invariants
+// x_k = (I_k - shift_k) scale_k:
+//   I1 = rho - 1, I2 = 3|u|^2, I3 = 3 tr Pi, I4 = 9 Pi:Pi, I5 = 9 u.Pi.u,
+//   I6 = sum_g g_g^2 / |H_g|^2_w.
+// The network's 805 values travel as a by-value kernel parameter, so they live in
+// the constant bank and feed the FMAs directly.
+#include "lb_collide.cuh"
+#include "lb_learned.cuh"
+
+namespace lb {
+
+template <class R>
+struct Net {
+    R v[kNetValues];
+};
+
+// Hermite higher-moment polynomials on D2Q9 and their weighted norms
+LB_HD constexpr double h6(int i) { return (c2(i, 0) * c2(i, 0) - 1.0 / 3.0) * c2(i, 1); }
+LB_HD constexpr double h7(int i) { return c2(i, 0) * (c2(i, 1) * c2(i, 1) - 1.0 / 3.0); }
+LB_HD constexpr double h8(int i) { return (c2(i, 0) * c2(i, 0) - 1.0 / 3.0) * (c2(i, 1) * c2(i, 1) - 1.0 / 3.0); }
+constexpr double kN6 = 2.0 / 27.0, kN7 = 2.0 / 27.0, kN8 = 4.0 / 81.0;
+
+template <class R> LB_DEV R act_tanh(R a);
+template <> LB_DEV float act_tanh<float>(float a) { return tanhf(a); }
+template <> LB_DEV double act_tanh<double>(double a) { return tanh(a); }
+template <class R> LB_DEV R act_exp(R a);
+template <> LB_DEV float act_exp<float>(float a) { return expf(a); }
+template <> LB_DEV double act_exp<double>(double a) { return exp(a); }
+
+// Everything the forward pass of one node computes (kept for the adjoint).
+template <class R>
+struct LearnedNode {
+    NodeMoments<D2Q9, R> m;
+    R feq[9];
+    R pxx, pxy, pyy, g6, g7, g8;
+    R x[kNetIn];
+    R h1[kNetHidden], h2[kNetHidden];
+    R z, ez, omg;
+};
+
+template <class R>
+LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
+{
+    const R* W1 = net.v;
+    const R* b1 = W1 + kNetHidden * kNetIn;
+    const R* W2 = b1 + kNetHidden;
+    const R* b2 = W2 + kNetHidden * kNetHidden;
+    const R* W3 = b2 + kNetHidden;
+    const R* b3 = W3 + kNetHidden;
+    const R* shift = b3 + 1;
+    const R* scale = shift + kNetIn;
+    R Fz[3] = {R(0), R(0), R(0)};
+    s.m = node_moments<D2Q9, false>(f, Fz);
+    equilibrium<D2Q9>(s.m, s.feq);
+    R pxx = R(0), pxy = R(0), pyy = R(0), g6 = R(0), g7 = R(0), g8 = R(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R d = f[i] - s.feq[i];
+        const int cx = c2(i, 0), cy = c2(i, 1);
+        if (cx) pxx += d;
+        if (cy) pyy += d;
+        if (cx && cy) pxy += (cx == cy) ? d : -d;
+        g6 += R(h6(i)) * d;
+        g7 += R(h7(i)) * d;
+        g8 += R(h8(i)) * d;
+    }
+    s.pxx = pxx; s.pxy = pxy; s.pyy = pyy; s.g6 = g6; s.g7 = g7; s.g8 = g8;
+    const R ux = s.m.ux, uy = s.m.uy;
+    R I[kNetIn];
+    I[0] = s.m.rho - R(1);
+    I[1] = R(3) * (ux * ux + uy * uy);
+    I[2] = R(3) * (pxx + pyy);
+    I[3] = R(9) * (pxx * pxx + R(2) * pxy * pxy + pyy * pyy);
+    I[4] = R(9) * (ux * ux * pxx + R(2) * ux * uy * pxy + uy * uy * pyy);
+    I[5] = g6 * g6 * R(1.0 / kN6) + g7 * g7 * R(1.0 / kN7) + g8 * g8 * R(1.0 / kN8);
+#pragma unroll
+    for (int k = 0; k < kNetIn; ++k) s.x[k] = (I[k] - shift[k]) * scale[k];
+#pragma unroll
+    for (int j = 0; j < kNetHidden; ++j) {
+        R a = b1[j];
+#pragma unroll
+        for (int k = 0; k < kNetIn; ++k) a += W1[j * kNetIn + k] * s.x[k];
+        s.h1[j] = act_tanh(a);
+    }
+#pragma unroll
+    for (int j = 0; j < kNetHidden; ++j) {
+        R a = b2[j];
+#pragma unroll
+        for (int k = 0; k < kNetHidden; ++k) a += W2[j * kNetHidden + k] * s.h1[k];
+        s.h2[j] = act_tanh(a);
+    }
+    R z = b3[0];
+#pragma unroll
+    for (int k = 0; k < kNetHidden; ++k) z += W3[k] * s.h2[k];
+    s.z = z;
+    s.ez = act_exp(z);
+    s.omg = R(1) / (s.ez + R(0.5));
+}
+
+template <class R>
+LB_DEV void learned_post(const LearnedNode<R>& s, R omega, R* f)
+{
+    const R ks = R(4.5) * (R(1) - omega);
+    const R kg = R(1) - s.omg;
+    const R tr3 = (s.pxx + s.pyy) * R(1.0 / 3.0);
+    const R q6 = s.g6 * R(1.0 / kN6), q7 = s.g7 * R(1.0 / kN7), q8 = s.g8 * R(1.0 / kN8);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = c2(i, 0), cy = c2(i, 1);
+        R qp = -tr3;
+        if (cx) qp += s.pxx;
+        if (cy) qp += s.pyy;
+        if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
+        const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
+        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + kg * ghost);
+    }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_learned_update(const T* src, T* dst, Geom g, typename Store<T>::Real omega,
+                                                        unsigned* status, const Net<typename Store<T>::Real> net)
+{
+    using R = typename Store<T>::Real;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y;
+    Nbr nb = make_nbr(g, x, y, 0);
+    const int n = x + g.nx * y;
+    R f[9];
+    load_node<D2Q9, MODE>(src, g, nb, n, f);
+    LearnedNode<R> s;
+    learned_forward(f, net, s);
+    learned_post(s, omega, f);
+    store_node<D2Q9, MODE>(dst, g, nb, n, f);
+    if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
+}
+
+// ---------------------------------------------------------------- adjoint
+constexpr int kAdjBlock = 128;
+
+// shared-memory staging of the per-node backprop vectors of one block
+template <class R>
+struct AdjShared {
+    R ga1[kAdjBlock][kNetHidden + 1];
+    R ga2[kAdjBlock][kNetHidden + 1];
+    R h1[kAdjBlock][kNetHidden + 1];
+    R h2[kAdjBlock][kNetHidden + 1];
+    R x[kAdjBlock][kNetIn + 1];
+    R gz[kAdjBlock];
+};
+
+template <class T>
+__global__ void __launch_bounds__(kAdjBlock) k_learned_adjoint(const T* state, const typename Store<T>::Real* lam_in,
+                                                               typename Store<T>::Real* lam_out, Geom g,
+                                                               typename Store<T>::Real omega,
+                                                               typename Store<T>::Real* gth_partials,
+                                                               const Net<typename Store<T>::Real> net)
+{
+    using R = typename Store<T>::Real;
+    extern __shared__ unsigned char smem_raw[];
+    AdjShared<R>& sh = *reinterpret_cast<AdjShared<R>*>(smem_raw);
+    const int t = threadIdx.x;
+    const int x = blockIdx.x * blockDim.x + t;
+    const int y = blockIdx.y;
+    const bool valid = x < g.nx;
+    R gz = R(0);
+    R ga1[kNetHidden], ga2[kNetHidden];
+    LearnedNode<R> s;
+    if (valid) {
+        const R* W1 = net.v;
+        const R* W2 = W1 + kNetHidden * kNetIn + kNetHidden;
+        const R* W3 = W2 + kNetHidden * kNetHidden + kNetHidden;
+        const R* scale = W3 + kNetHidden + 1 + kNetIn;
+        Nbr nb = make_nbr(g, x, y, 0);
+        const int n = x + g.nx * y;
+        R f[9], mu[9];
+        load_node<D2Q9, AB>(state, g, nb, n, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nb.node(g, c2(i, 0), c2(i, 1), 0)];
+        learned_forward(f, net, s);
+        const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
+        // sums of mu w over the basis
+        R smw = R(0), smwcx = R(0), smwcy = R(0), smwcucx = R(0), smwcucy = R(0), grho = R(0);
+        R sxx = R(0), syy = R(0), sxy = R(0), s6 = R(0), s7 = R(0), s8 = R(0);
+        const R base = R(1) - R(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R mw = mu[i] * R(D2Q9::w(i));
+            const int cx = c2(i, 0), cy = c2(i, 1);
+            const R cu = cdotu<D2Q9>(i, ux, uy, R(0));
+            grho += mw * (base + cu * (R(3) + R(4.5) * cu));
+            smw += mw;
+            smwcx += cx * mw;
+            smwcy += cy * mw;
+            smwcucx += cx * mw * cu;
+            smwcucy += cy * mw * cu;
+            if (cx) sxx += mw;
+            if (cy) syy += mw;
+            if (cx && cy) sxy += (cx == cy) ? mw : -mw;
+            s6 += R(h6(i)) * mw;
+            s7 += R(h7(i)) * mw;
+            s8 += R(h8(i)) * mw;
+        }
+        // equilibrium path: d f^eq / d rho, d f^eq / d u
+        R gux = rho * (R(3) * smwcx + R(9) * smwcucx - R(3) * ux * smw);
+        R guy = rho * (R(3) * smwcy + R(9) * smwcucy - R(3) * uy * smw);
+        // stress path: cotangent of (Pxx, Pxy, Pyy) from 4.5 (1 - w_s) w_i Q_i : Pi
+        const R ks = R(4.5) * (R(1) - omega);
+        R gPxx = ks * (sxx - smw * R(1.0 / 3.0));
+        R gPyy = ks * (syy - smw * R(1.0 / 3.0));
+        R gPxy = R(2) * ks * sxy;
+        // higher moments: cotangent of g_g and of w_g
+        const R kg = R(1) - s.omg;
+        const R q6 = s6 * R(1.0 / kN6), q7 = s7 * R(1.0 / kN7), q8 = s8 * R(1.0 / kN8);
+        R gg6 = kg * q6, gg7 = kg * q7, gg8 = kg * q8;
+        const R gomg = -(q6 * s.g6 + q7 * s.g7 + q8 * s.g8);
+        // w_g = 1/(e^z + 1/2): d w_g / dz = -e^z w_g^2
+        gz = gomg * (-s.ez * s.omg * s.omg);
+        // back through the network
+#pragma unroll
+        for (int k = 0; k < kNetHidden; ++k) ga2[k] = gz * W3[k] * (R(1) - s.h2[k] * s.h2[k]);
+#pragma unroll
+        for (int j = 0; j < kNetHidden; ++j) {
+            R a = R(0);
+#pragma unroll
+            for (int k = 0; k < kNetHidden; ++k) a += W2[k * kNetHidden + j] * ga2[k];
+            ga1[j] = a * (R(1) - s.h1[j] * s.h1[j]);
+        }
+        R gI[kNetIn];
+#pragma unroll
+        for (int m = 0; m < kNetIn; ++m) {
+            R a = R(0);
+#pragma unroll
+            for (int j = 0; j < kNetHidden; ++j) a += W1[j * kNetIn + m] * ga1[j];
+            gI[m] = a * scale[m];
+        }
+        // back through the invariants
+        grho += gI[0];
+        gux += R(6) * ux * gI[1];
+        guy += R(6) * uy * gI[1];
+        gPxx += R(3) * gI[2] + R(18) * s.pxx * gI[3] + R(9) * ux * ux * gI[4];
+        gPyy += R(3) * gI[2] + R(18) * s.pyy * gI[3] + R(9) * uy * uy * gI[4];
+        gPxy += R(36) * s.pxy * gI[3] + R(18) * ux * uy * gI[4];
+        gux += R(18) * (ux * s.pxx + uy * s.pxy) * gI[4];
+        guy += R(18) * (ux * s.pxy + uy * s.pyy) * gI[4];
+        gg6 += R(2) * s.g6 * R(1.0 / kN6) * gI[5];
+        gg7 += R(2) * s.g7 * R(1.0 / kN7) * gI[5];
+        gg8 += R(2) * s.g8 * R(1.0 / kN8) * gI[5];
+        // Pi = sum c c f - rho u u - rho I/3
+        grho -= gPxx * (ux * ux + R(1.0 / 3.0)) + gPxy * ux * uy + gPyy * (uy * uy + R(1.0 / 3.0));
+        gux -= rho * (R(2) * ux * gPxx + uy * gPxy);
+        guy -= rho * (ux * gPxy + R(2) * uy * gPyy);
+        const R inv = R(1) / rho;
+        const R gdotu = gux * ux + guy * uy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int cx = c2(i, 0), cy = c2(i, 1);
+            // direct paths: Pi (c c) and the higher moments (H_g); the equilibrium
+            // term of f* has no direct dependence on f
+            R v = R(0);
+            if (cx) v += gPxx;
+            if (cy) v += gPyy;
+            if (cx && cy) v += (cx == cy) ? gPxy : -gPxy;
+            v += R(h6(i)) * gg6 + R(h7(i)) * gg7 + R(h8(i)) * gg8;
+            v += grho + (cdotu<D2Q9>(i, gux, guy, R(0)) - gdotu) * inv;
+            lam_out[(int64_t)i * g.plane + n] = v;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kNetHidden; ++k) {
+            ga1[k] = R(0);
+            ga2[k] = R(0);
+            s.h1[k] = R(0);
+            s.h2[k] = R(0);
+        }
+#pragma unroll
+        for (int m = 0; m < kNetIn; ++m) s.x[m] = R(0);
+    }
+    // stage the outer-product factors and reduce them over the block's nodes
+#pragma unroll
+    for (int k = 0; k < kNetHidden; ++k) {
+        sh.ga1[t][k] = ga1[k];
+        sh.ga2[t][k] = ga2[k];
+        sh.h1[t][k] = s.h1[k];
+        sh.h2[t][k] = s.h2[k];
+    }
+#pragma unroll
+    for (int m = 0; m < kNetIn; ++m) sh.x[t][m] = s.x[m];
+    sh.gz[t] = gz;
+    __syncthreads();
+    R* out = gth_partials + (int64_t)(blockIdx.x + (int64_t)gridDim.x * blockIdx.y) * kNetTheta;
+    for (int o = t; o < kNetTheta; o += kAdjBlock) {
+        R acc = R(0);
+        if (o < kNetHidden * kNetIn) {  // W1[j][m] += ga1_j x_m
+            const int j = o / kNetIn, m = o % kNetIn;
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga1[q][j] * sh.x[q][m];
+        } else if (o < kNetHidden * kNetIn + kNetHidden) {  // b1
+            const int j = o - kNetHidden * kNetIn;
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga1[q][j];
+        } else if (o < kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden) {  // W2[j][k] += ga2_j h1_k
+            const int r = o - (kNetHidden * kNetIn + kNetHidden);
+            const int j = r / kNetHidden, k = r % kNetHidden;
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga2[q][j] * sh.h1[q][k];
+        } else if (o < kNetHidden * kNetIn + 2 * kNetHidden + kNetHidden * kNetHidden) {  // b2
+            const int j = o - (kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden);
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga2[q][j];
+        } else if (o < kNetTheta - 1) {  // W3[k] += gz h2_k
+            const int k = o - (kNetHidden * kNetIn + 2 * kNetHidden + kNetHidden * kNetHidden);
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.gz[q] * sh.h2[q][k];
+        } else {  // b3
+            for (int q = 0; q < kAdjBlock; ++q) acc += sh.gz[q];
+        }
+        out[o] = acc;
+    }
+}
+
+template <class R>
+static Net<R> make_net(const double* v)
+{
+    Net<R> n;
+    for (int k = 0; k < kNetValues; ++k) n.v[k] = (R)v[k];
+    return n;
+}
+
+template <class T>
+static cudaError_t launch_learned(const OpArgs& a, const double* netv)
+{
+    using R = typename Store<T>::Real;
+    const Net<R> net = make_net<R>(netv);
+    const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
+    if (a.op == OP_UPDATE) {
+        const T* src = (const T*)a.src;
+        T* dst = (T*)a.dst;
+        if (a.mode == AB) k_learned_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        else if (a.mode == AA_EVEN)
+            k_learned_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        else k_learned_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        return cudaGetLastError();
+    }
+    if (a.op == OP_ADJ_STEP) {
+        const size_t smem = sizeof(AdjShared<R>);
+        cudaError_t e = cudaFuncSetAttribute(k_learned_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_learned_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
+                                                         (R)a.omega, (R*)a.gth, net);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t run_learned_d2q9(const OpArgs& a, const double* net)
+{
+    if (a.g.nz != 1) return cudaErrorInvalidValue;
+    switch (a.storage) {
+    case S_F64: return launch_learned<double>(a, net);
+    case S_F32: return launch_learned<float>(a, net);
+    case S_F16: return launch_learned<__half>(a, net);
+    case S_BF16: return launch_learned<__nv_bfloat16>(a, net);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int64_t learned_adj_partial_count(const Geom& g)
+{
+    return (int64_t)((g.nx + kAdjBlock - 1) / kAdjBlock) * g.ny;
+}
+
+// out[o] (+)= sum_b partials[b][o]: one thread per parameter, blocks summed in order
+template <class P>
+__global__ void k_reduce_theta(const P* partials, int64_t nblk, void* out, int out_f64)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= kNetTheta) return;
+    double acc = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) acc += (double)partials[b * kNetTheta + o];
+    if (out_f64) ((double*)out)[o] += acc;
+    else ((float*)out)[o] += (float)acc;
+}
+
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, void* out, int out_f64,
+                                 cudaStream_t s)
+{
+    const int threads = 128, blocks = (kNetTheta + threads - 1) / threads;
+    if (part_f64) k_reduce_theta<double><<<blocks, threads, 0, s>>>((const double*)partials, nblk, out, out_f64);
+    else k_reduce_theta<float><<<blocks, threads, 0, s>>>((const float*)partials, nblk, out, out_f64);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Eq. 6 loss
+// pass 1: u of every node into scratch rows 0, 1; block partials of
+// sum |u - u_ref|^2 and sum |u|^2
+template <class T>
+__global__ void __launch_bounds__(128) k_eq6_u(const T* buf, Geom g, int mode, const void* uref, int f64,
+                                               typename Store<T>::Real* scr, double* partials)
+{
+    using R = typename Store<T>::Real;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    double v[2] = {0.0, 0.0};
+    if (x < g.nx) {
+        const int64_t N = (int64_t)g.nx * g.ny;
+        Nbr nb = make_nbr(g, x, y, 0);
+        const int n = x + g.nx * y;
+        R f[9];
+        if (mode == AB) load_node<D2Q9, AB>(buf, g, nb, n, f);
+        else if (mode == AA_EVEN) load_node<D2Q9, AA_EVEN>(buf, g, nb, n, f);
+        else load_node<D2Q9, AA_ODD>(buf, g, nb, n, f);
+        R Fz[3] = {R(0), R(0), R(0)};
+        NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
+        scr[n] = m.ux;
+        scr[g.plane + n] = m.uy;
+        const double dx = (double)m.ux - (f64 ? ((const double*)uref)[n] : (double)((const float*)uref)[n]);
+        const double dy = (double)m.uy - (f64 ? ((const double*)uref)[N + n] : (double)((const float*)uref)[N + n]);
+        v[0] = dx * dx + dy * dy;
+        v[1] = (double)m.ux * m.ux + (double)m.uy * m.uy;
+    }
+    __shared__ double sh[2][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 2; ++k) {
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0) sh[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        const int64_t b = blockIdx.x + (int64_t)gridDim.x * blockIdx.y;
+        for (int k = 0; k < 2; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            partials[2 * b + k] = s;
+        }
+    }
+}
+
+// pass 2: vorticity w = (v(x+1) - v(x-1))/2 - (u(y+1) - u(y-1))/2; scratch row 2 gets
+// r = 2 * 0.2 (w - w_ref) / N; block partials of sum (w - w_ref)^2
+template <class R>
+__global__ void __launch_bounds__(128) k_eq6_w(Geom g, const void* wref, int f64, R* scr, double* partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    double v = 0.0;
+    if (x < g.nx) {
+        const int64_t N = (int64_t)g.nx * g.ny;
+        Nbr nb = make_nbr(g, x, y, 0);
+        const int n = x + g.nx * y;
+        const R w = R(0.5) * (scr[g.plane + nb.node(g, 1, 0, 0)] - scr[g.plane + nb.node(g, -1, 0, 0)]) -
+                    R(0.5) * (scr[nb.node(g, 0, 1, 0)] - scr[nb.node(g, 0, -1, 0)]);
+        const double dw = (double)w - (f64 ? ((const double*)wref)[n] : (double)((const float*)wref)[n]);
+        scr[2 * g.plane + n] = (R)(0.4 * dw / (double)N);
+        v = dw * dw;
+    }
+    __shared__ double sh[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[w];
+        partials[blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+    }
+}
+
+// pass 3: dL/du and lambda_i = dL/du . (c_i - u)/rho
+template <class T>
+__global__ void __launch_bounds__(128) k_eq6_seed(const T* buf, Geom g, int mode, const void* uref, int f64,
+                                                  const typename Store<T>::Real* scr, const double* sums,
+                                                  double Eref, void* lam)
+{
+    using R = typename Store<T>::Real;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= g.nx) return;
+    const int64_t N = (int64_t)g.nx * g.ny;
+    Nbr nb = make_nbr(g, x, y, 0);
+    const int n = x + g.nx * y;
+    R f[9];
+    if (mode == AB) load_node<D2Q9, AB>(buf, g, nb, n, f);
+    else if (mode == AA_EVEN) load_node<D2Q9, AA_EVEN>(buf, g, nb, n, f);
+    else load_node<D2Q9, AA_ODD>(buf, g, nb, n, f);
+    R Fz[3] = {R(0), R(0), R(0)};
+    NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
+    const double E = 0.5 * sums[1] / (double)N;
+    const double ux = m.ux, uy = m.uy;
+    const double urx = f64 ? ((const double*)uref)[n] : (double)((const float*)uref)[n];
+    const double ury = f64 ? ((const double*)uref)[N + n] : (double)((const float*)uref)[N + n];
+    const R* r = scr + 2 * g.plane;
+    double gx = 1.2 * (ux - urx) / (double)N + 0.4 * (E - Eref) * ux / (double)N;
+    double gy = 1.2 * (uy - ury) / (double)N + 0.4 * (E - Eref) * uy / (double)N;
+    gy += 0.5 * (double)r[nb.node(g, -1, 0, 0)] - 0.5 * (double)r[nb.node(g, 1, 0, 0)];
+    gx += -0.5 * (double)r[nb.node(g, 0, -1, 0)] + 0.5 * (double)r[nb.node(g, 0, 1, 0)];
+    const double inv = 1.0 / (double)m.rho;
+    const double gdotu = gx * ux + gy * uy;
+    for (int i = 0; i < 9; ++i) {
+        const double v = (c2(i, 0) * gx + c2(i, 1) * gy - gdotu) * inv;
+        if (f64) ((double*)lam)[(int64_t)i * N + n] = v;
+        else ((float*)lam)[(int64_t)i * N + n] = (float)v;
+    }
+}
+
+__global__ void k_eq6_combine(const double* sums, int64_t N, double Eref, double* out)
+{
+    const double E = 0.5 * sums[1] / (double)N;
+    out[0] = 0.6 * sums[0] / (double)N + 0.2 * sums[2] / (double)N + 0.2 * (E - Eref) * (E - Eref);
+}
+
+template <class T>
+static cudaError_t loss_eq6_typed(const LossEq6Args& e, int* launches)
+{
+    using R = typename Store<T>::Real;
+    const OpArgs& a = e.a;
+    const dim3 bl = node_block(a.g), gr = node_grid(a.g);
+    const int64_t nb = node_grid_blocks(a.g);
+    double* p_u = e.partials;           // 2 * nb
+    double* p_w = e.partials + 2 * nb;  // nb
+    double* sums = e.partials + 3 * nb; // 3
+    R* scr = (R*)e.scratch;
+    k_eq6_u<T><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.mode, e.uref, e.io_f64, scr, p_u);
+    cudaError_t err = reduce_final(p_u, nb, 2, sums, a.stream);
+    if (err != cudaSuccess) return err;
+    k_eq6_w<R><<<gr, bl, 0, a.stream>>>(a.g, e.wref, e.io_f64, scr, p_w);
+    if ((err = reduce_final(p_w, nb, 1, sums + 2, a.stream)) != cudaSuccess) return err;
+    *launches += 4;
+    if (e.lam) {
+        k_eq6_seed<T><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.mode, e.uref, e.io_f64, scr, sums, e.Eref, e.lam);
+        *launches += 1;
+    }
+    k_eq6_combine<<<1, 1, 0, a.stream>>>(sums, e.N, e.Eref, e.result);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t loss_eq6_d2q9(const LossEq6Args& e, int* launches)
+{
+    switch (e.a.storage) {
+    case S_F64: return loss_eq6_typed<double>(e, launches);
+    case S_F32: return loss_eq6_typed<float>(e, launches);
+    case S_F16: return loss_eq6_typed<__half>(e, launches);
+    case S_BF16: return loss_eq6_typed<__nv_bfloat16>(e, launches);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lb

@@ -1,0 +1,37 @@
+// Learned moment-space collision on D2Q9 (Eq. 5, Sec. 3.1) and the Eq. 6 loss:
+// host-side declarations shared by lb_api.cu and lb_learned.cu.
+#pragma once
+
+#include "lb_ops.cuh"
+
+namespace lb {
+
+constexpr int kNetIn = 6, kNetHidden = 24;
+constexpr int kNetTheta = kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden + kNetHidden + kNetHidden + 1;
+constexpr int kNetValues = kNetTheta + 2 * kNetIn;  // + input shift and scale
+static_assert(kNetTheta == 793, "6-24-24-1 network has 793 parameters");
+
+// forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
+// net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint)
+cudaError_t run_learned_d2q9(const OpArgs& a, const double* net);
+// number of blocks of the learned adjoint launch (rows of the gradient partials)
+int64_t learned_adj_partial_count(const Geom& g);
+// out[793] (+)= sum over blocks of partials[block][793]
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, void* out, int out_f64,
+                                 cudaStream_t s);
+
+struct LossEq6Args {
+    OpArgs a;                    // state, geometry, stream
+    const void* uref = nullptr;  // [2][N] caller dtype
+    const void* wref = nullptr;  // [N]
+    double Eref = 0.0;
+    void* lam = nullptr;         // [9][N] caller dtype, may be null
+    int io_f64 = 1;
+    double* partials = nullptr;  // >= 3 * blocks + 8 doubles
+    double* result = nullptr;    // device double: the loss
+    void* scratch = nullptr;     // [3][plane] arithmetic type
+    int64_t N = 0;
+};
+cudaError_t loss_eq6_d2q9(const LossEq6Args& e, int* launches);
+
+}  // namespace lb

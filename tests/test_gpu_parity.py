@@ -1,0 +1,450 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error measure for populations: max over i, x of |f_gpu - f_oracle| / w_i (the
+populations scale with w_i). Bars: streaming (collision "none") bit-exact in
+FP64/FP32; FP64 collisions <= 1e-12; FP32 <= 1e-5 after 100 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import lbinputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+STENCILS = ["D2Q9", "D3Q19", "D3Q27"]
+TINY = {"D2Q9": [(5, 4, 1), (7, 3, 1), (33, 5, 1)], "D3Q19": [(5, 4, 3), (7, 6, 5)], "D3Q27": [(5, 4, 3), (7, 6, 5)]}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2106_12929_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def L(*a, **k):
+    from paper_2106_12929_gb300 import Lattice
+    return Lattice(*a, **k)
+
+
+def werr(a, b, w):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / w[:, None]))
+
+
+def gpu_pops(lat):
+    return lat.get_populations(torch.float64, "cpu").numpy()
+
+
+def near_eq(name, dims, seed, eps=0.05):
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    rho, u = lbinputs.random_moments(dims, seed=seed, u_amp=0.05)
+    return oracle.init_eq(name, dims, rho, u) + eps * 0.1 * w[:, None] * lbinputs.random_field((len(w), N), seed + 1)
+
+
+# ------------------------------------------------------------------ streaming
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_streaming_bit_exact(name, storage, layout):
+    d, c, w, _ = oracle.stencil(name)
+    for dims in TINY[name]:
+        N = oracle.n_nodes(dims)
+        f0 = lbinputs.random_populations(w, N, seed=3)
+        if storage == "f32":
+            f0 = f0.astype(np.float32).astype(np.float64)
+        lat = L(name, dims, 0.8, "none", storage=storage, layout=layout)
+        lat.set_populations(f0)
+        np.testing.assert_array_equal(gpu_pops(lat), f0)
+        for n in (1, 2, 3):
+            lat.step(1)
+            np.testing.assert_array_equal(gpu_pops(lat), oracle.step(name, dims, 0.8, "none", f0, nsteps=n))
+        lat.close()
+
+
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_streaming_half_storage_moves_values_unchanged(name, storage):
+    d, c, w, _ = oracle.stencil(name)
+    dims = TINY[name][0]
+    N = oracle.n_nodes(dims)
+    lat = L(name, dims, 0.8, "none", storage=storage)
+    lat.set_populations(lbinputs.random_populations(w, N, seed=4))
+    q0 = gpu_pops(lat)  # the quantised state
+    lat.step(3)
+    ref = oracle.step(name, dims, 0.8, "none", q0, nsteps=3)
+    # a load/store round trip of a quantised value may move it by one FP32 rounding at most
+    assert werr(gpu_pops(lat), ref, w) < 1e-6
+
+
+# ------------------------------------------------------------------ FP64 collision parity
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("coll", ["bgk", "regularized"])
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_collision_fp64_matches_oracle(name, coll, forced, layout):
+    d, c, w, _ = oracle.stencil(name)
+    for dims in TINY[name][:2]:
+        N = oracle.n_nodes(dims)
+        f0 = near_eq(name, dims, seed=11)
+        F = lbinputs.random_field((d, N), seed=12, amp=1e-3) if forced else None
+        lat = L(name, dims, 0.67, coll, storage="f64", layout=layout)
+        if forced:
+            lat.set_force(F)
+        lat.set_populations(f0)
+        lat.step(1)
+        ref1 = oracle.step(name, dims, 0.67, coll, f0, nsteps=1, F=F)
+        assert werr(gpu_pops(lat), ref1, w) <= 1e-12
+        lat.step(9)
+        ref10 = oracle.step(name, dims, 0.67, coll, ref1, nsteps=9, F=F)
+        assert werr(gpu_pops(lat), ref10, w) <= 1e-12
+        lat.close()
+
+
+@pytest.mark.parametrize("name", STENCILS)
+def test_aa_matches_ab_bit_exact(name):
+    d, c, w, _ = oracle.stencil(name)
+    dims = TINY[name][1]
+    f0 = near_eq(name, dims, seed=21)
+    for storage in ["f64", "f32"]:
+        a = L(name, dims, 0.6, "bgk", storage=storage, layout="ab")
+        b = L(name, dims, 0.6, "bgk", storage=storage, layout="aa")
+        a.set_populations(f0)
+        b.set_populations(f0)
+        for _ in range(4):
+            a.step(1)
+            b.step(1)
+            np.testing.assert_array_equal(gpu_pops(a), gpu_pops(b))
+            ra, ua = a.moments()
+            rb, ub = b.moments()
+            assert torch.equal(ra, rb) and torch.equal(ua, ub)
+
+
+# ------------------------------------------------------------------ FP32, 100 steps
+@pytest.mark.parametrize("name,n,coll,tau", [("D2Q9", 64, "bgk", 0.8), ("D3Q19", 64, "bgk", None),
+                                             ("D3Q27", 24, "regularized", 0.55)])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_fp32_100_steps_within_1e_5(name, n, coll, tau, layout):
+    d, c, w, _ = oracle.stencil(name)
+    if name == "D2Q9":
+        dims, rho, u = lbinputs.taylor_green_2d(n, u0=0.05)
+    else:
+        u0 = 0.1 / math.sqrt(3.0)
+        dims, rho, u = lbinputs.taylor_green_3d(n, u0=u0)
+        if tau is None:
+            tau = lbinputs.tau_from_reynolds(1600.0, u0, n)
+    lat = L(name, dims, tau, coll, storage="f32", layout=layout)
+    lat.init_from_moments(rho, u)
+    lat.step(100)
+    ref = oracle.step(name, dims, tau, coll, oracle.init_eq(name, dims, rho, u), nsteps=100)
+    assert werr(gpu_pops(lat), ref, w) <= 1e-5
+    r_o, u_o = oracle.moments(name, dims, ref)
+    r_g, u_g = lat.moments(torch.float64, "cpu")
+    assert np.max(np.abs(r_g.numpy() - r_o)) <= 1e-5
+    assert np.max(np.abs(u_g.numpy() - u_o)) <= 1e-5 * 0.1
+
+
+# ------------------------------------------------------------------ moments and sums
+@pytest.mark.parametrize("name", STENCILS)
+@pytest.mark.parametrize("forced", [False, True])
+def test_moments_and_reduce_fp64(name, forced):
+    d, c, w, _ = oracle.stencil(name)
+    dims = TINY[name][1]
+    N = oracle.n_nodes(dims)
+    f0 = near_eq(name, dims, seed=31)
+    F = lbinputs.random_field((d, N), seed=32, amp=1e-3) if forced else None
+    for layout in ["ab", "aa"]:
+        lat = L(name, dims, 0.7, "bgk", storage="f64", layout=layout)
+        if forced:
+            lat.set_force(F)
+        lat.set_populations(f0)
+        lat.step(3)
+        ref = oracle.step(name, dims, 0.7, "bgk", f0, nsteps=3, F=F)
+        r_o, u_o = oracle.moments(name, dims, ref, F=F)
+        r_g, u_g = lat.moments(torch.float64, "cpu")
+        np.testing.assert_allclose(r_g.numpy(), r_o, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(u_g.numpy(), u_o, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(lat.reduce(), oracle.reduce(name, dims, ref, F=F), rtol=1e-12, atol=1e-15)
+        # device outputs, FP32
+        r32, u32 = lat.moments(torch.float32, "cuda")
+        np.testing.assert_allclose(r32.cpu().numpy(), r_o, rtol=1e-6)
+
+
+def test_reduce_is_deterministic():
+    dims, rho, u = lbinputs.taylor_green_3d(48)
+    lat = L("D3Q19", dims, 0.6, "bgk", storage="f32")
+    lat.init_from_moments(rho, u)
+    lat.step(5)
+    a = lat.reduce()
+    b = lat.reduce()
+    np.testing.assert_array_equal(a, b)
+
+
+def test_init_from_device_fp32_arrays():
+    dims, rho, u = lbinputs.taylor_green_2d(32)
+    lat = L("D2Q9", dims, 0.8, "bgk", storage="f64")
+    lat.init_from_moments(torch.tensor(rho, dtype=torch.float32, device="cuda"),
+                          torch.tensor(u, dtype=torch.float32, device="cuda"))
+    ref = oracle.init_eq("D2Q9", dims, rho.astype(np.float32).astype(np.float64),
+                         u.astype(np.float32).astype(np.float64))
+    assert werr(gpu_pops(lat), ref, oracle.stencil("D2Q9")[2]) <= 1e-14
+
+
+# ------------------------------------------------------------------ half-precision storage
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+def test_half_storage_tracks_oracle(storage, tol):
+    name = "D2Q9"
+    d, c, w, _ = oracle.stencil(name)
+    dims, rho, u = lbinputs.taylor_green_2d(64, u0=0.05)
+    lat = L(name, dims, 0.8, "bgk", storage=storage)
+    lat.init_from_moments(rho, u)
+    lat.step(50)
+    ref = oracle.step(name, dims, 0.8, "bgk", oracle.init_eq(name, dims, rho, u), nsteps=50)
+    # error relative to the largest deviation from rest, which is what the shifted format stores
+    dev = np.max(np.abs(ref - w[:, None]) / w[:, None])
+    assert werr(gpu_pops(lat), ref, w) <= tol * dev
+
+
+# ------------------------------------------------------------------ learned collision
+def _net(tau, seed=5, out_scale=0.5):
+    th = lbinputs.random_mlp_params(seed, out_bias=math.log(tau - 0.5), out_scale=out_scale)
+    return np.concatenate([th, np.zeros(6), np.array([50.0, 100.0, 300.0, 1e5, 1e5, 1e5])])
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_learned_fp64_matches_oracle(layout):
+    name = "D2Q9"
+    d, c, w, _ = oracle.stencil(name)
+    dims = (33, 7, 1)
+    tau = 0.6
+    net = _net(tau)
+    f0 = near_eq(name, dims, seed=41)
+    lat = L(name, dims, tau, "learned", storage="f64", layout=layout)
+    lat.set_mlp(net)
+    lat.set_populations(f0)
+    lat.step(5)
+    ref = oracle.step(name, dims, tau, "learned", f0, nsteps=5, mlp=net)
+    assert werr(gpu_pops(lat), ref, w) <= 1e-12
+
+
+def test_learned_fp32_100_steps():
+    name = "D2Q9"
+    d, c, w, _ = oracle.stencil(name)
+    dims, rho, u = lbinputs.shear_layer(64, u0=0.05)
+    tau = 0.55
+    net = _net(tau, seed=6)
+    lat = L(name, dims, tau, "learned", storage="f32")
+    lat.set_mlp(net)
+    lat.init_from_moments(rho, u)
+    lat.step(100)
+    ref = oracle.step(name, dims, tau, "learned", oracle.init_eq(name, dims, rho, u), nsteps=100, mlp=net)
+    assert werr(gpu_pops(lat), ref, w) <= 1e-5
+
+
+def test_learned_with_bgk_network_equals_bgk():
+    name = "D2Q9"
+    dims, rho, u = lbinputs.shear_layer(32)
+    tau = 0.6
+    net = _net(tau, out_scale=0.0)
+    a = L(name, dims, tau, "learned", storage="f64")
+    a.set_mlp(net)
+    b = L(name, dims, tau, "bgk", storage="f64")
+    for lat in (a, b):
+        lat.init_from_moments(rho, u)
+        lat.step(20)
+    assert werr(gpu_pops(a), gpu_pops(b), oracle.stencil(name)[2]) <= 1e-13
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("name,dims,coll,forced", [
+    ("D2Q9", (9, 7, 1), "bgk", True), ("D2Q9", (9, 7, 1), "regularized", True),
+    ("D3Q19", (5, 4, 3), "bgk", True), ("D3Q27", (5, 4, 3), "regularized", False),
+    ("D2Q9", (9, 7, 1), "none", False)])
+def test_adjoint_fp64_matches_oracle(name, dims, coll, forced):
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    f0 = near_eq(name, dims, seed=51)
+    F = lbinputs.random_field((d, N), seed=52, amp=1e-3) if forced else None
+    lamT = lbinputs.random_field((len(w), N), seed=53)
+    n = 7
+    lat = L(name, dims, 0.7, coll, storage="f64", record_every=3)
+    if forced:
+        lat.set_force(F)
+    lat.set_populations(f0)
+    lat.step(n)
+    gF = torch.zeros((d, N), dtype=torch.float64) if forced else None
+    lam0 = lat.step_adjoint(torch.tensor(lamT), n, grad_F=gF)
+    ref_lam, ref_gF, _ = oracle.adjoint(name, dims, 0.7, coll, f0, n, lamT, F=F)
+    scale = np.max(np.abs(ref_lam))
+    assert np.max(np.abs(lam0.numpy() - ref_lam)) <= 1e-12 * scale
+    if forced:
+        assert np.max(np.abs(gF.numpy() - ref_gF)) <= 1e-12 * np.max(np.abs(ref_gF))
+    # the state is left at f^n
+    assert werr(gpu_pops(lat), oracle.step(name, dims, 0.7, coll, f0, nsteps=n, F=F), w) <= 1e-12
+
+
+def test_learned_adjoint_fp64_matches_oracle():
+    name = "D2Q9"
+    d, c, w, _ = oracle.stencil(name)
+    dims = (131, 3, 1)  # more than one block of the parameter-gradient reduction, ragged tail
+    N = oracle.n_nodes(dims)
+    tau = 0.6
+    net = _net(tau, seed=8)
+    f0 = near_eq(name, dims, seed=61)
+    lamT = lbinputs.random_field((9, N), seed=62)
+    lat = L(name, dims, tau, "learned", storage="f64", record_every=2)
+    lat.set_mlp(net)
+    lat.set_populations(f0)
+    lat.step(5)
+    gth = torch.zeros(793, dtype=torch.float64)
+    lam0 = lat.step_adjoint(torch.tensor(lamT), 5, grad_theta=gth)
+    ref_lam, _, ref_th = oracle.adjoint(name, dims, tau, "learned", f0, 5, lamT, mlp=net)
+    assert np.max(np.abs(lam0.numpy() - ref_lam)) <= 1e-11 * np.max(np.abs(ref_lam))
+    assert np.max(np.abs(gth.numpy() - ref_th)) <= 1e-10 * np.max(np.abs(ref_th))
+
+
+def test_adjoint_fp32_gradient_within_1e_4_of_fp64_reference():
+    # energy-field loss of a forced D2Q9 run: the FP32 GPU gradient w.r.t. F against
+    # the oracle's FP64 adjoint, which itself matches finite differences
+    name = "D2Q9"
+    d, c, w, _ = oracle.stencil(name)
+    dims, rho, u = lbinputs.shear_layer(64, u0=0.05)
+    N = oracle.n_nodes(dims)
+    tau = 0.6
+    F = lbinputs.smooth_force(dims, 1e-5, seed=12929)
+    et = lbinputs.random_field(N, 7, amp=1e-4) + 1e-3
+    n = 50
+    lat = L(name, dims, tau, "bgk", storage="f32", record_every=10)
+    lat.set_force(torch.tensor(F, dtype=torch.float32, device="cuda"))
+    lat.init_from_moments(rho, u)
+    lat.step(n)
+    gF = torch.zeros((2, N), dtype=torch.float32, device="cuda")
+    loss, lamT = lat.loss_energy(torch.tensor(et, dtype=torch.float32, device="cuda"), grad_F=gF)
+    lat.step_adjoint(lamT, n, grad_F=gF, want_lambda0=False)
+    f0 = oracle.init_eq(name, dims, rho, u)
+    fN = oracle.step(name, dims, tau, "bgk", f0, nsteps=n, F=F)
+    L_o, lam_o, gF_o = oracle.loss_energy(name, dims, fN, et, F=F)
+    _, gF_adj, _ = oracle.adjoint(name, dims, tau, "bgk", f0, n, lam_o, F=F)
+    ref = gF_o + gF_adj
+    assert abs(loss - L_o) <= 1e-4 * abs(L_o)
+    rel = np.linalg.norm(gF.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-4
+
+
+def test_adjoint_requires_matching_recording():
+    from paper_2106_12929_gb300 import LBError
+    dims = (8, 8, 1)
+    lat = L("D2Q9", dims, 0.7, "bgk", storage="f64", record_every=4)
+    lat.init_from_moments(np.ones(64), np.zeros((2, 64)))
+    lat.step(6)
+    with pytest.raises(LBError) as e:
+        lat.step_adjoint(torch.zeros((9, 64), dtype=torch.float64), 5)
+    assert e.value.code == "LB_ERR_STATE"
+    plain = L("D2Q9", dims, 0.7, "bgk", storage="f64")
+    plain.init_from_moments(np.ones(64), np.zeros((2, 64)))
+    plain.step(2)
+    with pytest.raises(LBError):
+        plain.step_adjoint(torch.zeros((9, 64), dtype=torch.float64), 2)
+
+
+# ------------------------------------------------------------------ loss seeds
+def test_energy_loss_and_moment_seed_fp64():
+    name = "D3Q19"
+    d, c, w, _ = oracle.stencil(name)
+    dims = (5, 4, 3)
+    N = 60
+    f0 = near_eq(name, dims, seed=71)
+    F = lbinputs.random_field((3, N), seed=72, amp=1e-3)
+    et = lbinputs.random_field(N, 73, amp=1e-3) + 2e-3
+    lat = L(name, dims, 0.7, "bgk", storage="f64")
+    lat.set_force(F)
+    lat.set_populations(f0)
+    gF = torch.zeros((3, N), dtype=torch.float64)
+    loss, lam = lat.loss_energy(torch.tensor(et), grad_F=gF)
+    L_o, lam_o, gF_o = oracle.loss_energy(name, dims, f0, et, F=F)
+    assert abs(loss - L_o) <= 1e-13 * abs(L_o)
+    np.testing.assert_allclose(lam.numpy(), lam_o, rtol=0, atol=1e-13 * np.abs(lam_o).max())
+    np.testing.assert_allclose(gF.numpy(), gF_o, rtol=0, atol=1e-13 * np.abs(gF_o).max())
+    gr = lbinputs.random_field(N, 74)
+    gu = lbinputs.random_field((3, N), 75)
+    gF2 = torch.zeros((3, N), dtype=torch.float64)
+    lam2 = lat.adjoint_seed_moments(torch.tensor(gr), torch.tensor(gu), grad_F=gF2)
+    lam2_o, gF2_o = oracle.seed_moments(name, dims, f0, gr, gu, F=F)
+    np.testing.assert_allclose(lam2.numpy(), lam2_o, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(gF2.numpy(), gF2_o, rtol=0, atol=1e-13)
+
+
+def test_eq6_loss_fp64():
+    dims = (17, 13, 1)
+    N = 17 * 13
+    f0 = near_eq("D2Q9", dims, seed=81)
+    uref = lbinputs.random_field((2, N), 82, amp=0.05)
+    wref = lbinputs.random_field(N, 83, amp=0.01)
+    lat = L("D2Q9", dims, 0.7, "bgk", storage="f64")
+    lat.set_populations(f0)
+    loss, lam = lat.loss_eq6(torch.tensor(uref), torch.tensor(wref), 1e-3)
+    L_o, lam_o = oracle.loss_eq6(dims, f0, uref, wref, 1e-3)
+    assert abs(loss - L_o) <= 1e-13 * abs(L_o)
+    np.testing.assert_allclose(lam.numpy(), lam_o, rtol=0, atol=1e-13 * np.abs(lam_o).max())
+
+
+# ------------------------------------------------------------------ failure detection
+def test_unstable_state_is_reported_not_trapped():
+    from paper_2106_12929_gb300 import LBError
+    name = "D2Q9"
+    dims = (16, 8, 1)
+    d, c, w, _ = oracle.stencil(name)
+    f0 = near_eq(name, dims, seed=91)
+    f0[3, 17] = float("nan")  # fault injected from the host
+    lat = L(name, dims, 0.7, "bgk", storage="f32", check_every=2)
+    lat.set_populations(f0)
+    with pytest.raises(LBError) as e:
+        lat.step(4)
+    assert e.value.code == "LB_ERR_UNSTABLE"
+    # the flag is cleared and the context stays usable
+    lat.set_populations(near_eq(name, dims, seed=92))
+    lat.step(4)
+    lat.check()
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_full_size_d3q19_256_sampled(layout):
+    """The benchmark's workload (D3Q19 BGK FP32, 256^3 TGV, Re 1600, Ma 0.1) in its
+    launch configuration: one step, 64 sampled nodes recomputed by the oracle one by one."""
+    name = "D3Q19"
+    d, c, w, _ = oracle.stencil(name)
+    n = 256
+    u0 = 0.1 / math.sqrt(3.0)
+    tau = lbinputs.tau_from_reynolds(1600.0, u0, n)
+    dims, rho, u = lbinputs.taylor_green_3d(n, u0=u0)
+    lat = L(name, dims, tau, "bgk", storage="f32", layout=layout)
+    lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    lat.step(1)
+    f1 = lat.get_populations(torch.float64, "cuda")
+    rng = np.random.default_rng(256)
+    xs = rng.integers(0, n, size=(64, 3))
+    xs[:4] = [[0, 0, 0], [n - 1, n - 1, n - 1], [0, n - 1, 7], [n - 1, 0, 0]]
+    # the FP32 state after init is f^eq rounded to FP32: the oracle starts from that
+    worst = 0.0
+    for x, y, z in xs:
+        node = x + n * (y + n * z)
+        got = f1[:, node].cpu().numpy()
+        for i in range(len(w)):
+            sx, sy, sz = (x - c[i, 0]) % n, (y - c[i, 1]) % n, (z - c[i, 2]) % n
+            src = sx + n * (sy + n * sz)
+            fsrc = oracle.init_eq(name, (1, 1, 1), [rho[src]], u[:, src].reshape(3, 1))[:, 0]
+            fsrc = fsrc.astype(np.float32).astype(np.float64)
+            post = oracle.collide_node(name, tau, "bgk", fsrc)
+            worst = max(worst, abs(got[i] - post[i]) / w[i])
+    assert worst <= 1e-6
+    # properties at full size: mass conserved, momentum zero
+    r = lat.reduce()
+    assert abs(r[0] / n ** 3 - rho.mean()) <= 1e-6
+    assert np.max(np.abs(r[1:4])) / n ** 3 <= 1e-7

@@ -1,0 +1,98 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every declared
+symbol, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_12929_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def _header_functions():
+    with open(os.path.join(ROOT, "include", "lb.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^LB_API\s+[\w\s\*]+?\b(lb_\w+)\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = _header_functions()
+    for required in ["lb_create", "lb_init_from_moments", "lb_step", "lb_moments", "lb_step_adjoint",
+                     "lb_reduce", "lb_get_populations", "lb_set_populations", "lb_destroy"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2106_12929_gb300 import _lib
+    names = _header_functions()
+    assert names == _lib.declared_symbols()
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.lb_status_string(code)
+    assert lib.lb_status_string(99) == b"unknown status"
+
+
+def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
+    from paper_2106_12929_gb300 import _lib
+    opt = _lib.Options()
+    lib.lb_default_options(ctypes.byref(opt))
+    for k, v in opt_kw.items():
+        setattr(opt, k, v)
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 3)(*dims)
+    rc = lib.lb_create(ctypes.byref(h), stencil, d, ctypes.c_double(tau), coll, ctypes.byref(opt))
+    return rc, h
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(tau=0.5), 1),                     # tau must exceed 1/2
+    (dict(tau=float("nan")), 1),
+    (dict(dims=(8, 8, 2)), 1),              # 2D stencil needs nz = 1
+    (dict(dims=(0, 8, 1)), 1),
+    (dict(stencil=7), 1),
+    (dict(coll=9), 1),
+    (dict(stencil=1, dims=(4, 4, 4), coll=2), 6),   # learned collision is D2Q9 only
+    (dict(storage=5), 1),
+    (dict(layout=1, record_every=5), 6),    # recording needs the AB layout
+])
+def test_create_rejects_bad_arguments_without_gpu(lib, kw, expect):
+    opt_keys = {"storage", "layout", "record_every", "check_every"}
+    opt = {k: v for k, v in kw.items() if k in opt_keys}
+    args = {k: v for k, v in kw.items() if k not in opt_keys}
+    rc, h = _create(lib, **args, **opt)
+    assert rc == expect
+    assert not h.value
+    assert lib.lb_last_error()
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.lb_step(None, 1) == 1
+    assert lib.lb_check(None) == 1
+    assert lib.lb_num_nodes(None) == -1
+    lib.lb_destroy(None)
+
+
+def test_adam_rejects_bad_arguments(lib):
+    assert lib.lb_adam_update(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1
+
+
+def test_product_path_has_no_cpu_fallback():
+    # the package must not import the oracle, and must raise if the library is missing
+    import paper_2106_12929_gb300 as pkg
+    pkg_dir = os.path.dirname(pkg.__file__)
+    for fn in os.listdir(pkg_dir):
+        if fn.endswith(".py"):
+            with open(os.path.join(pkg_dir, fn)) as fh:
+                src = fh.read()
+            assert "import oracle" not in src and "from oracle" not in src, fn
