@@ -154,6 +154,35 @@ def tgv_workload(n=N_GRID):
     return dims, tau, rho, u
 
 
+ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout)
+    "ab_f32": ("D3Q19", "f32", "ab"), "aa_f32": ("D3Q19", "f32", "aa"), "ab_f16": ("D3Q19", "f16", "ab"),
+    "ab_bf16": ("D3Q19", "bf16", "ab"), "aa_f16": ("D3Q19", "f16", "aa"), "ab_f64": ("D3Q19", "f64", "ab"),
+}
+
+
+def run_only(args):
+    """One workload only, K timed steps after W warm-up steps: a small, repeatable command
+    for profilers. Prints a JSON line with its GLUPS and roofline fraction."""
+    import torch
+    from paper_2106_12929_gb300 import Lattice, build
+    build.build()
+    if args.only == "adjoint":
+        print(json.dumps({"only": "adjoint", **adjoint_ratio(torch.cuda.current_stream(), n=args.grid or 1024,
+                                                             steps=args.steps)}))
+        return
+    stencil, storage, layout = ONLY[args.only]
+    dims, tau, rho, u = tgv_workload(args.grid or N_GRID)
+    N = int(np.prod(dims))
+    lat = Lattice(stencil, dims, tau, "bgk", storage=storage, layout=layout)
+    lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    lat.step(args.warmup)
+    t = time_steps(lat, args.steps, torch.cuda.current_stream())
+    lat.check()
+    g = N * args.steps / t / 1e9
+    print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "glups": round(g, 3),
+                      "hbm_frac": round(g * BYTES_PER_LU[(stencil, storage)] / measured_peak_hbm()[0], 4)}))
+
+
 def run_ours(args):
     import torch
     from paper_2106_12929_gb300 import Lattice, build
@@ -361,11 +390,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint"]), default=None,
+                    help="run a single workload (profiling aid); no contract line")
+    ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 

@@ -1,7 +1,8 @@
 // Per-node collision in registers: moments (Eq. 4), second-order equilibrium
 // (Eq. 3), BGK (Eq. 2), regularized (Latt & Chopard) and the Guo body-force source.
-// R is the arithmetic type (double or float); the populations f[Q] are replaced
-// by their post-collision values.
+// R is the arithmetic type (double or float). All values are deviations from rest,
+// delta_i = f_i - w_i (so rho - 1 = sum delta, rho u = sum c delta + F/2); the
+// arrays d[Q] are replaced by their post-collision deviations.
 #pragma once
 
 #include "lb_device.cuh"
@@ -13,27 +14,29 @@ enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3 };
 template <class St, class R>
 struct NodeMoments {
     R rho, ux, uy, uz;
+    R rho1;  // rho - 1
 };
 
-// rho = sum f, u = (sum c f + F/2) / rho
+// rho - 1 = sum delta, u = (sum c delta + F/2) / rho (sum w c = 0)
 template <class St, bool FORCE, class R>
-LB_DEV NodeMoments<St, R> node_moments(const R* f, const R* F)
+LB_DEV NodeMoments<St, R> node_moments(const R* d, const R* F)
 {
-    R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+    R rho1 = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
-        rho += f[i];
-        if (St::c(i, 0)) jx += St::c(i, 0) > 0 ? f[i] : -f[i];
-        if (St::c(i, 1)) jy += St::c(i, 1) > 0 ? f[i] : -f[i];
-        if (St::D == 3 && St::c(i, 2)) jz += St::c(i, 2) > 0 ? f[i] : -f[i];
+        rho1 += d[i];
+        if (St::c(i, 0)) jx += St::c(i, 0) > 0 ? d[i] : -d[i];
+        if (St::c(i, 1)) jy += St::c(i, 1) > 0 ? d[i] : -d[i];
+        if (St::D == 3 && St::c(i, 2)) jz += St::c(i, 2) > 0 ? d[i] : -d[i];
     }
     if constexpr (FORCE) {
         jx += R(0.5) * F[0];
         jy += R(0.5) * F[1];
         if (St::D == 3) jz += R(0.5) * F[2];
     }
-    R inv = R(1) / rho;
-    return {rho, jx * inv, jy * inv, jz * inv};
+    const R rho = R(1) + rho1;
+    const R inv = R(1) / rho;
+    return {rho, jx * inv, jy * inv, jz * inv, rho1};
 }
 
 template <class St, class R>
@@ -46,15 +49,16 @@ LB_DEV R cdotu(int i, R ux, R uy, R uz)
     return cu;
 }
 
-// f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)   (c_s^2 = 1/3)
+// f^eq_i - w_i, with f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)   (c_s^2 = 1/3):
+// deq_i = w_i [(rho - 1) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]
 template <class St, class R>
-LB_DEV void equilibrium(const NodeMoments<St, R>& m, R* feq)
+LB_DEV void equilibrium(const NodeMoments<St, R>& m, R* deq)
 {
-    R base = R(1) - R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
-        feq[i] = R(St::w(i)) * m.rho * (base + cu * (R(3) + R(4.5) * cu));
+        deq[i] = R(St::w(i)) * (m.rho1 + m.rho * (cu * (R(3) + R(4.5) * cu) - uu15));
     }
 }
 
@@ -68,8 +72,8 @@ LB_DEV R guo_source(int i, const NodeMoments<St, R>& m, const R* F, R pre)
     return pre * R(St::w(i)) * (R(3) * (cF - uF) + R(9) * cu * cF);
 }
 
-// In-place collision of one node. Returns false if the density is not a positive
-// finite number (the caller raises the context's status flag).
+// In-place collision of one node (f holds the deviations delta). Returns false if
+// the density is not a positive finite number (the caller raises the status flag).
 template <class St, int COLL, bool FORCE, class R>
 LB_DEV bool collide(R* f, const R* F, R omega)
 {

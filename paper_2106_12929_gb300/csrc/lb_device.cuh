@@ -80,29 +80,65 @@ template <> struct Store<__half> {
     static constexpr bool shifted = true;
     LB_DEV static float load(const __half* p) { return __half2float(*p); }
     LB_DEV static void store(__half* p, float v) { *p = __float2half_rn(v); }
+    LB_DEV static void store(__half* p, double v) { *p = __double2half(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     using Real = float;
     static constexpr bool shifted = true;
     LB_DEV static float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     LB_DEV static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    LB_DEV static void store(__nv_bfloat16* p, double v) { *p = __double2bfloat16(v); }
 };
 
+// Collision arithmetic works on deviations from rest, delta_i = f_i - w_i: the
+// moment sums then add small numbers (rho - 1 = sum delta, j = sum c delta) and
+// FP32 keeps its relative precision. Unshifted storage converts on load/store;
+// shifted (half) storage holds delta itself.
 template <class St, class T>
 LB_DEV typename Store<T>::Real load_pop(const T* p, int i)
 {
     using R = typename Store<T>::Real;
     R v = Store<T>::load(p);
-    if constexpr (Store<T>::shifted) v += R(St::w(i));
+    if constexpr (!Store<T>::shifted) v -= R(St::w(i));
     return v;
 }
 
 template <class St, class T>
-LB_DEV void store_pop(T* p, int i, typename Store<T>::Real v)
+LB_DEV void store_pop(T* p, int i, typename Store<T>::Real delta)
 {
     using R = typename Store<T>::Real;
-    if constexpr (Store<T>::shifted) v -= R(St::w(i));
+    if constexpr (!Store<T>::shifted) delta += R(St::w(i));
+    Store<T>::store(p, delta);
+}
+
+// the stored value itself, unconverted (streaming without collision moves it as is)
+template <class St, class T>
+LB_DEV typename Store<T>::Real load_raw(const T* p, int)
+{
+    return Store<T>::load(p);
+}
+template <class St, class T>
+LB_DEV void store_raw(T* p, int, typename Store<T>::Real v)
+{
     Store<T>::store(p, v);
+}
+
+// FP64 value of the population f_i (for copies out of the library)
+template <class St, class T>
+LB_DEV double load_f64(const T* p, int i)
+{
+    double v = (double)Store<T>::load(p);
+    if constexpr (Store<T>::shifted) v += St::w(i);
+    return v;
+}
+// store f_i given in FP64 (the shift, if any, is taken in FP64 before rounding)
+template <class St, class T>
+LB_DEV void store_f64(T* p, int i, double f)
+{
+    using R = typename Store<T>::Real;
+    if constexpr (Store<T>::shifted) f -= St::w(i);
+    if constexpr (Store<T>::shifted || sizeof(R) == 8) Store<T>::store(p, f);
+    else Store<T>::store(p, (float)f);
 }
 
 // ----------------------------------------------------------------------------
@@ -143,7 +179,7 @@ LB_DEV Nbr make_nbr(const Geom& g, int x, int y, int z)
 // ----------------------------------------------------------------------------
 enum Mode { AB = 0, AA_EVEN = 1, AA_ODD = 2 };
 
-template <class St, int MODE, class T>
+template <class St, int MODE, bool RAW = false, class T>
 LB_DEV void load_node(const T* buf, const Geom& g, const Nbr& nb, int n, typename Store<T>::Real* f)
 {
 #pragma unroll
@@ -156,11 +192,13 @@ LB_DEV void load_node(const T* buf, const Geom& g, const Nbr& nb, int n, typenam
             src = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
             if constexpr (MODE == AA_ODD) slot = opp(i);
         }
-        f[i] = load_pop<St>(buf + (int64_t)slot * g.plane + src, slot);
+        const T* p = buf + (int64_t)slot * g.plane + src;
+        if constexpr (RAW) f[i] = load_raw<St>(p, slot);
+        else f[i] = load_pop<St>(p, slot);
     }
 }
 
-template <class St, int MODE, class T>
+template <class St, int MODE, bool RAW = false, class T>
 LB_DEV void store_node(T* buf, const Geom& g, const Nbr& nb, int n, const typename Store<T>::Real* f)
 {
 #pragma unroll
@@ -169,7 +207,27 @@ LB_DEV void store_node(T* buf, const Geom& g, const Nbr& nb, int n, const typena
         int slot = i;
         if constexpr (MODE == AA_EVEN) slot = opp(i);
         if constexpr (MODE == AA_ODD) dst = nb.node(g, St::c(i, 0), St::c(i, 1), St::c(i, 2));
-        store_pop<St>(buf + (int64_t)slot * g.plane + dst, slot, f[i]);
+        T* p = buf + (int64_t)slot * g.plane + dst;
+        if constexpr (RAW) store_raw<St>(p, slot, f[i]);
+        else store_pop<St>(p, slot, f[i]);
+    }
+}
+
+// FP64 populations of one node's pre-collision state (copies out of the library)
+template <class St, int MODE, class T>
+LB_DEV void load_node_f64(const T* buf, const Geom& g, const Nbr& nb, int n, double* f)
+{
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        int src;
+        int slot = i;
+        if constexpr (MODE == AA_EVEN) {
+            src = n;
+        } else {
+            src = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
+            if constexpr (MODE == AA_ODD) slot = opp(i);
+        }
+        f[i] = load_f64<St>(buf + (int64_t)slot * g.plane + src, slot);
     }
 }
 

@@ -61,26 +61,40 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     if (!id.valid) return;
     Nbr nb = make_nbr(g, id.x, id.y, id.z);
     R f[St::Q];
-    load_node<St, MODE>(src, g, nb, id.n, f);
+    constexpr bool RAW = COLL == NONE;  // streaming only: move the stored values untouched
+    load_node<St, MODE, RAW>(src, g, nb, id.n, f);
     R Fl[3] = {R(0), R(0), R(0)};
     if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
     bool ok = collide<St, COLL, FORCE>(f, Fl, omega);
-    store_node<St, MODE>(dst, g, nb, id.n, f);
+    store_node<St, MODE, RAW>(dst, g, nb, id.n, f);
     if (!ok) atomicOr(status, 1u);
 }
 
 // Write a natural-layout state value set into the buffer for the given mode:
 // AB keeps f*_i(x) at x (the next pull reads it from x + c_i), so the state
-// f_i(x) goes to x - c_i; AA (even parity) stores it in place.
+// f_i(x) goes to x - c_i; AA (even parity) stores it in place. Values are
+// deviations delta_i (store_state) or FP64 populations f_i (store_state_f64).
+template <class St, int MODE>
+LB_DEV int state_slot_node(const Geom& g, const Nbr& nb, int n, int i)
+{
+    if constexpr (MODE == AB) return nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
+    return n;
+}
+
 template <class St, int MODE, class T>
-LB_DEV void store_state(T* buf, const Geom& g, const Nbr& nb, int n, const typename Store<T>::Real* f)
+LB_DEV void store_state(T* buf, const Geom& g, const Nbr& nb, int n, const typename Store<T>::Real* d)
 {
 #pragma unroll
-    for (int i = 0; i < St::Q; ++i) {
-        int dst = n;
-        if constexpr (MODE == AB) dst = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
-        store_pop<St>(buf + (int64_t)i * g.plane + dst, i, f[i]);
-    }
+    for (int i = 0; i < St::Q; ++i)
+        store_pop<St>(buf + (int64_t)i * g.plane + state_slot_node<St, MODE>(g, nb, n, i), i, d[i]);
+}
+
+template <class St, int MODE, class T>
+LB_DEV void store_state_f64(T* buf, const Geom& g, const Nbr& nb, int n, const double* f)
+{
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i)
+        store_f64<St>(buf + (int64_t)i * g.plane + state_slot_node<St, MODE>(g, nb, n, i), i, f[i]);
 }
 
 // ------------------------------------------------------------------ init (K5)
@@ -93,7 +107,9 @@ __global__ void __launch_bounds__(128) k_init_eq(T* buf, Geom g, const void* rho
     Nbr nb = make_nbr(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     NodeMoments<St, R> m;
-    m.rho = (R)io_load(rho, f64, id.n);
+    const double r = io_load(rho, f64, id.n);
+    m.rho = (R)r;
+    m.rho1 = (R)(r - 1.0);
     m.ux = (R)io_load(u, f64, id.n);
     m.uy = (R)io_load(u, f64, N + id.n);
     m.uz = St::D == 3 ? (R)io_load(u, f64, 2 * N + id.n) : R(0);
@@ -111,24 +127,23 @@ __global__ void __launch_bounds__(128) k_set(T* buf, Geom g, const void* fin, in
     if (!id.valid) return;
     Nbr nb = make_nbr(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-    R f[St::Q];
+    double f[St::Q];
 #pragma unroll
-    for (int i = 0; i < St::Q; ++i) f[i] = (R)io_load(fin, f64, (int64_t)i * N + id.n);
-    store_state<St, MODE>(buf, g, nb, id.n, f);
+    for (int i = 0; i < St::Q; ++i) f[i] = io_load(fin, f64, (int64_t)i * N + id.n);
+    store_state_f64<St, MODE>(buf, g, nb, id.n, f);
 }
 
 template <class St, class T, int MODE>
 __global__ void __launch_bounds__(128) k_get(const T* buf, Geom g, void* fout, int f64)
 {
-    using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
     Nbr nb = make_nbr(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-    R f[St::Q];
-    load_node<St, MODE>(buf, g, nb, id.n, f);
+    double f[St::Q];
+    load_node_f64<St, MODE>(buf, g, nb, id.n, f);
 #pragma unroll
-    for (int i = 0; i < St::Q; ++i) io_store(fout, f64, (int64_t)i * N + id.n, (double)f[i]);
+    for (int i = 0; i < St::Q; ++i) io_store(fout, f64, (int64_t)i * N + id.n, f[i]);
 }
 
 // ------------------------------------------------------------------ moments (K3)

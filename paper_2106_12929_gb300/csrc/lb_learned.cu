@@ -1,6 +1,7 @@
 // Learned moment-space collision on D2Q9 (Eq. 5, Sec. 3.1), its discrete adjoint
 // with the network-parameter gradient, and the Eq. 6 training loss.
 //
+// Populations are handled as deviations delta_i = f_i - w_i (as in lb_collide.cuh).
 // Moment basis (Hermite, orthogonal under the weights w_i): 1, cx, cy,
 // cx^2 - 1/3, cx cy, cy^2 - 1/3 (stress rows), (cx^2 - 1/3) cy, cx (cy^2 - 1/3),
 // (cx^2 - 1/3)(cy^2 - 1/3) (higher rows; their equilibria vanish for the
@@ -78,7 +79,7 @@ LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
     s.pxx = pxx; s.pxy = pxy; s.pyy = pyy; s.g6 = g6; s.g7 = g7; s.g8 = g8;
     const R ux = s.m.ux, uy = s.m.uy;
     R I[kNetIn];
-    I[0] = s.m.rho - R(1);
+    I[0] = s.m.rho1;
     I[1] = R(3) * (ux * ux + uy * uy);
     I[2] = R(3) * (pxx + pyy);
     I[3] = R(9) * (pxx * pxx + R(2) * pxy * pxy + pyy * pyy);
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_learned_adjoint(const T* state, c
         } else {  // b3
             for (int q = 0; q < kAdjBlock; ++q) acc += sh.gz[q];
         }
-        out[o] = acc;
+        out[o] += acc;  // partials accumulate over the adjoint steps of one run
     }
 }
 

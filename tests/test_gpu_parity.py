@@ -78,9 +78,8 @@ def test_streaming_half_storage_moves_values_unchanged(name, storage):
     lat.set_populations(lbinputs.random_populations(w, N, seed=4))
     q0 = gpu_pops(lat)  # the quantised state
     lat.step(3)
-    ref = oracle.step(name, dims, 0.8, "none", q0, nsteps=3)
-    # a load/store round trip of a quantised value may move it by one FP32 rounding at most
-    assert werr(gpu_pops(lat), ref, w) < 1e-6
+    # streaming moves the stored values untouched
+    np.testing.assert_array_equal(gpu_pops(lat), oracle.step(name, dims, 0.8, "none", q0, nsteps=3))
 
 
 # ------------------------------------------------------------------ FP64 collision parity
