@@ -193,6 +193,31 @@ LB_API lb_status lb_step_adjoint(lb_ctx* ctx, const void* lambda_T, int64_t n, v
 LB_API lb_status lb_adam_update(float* theta, float* m, float* v, const float* grad, int64_t n, double lr, double b1,
                          double b2, double eps, int64_t t, void* stream);
 
+/* ------------------------------------------------------- without allocation ---- */
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory where they need the global sums: for instance code that
+ * has given all device memory to another framework's caching allocator, or a
+ * latency-critical loop in which cudaMalloc / cudaFree (which may synchronise the
+ * whole device) are not acceptable.
+ *
+ * Same sums as lb_reduce (out[0] = sum rho, out[1..3] = sum rho u, out[4] =
+ * (1/2N) sum |u|^2, out[5] = (1/2N) sum rho |u|^2, FP64, deterministic), but for a
+ * caller-owned pre-collision state f[Q][N] in natural layout on the current device,
+ * with an optional force F[d][N] (NULL = none) of the same type; mem must be
+ * LB_DEVICE_F64 or LB_DEVICE_F32. out is host memory. The work runs on cuda_stream
+ * (NULL = legacy default stream) and the call synchronises that stream.
+ *
+ * It needs no context and performs no device allocation: its per-block partial sums
+ * live in a fixed file-scope device array of the library (about 385 KB, held on every
+ * GPU that loads the library until the process exits), which limits the grid to
+ * N <= 33,554,432 nodes; larger grids are rejected with LB_ERR_ARG. The first call on
+ * a device looks up that array's device address (with that device current); make
+ * that first call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU (other streams or threads on the same device) race, so order
+ * them. Errors: LB_ERR_ARG (arguments, size), LB_ERR_CUDA. */
+LB_API lb_status lb_reduce_noalloc(lb_stencil stencil, const int64_t dims[3], const void* f, const void* F,
+                                   lb_mem mem, double out[6], void* cuda_stream);
+
 /* ------------------------------------------------------------------ info ---- */
 LB_API int64_t lb_num_nodes(const lb_ctx* ctx);
 LB_API int lb_q(const lb_ctx* ctx);

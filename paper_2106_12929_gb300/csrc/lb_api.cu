@@ -49,6 +49,10 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace lb {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace lb
+
 struct lb_ctx {
     int stencil = 0, Q = 9, D = 2;
     int64_t dims[3] = {1, 1, 1};

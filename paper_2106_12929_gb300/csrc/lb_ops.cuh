@@ -91,6 +91,9 @@ inline cudaError_t run_op(int stencil, const OpArgs& a)
     return table[stencil][a.storage](a);
 }
 
+// message returned by lb_last_error() on the calling thread (lb_api.cu)
+void set_last_error(const char* msg);
+
 // stencil-independent helpers (lb_aux.cu)
 cudaError_t reduce_final(const double* partials, int64_t nblocks, int width, double* out, cudaStream_t s);
 cudaError_t convert_copy(const void* src, int src_f64, void* dst, int dst_f64, int64_t n, int64_t src_stride,
