@@ -6,5 +6,6 @@ the Python binding over it. Importing it does not load the library; the first
 """
 from ._lib import LBError, load  # noqa: F401
 from .lattice import Lattice, adam_update  # noqa: F401
+from .autograd import lb_run  # noqa: F401
 
-__all__ = ["Lattice", "LBError", "adam_update", "load"]
+__all__ = ["Lattice", "LBError", "adam_update", "lb_run", "load"]

@@ -11,6 +11,10 @@ namespace lb {
 
 enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3 };
 
+// 1/x rounded to nearest (FP32: the hardware reciprocal with IEEE rounding, not a division)
+LB_DEV float recip(float x) { return __frcp_rn(x); }
+LB_DEV double recip(double x) { return 1.0 / x; }
+
 template <class St, class R>
 struct NodeMoments {
     R rho, ux, uy, uz;
@@ -35,7 +39,7 @@ LB_DEV NodeMoments<St, R> node_moments(const R* d, const R* F)
         if (St::D == 3) jz += R(0.5) * F[2];
     }
     const R rho = R(1) + rho1;
-    const R inv = R(1) / rho;
+    const R inv = recip(rho);
     return {rho, jx * inv, jy * inv, jz * inv, rho1};
 }
 
@@ -50,15 +54,24 @@ LB_DEV R cdotu(int i, R ux, R uy, R uz)
 }
 
 // f^eq_i - w_i, with f^eq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)   (c_s^2 = 1/3):
-// deq_i = w_i [(rho - 1) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]
+// deq_i = w_i [(rho - 1) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)].
+// Opposite velocities are stored as neighbours (i odd, i + 1) and share the even part
+// w (rho - 1) + w rho (4.5 (c.u)^2 - 1.5 u.u); the odd part 3 w rho c.u changes sign.
 template <class St, class R>
-LB_DEV void equilibrium(const NodeMoments<St, R>& m, R* deq)
+LB_DEV void equilibrium(const NodeMoments<St, R>& m, R* deq, R scale = R(1))
 {
+    // scale multiplies every deq_i (BGK passes omega and relaxes with one FMA per population)
     const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    const R sr1 = scale * m.rho1, sr = scale * m.rho;
+    deq[0] = R(St::w(0)) * (sr1 - sr * uu15);
 #pragma unroll
-    for (int i = 0; i < St::Q; ++i) {
-        R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
-        deq[i] = R(St::w(i)) * (m.rho1 + m.rho * (cu * (R(3) + R(4.5) * cu) - uu15));
+    for (int i = 1; i < St::Q; i += 2) {
+        const R w = R(St::w(i));
+        const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
+        const R even = w * sr1 + (w * sr) * (R(4.5) * cu * cu - uu15);
+        const R odd = (R(3) * w * sr) * cu;
+        deq[i] = even + odd;
+        deq[i + 1] = even - odd;
     }
 }
 
@@ -82,16 +95,19 @@ LB_DEV bool collide(R* f, const R* F, R omega)
     } else {
         NodeMoments<St, R> m = node_moments<St, FORCE>(f, F);
         R feq[St::Q];
-        equilibrium<St>(m, feq);
         const R pre = R(1) - R(0.5) * omega;
         if constexpr (COLL == BGK) {
+            // f* = (1 - omega) f + omega f^eq (+ S), with omega folded into the equilibrium
+            equilibrium<St>(m, feq, omega);
+            const R keep = R(1) - omega;
 #pragma unroll
             for (int i = 0; i < St::Q; ++i) {
-                R v = f[i] - omega * (f[i] - feq[i]);
+                R v = keep * f[i] + feq[i];
                 if constexpr (FORCE) v += guo_source<St>(i, m, F, pre);
                 f[i] = v;
             }
-        } else {  // REG: keep only the Hermite order <= 2 projection of f - f^eq
+        } else {
+            equilibrium<St>(m, feq);  // REG: keep only the Hermite order <= 2 projection of f - f^eq
             R pxx = R(0), pyy = R(0), pzz = R(0), pxy = R(0), pxz = R(0), pyz = R(0);
             R ax = R(0), ay = R(0), az = R(0);
 #pragma unroll

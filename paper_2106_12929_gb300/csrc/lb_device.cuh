@@ -141,6 +141,57 @@ LB_DEV void store_f64(T* p, int i, double f)
     else Store<T>::store(p, (float)f);
 }
 
+// Two x-adjacent values (nodes x0 and x0 + 1, x0 even) as one aligned vector access.
+template <class T> struct Pair2;
+template <> struct Pair2<double> {
+    LB_DEV static void load(const double* p, double& a, double& b) { double2 v = *(const double2*)p; a = v.x; b = v.y; }
+    LB_DEV static void store(double* p, double a, double b) { *(double2*)p = make_double2(a, b); }
+};
+template <> struct Pair2<float> {
+    LB_DEV static void load(const float* p, float& a, float& b) { float2 v = *(const float2*)p; a = v.x; b = v.y; }
+    LB_DEV static void store(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
+};
+template <> struct Pair2<__half> {
+    LB_DEV static void load(const __half* p, float& a, float& b)
+    {
+        const float2 v = __half22float2(*(const __half2*)p);
+        a = v.x;
+        b = v.y;
+    }
+    LB_DEV static void store(__half* p, float a, float b) { *(__half2*)p = __floats2half2_rn(a, b); }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    LB_DEV static void load(const __nv_bfloat16* p, float& a, float& b)
+    {
+        const float2 v = __bfloat1622float2(*(const __nv_bfloat162*)p);
+        a = v.x;
+        b = v.y;
+    }
+    LB_DEV static void store(__nv_bfloat16* p, float a, float b) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a, b); }
+};
+
+// deviations of two adjacent nodes from one vector load / into one vector store
+template <class St, class T>
+LB_DEV void load_pop2(const T* p, int i, typename Store<T>::Real& a, typename Store<T>::Real& b)
+{
+    using R = typename Store<T>::Real;
+    Pair2<T>::load(p, a, b);
+    if constexpr (!Store<T>::shifted) {
+        a -= R(St::w(i));
+        b -= R(St::w(i));
+    }
+}
+template <class St, class T>
+LB_DEV void store_pop2(T* p, int i, typename Store<T>::Real a, typename Store<T>::Real b)
+{
+    using R = typename Store<T>::Real;
+    if constexpr (!Store<T>::shifted) {
+        a += R(St::w(i));
+        b += R(St::w(i));
+    }
+    Pair2<T>::store(p, a, b);
+}
+
 // ----------------------------------------------------------------------------
 // Grid geometry and periodic neighbours of one node.
 // ----------------------------------------------------------------------------
@@ -149,22 +200,52 @@ struct Geom {
     int64_t plane;  // element stride between population planes (>= N, padded)
 };
 
-// Node coordinates and the wrapped +/-1 neighbours along each axis.
+// Node coordinates and the wrapped +/-1 neighbours along each axis, plus the byte
+// offsets of the populations around the node for an element size S: per thread the
+// three x positions, per block (uniform: y, z come from blockIdx) the nine rows.
+// A population access is then base + slot * plane_bytes + row + x: one add per load
+// instead of index arithmetic per direction.
 struct Nbr {
     int x[3], y[3], z[3];  // index 0: coordinate - 1, 1: coordinate, 2: coordinate + 1 (wrapped)
+    int64_t xo[3];         // x[k] * S
+    int64_t ro[3][3];      // (y[dy] + ny z[dz]) nx S
+    int64_t pb;            // plane * S
     LB_DEV int node(const Geom& g, int dx, int dy, int dz) const
     {
         return x[dx + 1] + g.nx * (y[dy + 1] + g.ny * z[dz + 1]);
     }
+    LB_DEV int64_t boff(int slot, int dx, int dy, int dz) const
+    {
+        return slot * pb + ro[dy + 1][dz + 1] + xo[dx + 1];
+    }
 };
 
+template <int S = 4>
 LB_DEV Nbr make_nbr(const Geom& g, int x, int y, int z)
 {
     Nbr n;
     n.x[0] = x == 0 ? g.nx - 1 : x - 1; n.x[1] = x; n.x[2] = x == g.nx - 1 ? 0 : x + 1;
     n.y[0] = y == 0 ? g.ny - 1 : y - 1; n.y[1] = y; n.y[2] = y == g.ny - 1 ? 0 : y + 1;
     n.z[0] = z == 0 ? g.nz - 1 : z - 1; n.z[1] = z; n.z[2] = z == g.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n.xo[k] = (int64_t)n.x[k] * S;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) n.ro[a][b] = ((int64_t)n.y[a] + (int64_t)g.ny * n.z[b]) * g.nx * S;
+    n.pb = g.plane * S;
     return n;
+}
+
+template <class T>
+LB_DEV const T* at(const T* buf, const Nbr& nb, int slot, int dx, int dy, int dz)
+{
+    return (const T*)((const char*)buf + nb.boff(slot, dx, dy, dz));
+}
+template <class T>
+LB_DEV T* at(T* buf, const Nbr& nb, int slot, int dx, int dy, int dz)
+{
+    return (T*)((char*)buf + nb.boff(slot, dx, dy, dz));
 }
 
 // ----------------------------------------------------------------------------
@@ -184,15 +265,9 @@ LB_DEV void load_node(const T* buf, const Geom& g, const Nbr& nb, int n, typenam
 {
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
-        int src;
-        int slot = i;
-        if constexpr (MODE == AA_EVEN) {
-            src = n;
-        } else {
-            src = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
-            if constexpr (MODE == AA_ODD) slot = opp(i);
-        }
-        const T* p = buf + (int64_t)slot * g.plane + src;
+        const int slot = (MODE == AA_ODD) ? opp(i) : i;
+        const int s = (MODE == AA_EVEN) ? 0 : -1;
+        const T* p = at(buf, nb, slot, s * St::c(i, 0), s * St::c(i, 1), s * St::c(i, 2));
         if constexpr (RAW) f[i] = load_raw<St>(p, slot);
         else f[i] = load_pop<St>(p, slot);
     }
@@ -203,11 +278,9 @@ LB_DEV void store_node(T* buf, const Geom& g, const Nbr& nb, int n, const typena
 {
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
-        int dst = n;
-        int slot = i;
-        if constexpr (MODE == AA_EVEN) slot = opp(i);
-        if constexpr (MODE == AA_ODD) dst = nb.node(g, St::c(i, 0), St::c(i, 1), St::c(i, 2));
-        T* p = buf + (int64_t)slot * g.plane + dst;
+        const int slot = (MODE == AA_EVEN) ? opp(i) : i;
+        const int s = (MODE == AA_ODD) ? 1 : 0;
+        T* p = at(buf, nb, slot, s * St::c(i, 0), s * St::c(i, 1), s * St::c(i, 2));
         if constexpr (RAW) store_raw<St>(p, slot, f[i]);
         else store_pop<St>(p, slot, f[i]);
     }
@@ -219,15 +292,9 @@ LB_DEV void load_node_f64(const T* buf, const Geom& g, const Nbr& nb, int n, dou
 {
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
-        int src;
-        int slot = i;
-        if constexpr (MODE == AA_EVEN) {
-            src = n;
-        } else {
-            src = nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2));
-            if constexpr (MODE == AA_ODD) slot = opp(i);
-        }
-        f[i] = load_f64<St>(buf + (int64_t)slot * g.plane + src, slot);
+        const int slot = (MODE == AA_ODD) ? opp(i) : i;
+        const int s = (MODE == AA_EVEN) ? 0 : -1;
+        f[i] = load_f64<St>(at(buf, nb, slot, s * St::c(i, 0), s * St::c(i, 1), s * St::c(i, 2)), slot);
     }
 }
 

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     R f[St::Q];
     constexpr bool RAW = COLL == NONE;  // streaming only: move the stored values untouched
     load_node<St, MODE, RAW>(src, g, nb, id.n, f);
@@ -68,6 +68,74 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     bool ok = collide<St, COLL, FORCE>(f, Fl, omega);
     store_node<St, MODE, RAW>(dst, g, nb, id.n, f);
     if (!ok) atomicOr(status, 1u);
+}
+
+// Two nodes per thread (x0 = 2 t and x0 + 1; nx even). An access whose x shift is 0
+// serves both nodes with one aligned vector load or store; a shift of -1 or +1 takes
+// two scalar accesses, the inner one at a fixed byte distance from the vector
+// address. Every AB store and every non-x-moving load is a vector access, which
+// halves the memory instructions and conversions per node.
+template <class St, class T, int COLL, bool FORCE, int MODE>
+__global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
+                                                     typename Store<T>::Real omega, unsigned* status)
+{
+    using R = typename Store<T>::Real;
+    constexpr int S = sizeof(T);
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int yy[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+    const int zz[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+    const int64_t xo_m = (int64_t)(x0 == 0 ? g.nx - 1 : x0 - 1) * S;       // x0 - 1
+    const int64_t xo_0 = (int64_t)x0 * S;                                    // x0 (x0 + 1 = xo_0 + S)
+    const int64_t xo_2 = (int64_t)(x0 + 2 == g.nx ? 0 : x0 + 2) * S;        // x0 + 2
+    const int64_t pb = g.plane * S;
+    auto row = [&](int dy, int dz) -> int64_t {
+        return ((int64_t)yy[dy + 1] + (int64_t)g.ny * zz[dz + 1]) * g.nx * S;
+    };
+    R f0[St::Q], f1[St::Q];
+    constexpr int ls = (MODE == AA_EVEN) ? 0 : -1;  // load shift along c_i
+    constexpr int ss = (MODE == AA_ODD) ? 1 : 0;    // store shift along c_i
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        const int slot = (MODE == AA_ODD) ? opp(i) : i;
+        const int sx = ls * St::c(i, 0);
+        const char* base = (const char*)src + slot * pb + row(ls * St::c(i, 1), ls * St::c(i, 2));
+        if (sx == 0) {
+            load_pop2<St>((const T*)(base + xo_0), slot, f0[i], f1[i]);
+        } else if (sx < 0) {
+            f0[i] = load_pop<St>((const T*)(base + xo_m), slot);
+            f1[i] = load_pop<St>((const T*)(base + xo_0), slot);
+        } else {
+            f0[i] = load_pop<St>((const T*)(base + xo_0 + S), slot);
+            f1[i] = load_pop<St>((const T*)(base + xo_2), slot);
+        }
+    }
+    R F0[3] = {R(0), R(0), R(0)}, F1[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) {
+        const int n0 = x0 + g.nx * (y + g.ny * z);
+        Pair2<R>::load(F + n0, F0[0], F1[0]);
+        Pair2<R>::load(F + g.plane + n0, F0[1], F1[1]);
+        if (St::D == 3) Pair2<R>::load(F + 2 * g.plane + n0, F0[2], F1[2]);
+    }
+    const bool ok0 = collide<St, COLL, FORCE>(f0, F0, omega);
+    const bool ok1 = collide<St, COLL, FORCE>(f1, F1, omega);
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        const int slot = (MODE == AA_EVEN) ? opp(i) : i;
+        const int sx = ss * St::c(i, 0);
+        char* base = (char*)dst + slot * pb + row(ss * St::c(i, 1), ss * St::c(i, 2));
+        if (sx == 0) {
+            store_pop2<St>((T*)(base + xo_0), slot, f0[i], f1[i]);
+        } else if (sx < 0) {
+            store_pop<St>((T*)(base + xo_m), slot, f0[i]);
+            store_pop<St>((T*)(base + xo_0), slot, f1[i]);
+        } else {
+            store_pop<St>((T*)(base + xo_0 + S), slot, f0[i]);
+            store_pop<St>((T*)(base + xo_2), slot, f1[i]);
+        }
+    }
+    if (!(ok0 && ok1)) atomicOr(status, 1u);
 }
 
 // Write a natural-layout state value set into the buffer for the given mode:
@@ -104,7 +172,7 @@ __global__ void __launch_bounds__(128) k_init_eq(T* buf, Geom g, const void* rho
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     NodeMoments<St, R> m;
     const double r = io_load(rho, f64, id.n);
@@ -125,7 +193,7 @@ __global__ void __launch_bounds__(128) k_set(T* buf, Geom g, const void* fin, in
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     double f[St::Q];
 #pragma unroll
@@ -138,7 +206,7 @@ __global__ void __launch_bounds__(128) k_get(const T* buf, Geom g, void* fout, i
 {
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     double f[St::Q];
     load_node_f64<St, MODE>(buf, g, nb, id.n, f);
@@ -154,7 +222,7 @@ __global__ void __launch_bounds__(128) k_moments(const T* buf, const typename St
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     R f[St::Q];
     load_node<St, MODE>(buf, g, nb, id.n, f);
@@ -204,7 +272,7 @@ __global__ void __launch_bounds__(128) k_reduce_partial(const T* buf, const type
     NodeIdx id = node_index(g);
     double v[6] = {0, 0, 0, 0, 0, 0};
     if (id.valid) {
-        Nbr nb = make_nbr(g, id.x, id.y, id.z);
+        Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
         R f[St::Q];
         load_node<St, MODE>(buf, g, nb, id.n, f);
         R Fl[3] = {R(0), R(0), R(0)};
@@ -231,7 +299,7 @@ __global__ void __launch_bounds__(128) k_adj_seed(const T* buf, const typename S
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     R f[St::Q];
     load_node<St, MODE>(buf, g, nb, id.n, f);
@@ -266,7 +334,7 @@ __global__ void __launch_bounds__(128) k_loss_energy(const T* buf, const typenam
     NodeIdx id = node_index(g);
     double v[1] = {0.0};
     if (id.valid) {
-        Nbr nb = make_nbr(g, id.x, id.y, id.z);
+        Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
         const int64_t N = (int64_t)g.nx * g.ny * g.nz;
         R f[St::Q];
         load_node<St, MODE>(buf, g, nb, id.n, f);
@@ -309,7 +377,7 @@ __global__ void __launch_bounds__(128) k_adj_step(const T* state, const typename
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
-    Nbr nb = make_nbr(g, id.x, id.y, id.z);
+    Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     R f[St::Q], mu[St::Q];
     load_node<St, AB>(state, g, nb, id.n, f);
 #pragma unroll
@@ -333,10 +401,23 @@ template <class St, class T, int COLL, bool FORCE>
 cudaError_t launch_update(const OpArgs& a)
 {
     using R = typename Store<T>::Real;
-    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
     const R* F = (const R*)a.F;
+    if (COLL != NONE && a.g.nx % 2 == 0) {
+        // two nodes per thread; 128 threads cover 256 x positions
+        const int pairs = a.g.nx / 2;
+        const dim3 bl(pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32, 1, 1);
+        const dim3 gr((pairs + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
+        if (a.mode == AB)
+            k_update_pair<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+        else if (a.mode == AA_EVEN)
+            k_update_pair<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+        else
+            k_update_pair<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+        return cudaGetLastError();
+    }
+    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
     if (a.mode == AB) k_update<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
     else if (a.mode == AA_EVEN)
         k_update<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);

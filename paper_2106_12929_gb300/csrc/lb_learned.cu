@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) k_learned_update(const T* src, T* dst, Ge
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= g.nx) return;
     const int y = blockIdx.y;
-    Nbr nb = make_nbr(g, x, y, 0);
+    Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
     const int n = x + g.nx * y;
     R f[9];
     load_node<D2Q9, MODE>(src, g, nb, n, f);
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_learned_adjoint(const T* state, c
         const R* W2 = W1 + kNetHidden * kNetIn + kNetHidden;
         const R* W3 = W2 + kNetHidden * kNetHidden + kNetHidden;
         const R* scale = W3 + kNetHidden + 1 + kNetIn;
-        Nbr nb = make_nbr(g, x, y, 0);
+        Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
         const int n = x + g.nx * y;
         R f[9], mu[9];
         load_node<D2Q9, AB>(state, g, nb, n, f);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128) k_eq6_u(const T* buf, Geom g, int mode, c
     double v[2] = {0.0, 0.0};
     if (x < g.nx) {
         const int64_t N = (int64_t)g.nx * g.ny;
-        Nbr nb = make_nbr(g, x, y, 0);
+        Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
         const int n = x + g.nx * y;
         R f[9];
         if (mode == AB) load_node<D2Q9, AB>(buf, g, nb, n, f);
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(128) k_eq6_seed(const T* buf, Geom g, int mode
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= g.nx) return;
     const int64_t N = (int64_t)g.nx * g.ny;
-    Nbr nb = make_nbr(g, x, y, 0);
+    Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
     const int n = x + g.nx * y;
     R f[9];
     if (mode == AB) load_node<D2Q9, AB>(buf, g, nb, n, f);

@@ -16,7 +16,10 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 STENCILS = ["D2Q9", "D3Q19", "D3Q27"]
-TINY = {"D2Q9": [(5, 4, 1), (7, 3, 1), (33, 5, 1)], "D3Q19": [(5, 4, 3), (7, 6, 5)], "D3Q27": [(5, 4, 3), (7, 6, 5)]}
+# odd nx runs the one-node-per-thread kernel, even nx the two-nodes-per-thread one
+TINY = {"D2Q9": [(5, 4, 1), (6, 5, 1), (33, 5, 1), (2, 3, 1), (258, 3, 1)],
+        "D3Q19": [(5, 4, 3), (6, 5, 3), (7, 6, 5), (2, 3, 3)],
+        "D3Q27": [(5, 4, 3), (4, 5, 3), (7, 6, 5), (2, 2, 3)]}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -89,7 +92,7 @@ def test_streaming_half_storage_moves_values_unchanged(name, storage):
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_collision_fp64_matches_oracle(name, coll, forced, layout):
     d, c, w, _ = oracle.stencil(name)
-    for dims in TINY[name][:2]:
+    for dims in TINY[name][:4]:
         N = oracle.n_nodes(dims)
         f0 = near_eq(name, dims, seed=11)
         F = lbinputs.random_field((d, N), seed=12, amp=1e-3) if forced else None
@@ -107,11 +110,12 @@ def test_collision_fp64_matches_oracle(name, coll, forced, layout):
 
 
 @pytest.mark.parametrize("name", STENCILS)
-def test_aa_matches_ab_bit_exact(name):
+@pytest.mark.parametrize("which", [0, 1, 3])
+def test_aa_matches_ab_bit_exact(name, which):
     d, c, w, _ = oracle.stencil(name)
-    dims = TINY[name][1]
+    dims = TINY[name][which]
     f0 = near_eq(name, dims, seed=21)
-    for storage in ["f64", "f32"]:
+    for storage in ["f64", "f32", "f16"]:
         a = L(name, dims, 0.6, "bgk", storage=storage, layout="ab")
         b = L(name, dims, 0.6, "bgk", storage=storage, layout="aa")
         a.set_populations(f0)
@@ -447,3 +451,48 @@ def test_full_size_d3q19_256_sampled(layout):
     r = lat.reduce()
     assert abs(r[0] / n ** 3 - rho.mean()) <= 1e-6
     assert np.max(np.abs(r[1:4])) / n ** 3 <= 1e-7
+
+
+# ------------------------------------------------------------------ torch.autograd
+def test_autograd_force_gradient_matches_oracle():
+    from paper_2106_12929_gb300 import Lattice, lb_run
+    name = "D2Q9"
+    dims, rho, u = lbinputs.shear_layer(32, u0=0.05)
+    N = 32 * 32
+    tau = 0.6
+    F0 = lbinputs.smooth_force(dims, 1e-4, seed=3)
+    et = lbinputs.random_field(N, 4, amp=1e-4) + 1e-3
+    lat = Lattice(name, dims, tau, "bgk", storage="f64", record_every=4)
+    F = torch.tensor(F0, device="cuda", requires_grad=True)
+    r, v = lb_run(lat, torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"), 10, F=F)
+    e = 0.5 * r * (v * v).sum(0)
+    loss = ((e - torch.tensor(et, device="cuda")) ** 2).sum()
+    loss.backward()
+    f0 = oracle.init_eq(name, dims, rho, u)
+    fN = oracle.step(name, dims, tau, "bgk", f0, nsteps=10, F=F0)
+    L_o, lam_o, gF_o = oracle.loss_energy(name, dims, fN, et, F=F0)
+    _, gF_adj, _ = oracle.adjoint(name, dims, tau, "bgk", f0, 10, lam_o, F=F0)
+    ref = gF_o + gF_adj
+    assert abs(loss.item() - L_o) <= 1e-12 * L_o
+    assert np.max(np.abs(F.grad.cpu().numpy() - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_autograd_network_gradient_matches_oracle():
+    from paper_2106_12929_gb300 import Lattice, lb_run
+    dims, rho, u = lbinputs.shear_layer(24, u0=0.05)
+    N = 24 * 24
+    tau = 0.6
+    net = _net(tau, seed=9)
+    lat = Lattice("D2Q9", dims, tau, "learned", storage="f64", record_every=3)
+    theta = torch.tensor(net[:793], device="cuda", requires_grad=True)
+    extra = torch.tensor(net[793:], device="cuda")
+    wu = lbinputs.random_field((2, N), 5)
+    r, v = lb_run(lat, torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"), 7, theta=theta,
+                  net_extra=extra)
+    loss = (v * torch.tensor(wu, device="cuda")).sum()
+    loss.backward()
+    f0 = oracle.init_eq("D2Q9", dims, rho, u)
+    fN = oracle.step("D2Q9", dims, tau, "learned", f0, nsteps=7, mlp=net)
+    lamN, _ = oracle.seed_moments("D2Q9", dims, fN, None, wu)
+    _, _, gth = oracle.adjoint("D2Q9", dims, tau, "learned", f0, 7, lamN, mlp=net)
+    assert np.max(np.abs(theta.grad.cpu().numpy() - gth)) <= 1e-10 * np.max(np.abs(gth))
