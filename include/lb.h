@@ -186,6 +186,24 @@ LB_API lb_status lb_loss_eq6(lb_ctx* ctx, const void* u_ref, const void* w_ref, 
 LB_API lb_status lb_step_adjoint(lb_ctx* ctx, const void* lambda_T, int64_t n, void* lambda_0, void* grad_F,
                           void* grad_theta, lb_mem mem);
 
+/* The six inputs of the learned collision's network at every node of the current
+ * D2Q9 state, before standardisation (Sec. 3.1 "local moments"; see lb_set_mlp):
+ * I[0] = rho - 1, I[1] = |u|^2/c_s^2, I[2] = tr Pi/c_s^2, I[3] = Pi:Pi/c_s^4,
+ * I[4] = u.Pi.u/c_s^4, I[5] = sum of the squared higher (ghost) moments over their
+ * weighted norms; Pi = sum c c (f - f^eq). Layout I[6][N]. Any collision kind. */
+LB_API lb_status lb_learned_inputs(lb_ctx* ctx, void* I, lb_mem mem);
+
+/* Coarse-graining used to build training data (Sec. 3.1: the fine trajectory is
+ * mapped onto a grid with half the resolution): the coarse context's state becomes
+ * f^eq(rho_c, u_c), where rho_c and rho_c u_c are the means of rho and rho u over each
+ * 2 x 2 (x 2) block of the fine context's current state. Same velocity set, fine
+ * dims = 2 x coarse dims, one device. Resets the coarse step counter and recording. */
+LB_API lb_status lb_coarsen_into(const lb_ctx* fine, lb_ctx* coarse);
+
+/* Vorticity w[N] = (v(x+1) - v(x-1))/2 - (u(y+1) - u(y-1))/2 of the current D2Q9 state
+ * (the Eq. 6 vorticity, second-order central differences on the periodic grid). */
+LB_API lb_status lb_vorticity(lb_ctx* ctx, void* w, lb_mem mem);
+
 /* One Adam update of n parameters in device memory (FP32):
  * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
  * theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). t >= 1 is the step

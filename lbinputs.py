@@ -164,6 +164,13 @@ def smooth_force(dims, amplitude: float, seed: int, modes: int = 4):
     return F
 
 
+def smooth_scalar(dims, mean: float, rel_amp: float, seed: int, modes: int = 4):
+    """Seeded smooth positive scalar field mean * (1 + rel_amp * s(x)), s a sum of the lowest
+    Fourier modes scaled to max |s| = 1 (used as a target field of a loss)."""
+    s = smooth_force(dims, 1.0, seed, modes)[0]
+    return mean * (1.0 + rel_amp * s)
+
+
 def random_moments(dims, seed: int, u_amp: float = 0.05, rho_amp: float = 0.02):
     """Seeded random (rho, u) fields: rho = 1 + rho_amp r, u = u_amp r', r uniform in [-1, 1]."""
     nx, ny, nz = (int(v) for v in dims)

@@ -67,6 +67,9 @@ _SIGNATURES = {
     "lb_loss_energy": (_INT, [_P, _P, ctypes.POINTER(_D), _P, _P, _INT]),
     "lb_loss_eq6": (_INT, [_P, _P, _P, _D, ctypes.POINTER(_D), _P, _INT]),
     "lb_step_adjoint": (_INT, [_P, _P, _I64, _P, _P, _P, _INT]),
+    "lb_coarsen_into": (_INT, [_P, _P]),
+    "lb_learned_inputs": (_INT, [_P, _P, _INT]),
+    "lb_vorticity": (_INT, [_P, _P, _INT]),
     "lb_adam_update": (_INT, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I64, _P]),
     "lb_reduce_noalloc": (_INT, [_INT, ctypes.POINTER(_I64), _P, _P, _INT, ctypes.POINTER(_D), _P]),
     "lb_num_nodes": (_I64, [_P]),

@@ -763,6 +763,95 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     return LB_OK;
 }
 
+lb_status lb_coarsen_into(const lb_ctx* fine_c, lb_ctx* c)
+{
+    lb_ctx* f = const_cast<lb_ctx*>(fine_c);
+    lb_status s = check_ctx(f);
+    if (s != LB_OK) return s;
+    if ((s = check_ctx(c)) != LB_OK) return s;
+    if (f->stencil != c->stencil) return fail(LB_ERR_ARG, "coarsening needs the same velocity set");
+    if (f->device != c->device) return fail(LB_ERR_ARG, "coarsening needs both contexts on one device");
+    for (int a = 0; a < f->D; ++a)
+        if (f->dims[a] != 2 * c->dims[a]) return fail(LB_ERR_ARG, "fine dims must be twice the coarse dims");
+    DeviceGuard guard(c->device);
+    // work on the fine context's stream, then order the coarse stream after it
+    double *rf = nullptr, *uf = nullptr, *rc = nullptr, *uc = nullptr;
+    cudaStream_t st = f->stream;
+    LB_CUDA(c, cudaMallocAsync((void**)&rf, (size_t)(f->N * 8), st), "coarsen scratch");
+    LB_CUDA(c, cudaMallocAsync((void**)&uf, (size_t)(f->N * f->D * 8), st), "coarsen scratch");
+    LB_CUDA(c, cudaMallocAsync((void**)&rc, (size_t)(c->N * 8), st), "coarsen scratch");
+    LB_CUDA(c, cudaMallocAsync((void**)&uc, (size_t)(c->N * c->D * 8), st), "coarsen scratch");
+    lb::OpArgs a = base_args(f, lb::OP_MOMENTS);
+    a.out0 = rf;
+    a.out1 = uf;
+    a.io_f64 = 1;
+    if ((s = launch(f, a, "coarsen moments")) != LB_OK) return s;
+    LB_CUDA(c, lb::coarsen2(rf, uf, (int)f->dims[0], (int)f->dims[1], (int)f->dims[2], f->D, rc, uc, st), "coarsen");
+    f->launches += 1;
+    if (c->stream != st) {
+        cudaEvent_t ev;
+        LB_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "coarsen event");
+        LB_CUDA(c, cudaEventRecord(ev, st), "coarsen event");
+        LB_CUDA(c, cudaStreamWaitEvent(c->stream, ev, 0), "coarsen event");
+        cudaEventDestroy(ev);
+    }
+    c->aa_parity = 0;
+    c->state = c->ab[0];
+    lb::OpArgs b = base_args(c, lb::OP_INIT_EQ);
+    b.dst = c->state;
+    b.in0 = rc;
+    b.in1 = uc;
+    b.io_f64 = 1;
+    if ((s = launch(c, b, "coarse init")) != LB_OK) return s;
+    reset_recording(c);
+    if (c->stream != st) LB_CUDA(c, cudaStreamSynchronize(c->stream), "coarsen sync");
+    cudaFreeAsync(rf, st);
+    cudaFreeAsync(uf, st);
+    cudaFreeAsync(rc, st);
+    cudaFreeAsync(uc, st);
+    return LB_OK;
+}
+
+lb_status lb_vorticity(lb_ctx* c, void* w, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (c->stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "vorticity is provided for D2Q9");
+    if (!w || !mem_valid(m)) return fail(LB_ERR_ARG, "w and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    double* u = nullptr;
+    LB_CUDA(c, cudaMallocAsync((void**)&u, (size_t)(c->N * 2 * 8), c->stream), "vorticity scratch");
+    lb::OpArgs a = base_args(c, lb::OP_MOMENTS);
+    a.out0 = nullptr;
+    a.out1 = u;
+    a.io_f64 = 1;
+    if ((s = launch(c, a, "vorticity moments")) != LB_OK) return s;
+    Staged sw;
+    if ((s = stage_out_alloc(c, sw, w, c->N, m, false, "vorticity")) != LB_OK) return s;
+    LB_CUDA(c, lb::vorticity2d(u, (int)c->dims[0], (int)c->dims[1], sw.dev, mem_f64(m), c->stream), "vorticity");
+    c->launches += 1;
+    cudaFreeAsync(u, c->stream);
+    return stage_out_finish(c, sw, w, "vorticity");
+}
+
+lb_status lb_learned_inputs(lb_ctx* c, void* I, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (c->stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "the learned collision's inputs are defined for D2Q9");
+    if (!I || !mem_valid(m)) return fail(LB_ERR_ARG, "I and a valid lb_mem are required");
+    DeviceGuard guard(c->device);
+    Staged so;
+    if ((s = stage_out_alloc(c, so, I, 6 * c->N, m, false, "inputs")) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_MOMENTS);
+    a.out0 = so.dev;
+    a.io_f64 = mem_f64(m);
+    cudaError_t e = lb::learned_inputs_d2q9(a);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned inputs");
+    return stage_out_finish(c, so, I, "inputs");
+}
+
 lb_status lb_adam_update(float* theta, float* mm, float* v, const float* g, int64_t n, double lr, double b1, double b2,
                          double eps, int64_t t, void* stream)
 {

@@ -82,4 +82,64 @@ cudaError_t adam_update(float* theta, float* m, float* v, const float* grad, int
     return cudaGetLastError();
 }
 
+// Block average by 2 in every axis of a grid with even extents: per coarse node the
+// mean density and the mean momentum of its 2^d fine nodes; u_c = mean(rho u) / mean(rho).
+// Fine and coarse arrays are FP64, component-major, x fastest.
+__global__ void k_coarsen2(const double* rho_f, const double* u_f, int nxf, int nyf, int nzf, int d, double* rho_c,
+                           double* u_c)
+{
+    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf > 1 ? nzf / 2 : 1;
+    const int64_t Nc = (int64_t)nxc * nyc * nzc, Nf = (int64_t)nxf * nyf * nzf;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < Nc; n += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(n % nxc), Y = (int)((n / nxc) % nyc), Z = (int)(n / ((int64_t)nxc * nyc));
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        const int zc = nzf > 1 ? 2 : 1;
+        for (int c = 0; c < zc; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    const int64_t m = (2 * X + a) + (int64_t)nxf * ((2 * Y + b) + (int64_t)nyf * (zc * Z + c));
+                    const double rf = rho_f[m];
+                    r += rf;
+                    for (int k = 0; k < d; ++k) j[k] += rf * u_f[k * Nf + m];
+                }
+        rho_c[n] = r / (double)(4 * zc);
+        for (int k = 0; k < d; ++k) u_c[k * Nc + n] = j[k] / r;
+    }
+}
+
+cudaError_t coarsen2(const double* rho_f, const double* u_f, int nxf, int nyf, int nzf, int d, double* rho_c,
+                     double* u_c, cudaStream_t s)
+{
+    const int64_t Nc = (int64_t)(nxf / 2) * (nyf / 2) * (nzf > 1 ? nzf / 2 : 1);
+    int64_t blocks = (Nc + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_coarsen2<<<(unsigned)blocks, 256, 0, s>>>(rho_f, u_f, nxf, nyf, nzf, d, rho_c, u_c);
+    return cudaGetLastError();
+}
+
+// 2D vorticity w = (v(x+1) - v(x-1))/2 - (u(y+1) - u(y-1))/2 of a velocity field u[2][N]
+// (FP64) on a periodic nx x ny grid, written as FP64 or FP32.
+__global__ void k_vorticity2d(const double* u, int nx, int ny, void* w, int w_f64)
+{
+    const int64_t N = (int64_t)nx * ny;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        const int xp = x == nx - 1 ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+        const double v = 0.5 * (u[N + xp + (int64_t)nx * y] - u[N + xm + (int64_t)nx * y]) -
+                         0.5 * (u[x + (int64_t)nx * yp] - u[x + (int64_t)nx * ym]);
+        if (w_f64) ((double*)w)[n] = v;
+        else ((float*)w)[n] = (float)v;
+    }
+}
+
+cudaError_t vorticity2d(const double* u, int nx, int ny, void* w, int w_f64, cudaStream_t s)
+{
+    const int64_t N = (int64_t)nx * ny;
+    int64_t blocks = (N + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_vorticity2d<<<(unsigned)blocks, 256, 0, s>>>(u, nx, ny, w, w_f64);
+    return cudaGetLastError();
+}
+
 }  // namespace lb

@@ -50,17 +50,10 @@ struct LearnedNode {
     R z, ez, omg;
 };
 
+// Moments, equilibrium, stress and higher moments, and the six network inputs of one node.
 template <class R>
-LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
+LB_DEV void learned_inputs(const R* f, LearnedNode<R>& s, R* I)
 {
-    const R* W1 = net.v;
-    const R* b1 = W1 + kNetHidden * kNetIn;
-    const R* W2 = b1 + kNetHidden;
-    const R* b2 = W2 + kNetHidden * kNetHidden;
-    const R* W3 = b2 + kNetHidden;
-    const R* b3 = W3 + kNetHidden;
-    const R* shift = b3 + 1;
-    const R* scale = shift + kNetIn;
     R Fz[3] = {R(0), R(0), R(0)};
     s.m = node_moments<D2Q9, false>(f, Fz);
     equilibrium<D2Q9>(s.m, s.feq);
@@ -78,13 +71,27 @@ LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
     }
     s.pxx = pxx; s.pxy = pxy; s.pyy = pyy; s.g6 = g6; s.g7 = g7; s.g8 = g8;
     const R ux = s.m.ux, uy = s.m.uy;
-    R I[kNetIn];
     I[0] = s.m.rho1;
     I[1] = R(3) * (ux * ux + uy * uy);
     I[2] = R(3) * (pxx + pyy);
     I[3] = R(9) * (pxx * pxx + R(2) * pxy * pxy + pyy * pyy);
     I[4] = R(9) * (ux * ux * pxx + R(2) * ux * uy * pxy + uy * uy * pyy);
     I[5] = g6 * g6 * R(1.0 / kN6) + g7 * g7 * R(1.0 / kN7) + g8 * g8 * R(1.0 / kN8);
+}
+
+template <class R>
+LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
+{
+    const R* W1 = net.v;
+    const R* b1 = W1 + kNetHidden * kNetIn;
+    const R* W2 = b1 + kNetHidden;
+    const R* b2 = W2 + kNetHidden * kNetHidden;
+    const R* W3 = b2 + kNetHidden;
+    const R* b3 = W3 + kNetHidden;
+    const R* shift = b3 + 1;
+    const R* scale = shift + kNetIn;
+    R I[kNetIn];
+    learned_inputs(f, s, I);
 #pragma unroll
     for (int k = 0; k < kNetIn; ++k) s.x[k] = (I[k] - shift[k]) * scale[k];
 #pragma unroll
@@ -145,6 +152,49 @@ __global__ void __launch_bounds__(128) k_learned_update(const T* src, T* dst, Ge
     learned_post(s, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
+}
+
+// the six network inputs of every node of the current state: I[k][N]
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_learned_inputs(const T* buf, Geom g, void* out, int f64)
+{
+    using R = typename Store<T>::Real;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y;
+    Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
+    const int n = x + g.nx * y;
+    const int64_t N = (int64_t)g.nx * g.ny;
+    R f[9];
+    load_node<D2Q9, MODE>(buf, g, nb, n, f);
+    LearnedNode<R> s;
+    R I[kNetIn];
+    learned_inputs(f, s, I);
+    for (int k = 0; k < kNetIn; ++k) {
+        if (f64) ((double*)out)[k * N + n] = (double)I[k];
+        else ((float*)out)[k * N + n] = (float)I[k];
+    }
+}
+
+template <class T>
+static cudaError_t launch_inputs(const OpArgs& a)
+{
+    const dim3 bl(128, 1, 1), gr((a.g.nx + 127) / 128, a.g.ny, 1);
+    if (a.mode == AB) k_learned_inputs<T, AB><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.out0, a.io_f64);
+    else if (a.mode == AA_EVEN) k_learned_inputs<T, AA_EVEN><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.out0, a.io_f64);
+    else k_learned_inputs<T, AA_ODD><<<gr, bl, 0, a.stream>>>((const T*)a.src, a.g, a.out0, a.io_f64);
+    return cudaGetLastError();
+}
+
+cudaError_t learned_inputs_d2q9(const OpArgs& a)
+{
+    switch (a.storage) {
+    case S_F64: return launch_inputs<double>(a);
+    case S_F32: return launch_inputs<float>(a);
+    case S_F16: return launch_inputs<__half>(a);
+    case S_BF16: return launch_inputs<__nv_bfloat16>(a);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------- adjoint

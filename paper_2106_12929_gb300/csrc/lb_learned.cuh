@@ -14,6 +14,8 @@ static_assert(kNetTheta == 793, "6-24-24-1 network has 793 parameters");
 // forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
 // net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint)
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net);
+// out[6][N] <- the six network inputs (moment invariants) of every node of the state a.src
+cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // number of blocks of the learned adjoint launch (rows of the gradient partials)
 int64_t learned_adj_partial_count(const Geom& g);
 // out[793] (+)= sum over blocks of partials[block][793]

@@ -98,6 +98,9 @@ void set_last_error(const char* msg);
 cudaError_t reduce_final(const double* partials, int64_t nblocks, int width, double* out, cudaStream_t s);
 cudaError_t convert_copy(const void* src, int src_f64, void* dst, int dst_f64, int64_t n, int64_t src_stride,
                          int64_t dst_stride, int rows, int accumulate, cudaStream_t s);
+cudaError_t coarsen2(const double* rho_f, const double* u_f, int nxf, int nyf, int nzf, int d, double* rho_c,
+                     double* u_c, cudaStream_t s);
+cudaError_t vorticity2d(const double* u, int nx, int ny, void* w, int w_f64, cudaStream_t s);
 cudaError_t adam_update(float* theta, float* m, float* v, const float* grad, int64_t n, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t s);
 

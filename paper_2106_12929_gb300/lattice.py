@@ -171,6 +171,22 @@ class Lattice:
         _lib.check(self._lib.lb_reduce(self._h, out), "lb_reduce")
         return np.array(list(out))
 
+    def coarsen_from(self, fine: "Lattice"):
+        """This (coarse) lattice's state <- f^eq of the 2x block-averaged moments of `fine`."""
+        _lib.check(self._lib.lb_coarsen_into(fine._h, self._h), "lb_coarsen_into")
+        return self
+
+    def vorticity(self, dtype=torch.float64, device=None) -> torch.Tensor:
+        w = self._out((self.N,), dtype, device)
+        _lib.check(self._lib.lb_vorticity(self._h, w.data_ptr(), _mem_code(w)), "lb_vorticity")
+        return w
+
+    def learned_inputs(self, dtype=torch.float64, device=None) -> torch.Tensor:
+        """The six (unstandardised) network inputs of every node, [6, N]."""
+        out = self._out((6, self.N), dtype, device)
+        _lib.check(self._lib.lb_learned_inputs(self._h, out.data_ptr(), _mem_code(out)), "lb_learned_inputs")
+        return out
+
     # ------------------------------------------------------------------ adjoint
     def adjoint_seed_moments(self, grad_rho, grad_u, grad_F=None, dtype=None, device=None):
         gu = _to_tensor(grad_u)
