@@ -51,7 +51,7 @@ class TrainConfig:
     spinup: int = 4000          # fine steps before the first snapshot
     snap_every: int = 400       # fine steps between snapshots
     n_snap: int = 16
-    holdout: int = 4            # last snapshots, never trained on
+    holdout: int = 4            # last snapshots: test set; the `holdout` before them: validation
     horizon: int = 100          # coarse steps per rollout
     batch: int = 4
     iters: int = 300
@@ -92,7 +92,7 @@ def make_shear_data(cfg: TrainConfig):
     fine.check()
     # standardisation of the network inputs from the coarse snapshots
     stats = []
-    for s in samples[: cfg.n_snap - cfg.holdout]:
+    for s in samples[: cfg.n_snap - 2 * cfg.holdout]:
         tmp.init_from_moments(s.rho0.double(), s.u0.double())
         tmp.step(5)
         stats.append(tmp.learned_inputs(torch.float64, "cuda"))
@@ -130,8 +130,10 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
         samples, extra = make_shear_data(cfg)
     nc = cfg.n_fine // 2
     tau_c = coarse_tau(cfg.tau_fine)
-    train_set = samples[: len(samples) - cfg.holdout]
-    hold = samples[len(samples) - cfg.holdout:]
+    n = len(samples)
+    train_set = samples[: n - 2 * cfg.holdout]
+    val = samples[n - 2 * cfg.holdout: n - cfg.holdout]   # early stopping
+    hold = samples[n - cfg.holdout:]                       # reported gain, never used for choices
     theta = init_theta(tau_c, cfg.seed)
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
@@ -140,8 +142,10 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
     hist = {"train_loss": [], "holdout_loss": []}
     lat.set_mlp(torch.cat([theta, extra]))
     base_hold = mean_loss(lat, hold, cfg.horizon)
+    base_val = mean_loss(lat, val, cfg.horizon)
     hist["holdout_loss"].append((0, base_hold))
-    best = (base_hold, 0, theta.clone())  # early stopping on the held-out loss
+    hist["val_loss"] = [(0, base_val)]
+    best = (base_val, 0, theta.clone())  # early stopping on the validation loss
     t0 = time.perf_counter()
     for it in range(1, cfg.iters + 1):
         lat.set_mlp(torch.cat([theta, extra]))
@@ -155,11 +159,13 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
         if it % max(1, cfg.iters // 20) == 0 or it == cfg.iters:
             lat.set_mlp(torch.cat([theta, extra]))
             hl = mean_loss(lat, hold, cfg.horizon)
+            vl = mean_loss(lat, val, cfg.horizon)
             hist["holdout_loss"].append((it, hl))
-            if hl < best[0]:
-                best = (hl, it, theta.clone())
+            hist["val_loss"].append((it, vl))
+            if vl < best[0]:
+                best = (vl, it, theta.clone())
             if log:
-                log(f"iter {it}: train {hist['train_loss'][-1]:.4e} holdout {hl:.4e} (BGK {base_hold:.4e})")
+                log(f"iter {it}: train {hist['train_loss'][-1]:.4e} val {vl:.4e} test {hl:.4e} (BGK {base_hold:.4e})")
     torch.cuda.synchronize()
     hist["train_seconds"] = time.perf_counter() - t0
     theta = best[2]

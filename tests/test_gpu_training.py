@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 def test_training_reduces_holdout_loss_below_bgk():
     from paper_2106_12929_gb300 import build, training
     build.build()
-    cfg = training.TrainConfig(n_fine=256, tau_fine=0.503, spinup=1500, snap_every=100, n_snap=12, holdout=3,
+    cfg = training.TrainConfig(n_fine=256, tau_fine=0.503, spinup=1500, snap_every=100, n_snap=14, holdout=3,
                                horizon=40, batch=4, iters=80, lr=0.05, record_every=10)
     theta, extra, hist = training.train(cfg, log=print)
     print({k: v for k, v in hist.items() if k != "train_loss"})
