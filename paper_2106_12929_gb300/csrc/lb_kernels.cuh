@@ -396,6 +396,76 @@ __global__ void __launch_bounds__(128) k_adj_step(const T* state, const typename
     }
 }
 
+// Two nodes per thread (x0 = 2 t, x0 + 1; nx even), the access pattern of k_update_pair:
+// the state is pulled from x - c_i, the adjoints from x + c_i; accesses whose x shift is 0
+// are one aligned vector load / store for both nodes.
+template <class St, class T, int COLL, bool FORCE>
+__global__ void __launch_bounds__(128) k_adj_step_pair(const T* state, const typename Store<T>::Real* F,
+                                                       const typename Store<T>::Real* lam_in,
+                                                       typename Store<T>::Real* lam_out,
+                                                       typename Store<T>::Real* gF, Geom g,
+                                                       typename Store<T>::Real omega)
+{
+    using R = typename Store<T>::Real;
+    constexpr int S = sizeof(T), SR = sizeof(R);
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int yy[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+    const int zz[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+    const int xm = x0 == 0 ? g.nx - 1 : x0 - 1, x2 = x0 + 2 == g.nx ? 0 : x0 + 2;
+    auto row = [&](int dy, int dz) -> int64_t { return (int64_t)yy[dy + 1] + (int64_t)g.ny * zz[dz + 1]; };
+    R f0[St::Q], f1[St::Q], m0[St::Q], m1[St::Q];
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        const int cx = St::c(i, 0);
+        // state: f_i(x) = buf_i(x - c_i)
+        const char* b = (const char*)state + (int64_t)i * g.plane * S + row(-St::c(i, 1), -St::c(i, 2)) * g.nx * S;
+        if (cx == 0) {
+            load_pop2<St>((const T*)(b + (int64_t)x0 * S), i, f0[i], f1[i]);
+        } else if (cx > 0) {
+            f0[i] = load_pop<St>((const T*)(b + (int64_t)xm * S), i);
+            f1[i] = load_pop<St>((const T*)(b + (int64_t)x0 * S), i);
+        } else {
+            f0[i] = load_pop<St>((const T*)(b + (int64_t)(x0 + 1) * S), i);
+            f1[i] = load_pop<St>((const T*)(b + (int64_t)x2 * S), i);
+        }
+        // adjoints: mu_i(x) = lambda_i(x + c_i)
+        const R* l = lam_in + (int64_t)i * g.plane + row(St::c(i, 1), St::c(i, 2)) * g.nx;
+        if (cx == 0) {
+            Pair2<R>::load(l + x0, m0[i], m1[i]);
+        } else if (cx > 0) {
+            m0[i] = l[x0 + 1];
+            m1[i] = l[x2];
+        } else {
+            m0[i] = l[xm];
+            m1[i] = l[x0];
+        }
+    }
+    (void)SR;
+    const int64_t n0 = x0 + (int64_t)g.nx * (y + (int64_t)g.ny * z);
+    R F0[3] = {R(0), R(0), R(0)}, F1[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) {
+        Pair2<R>::load(F + n0, F0[0], F1[0]);
+        Pair2<R>::load(F + g.plane + n0, F0[1], F1[1]);
+        if (St::D == 3) Pair2<R>::load(F + 2 * g.plane + n0, F0[2], F1[2]);
+    }
+    R g0[3], g1[3];
+    adjoint_node<St, COLL, FORCE>(f0, F0, m0, omega, g0);
+    adjoint_node<St, COLL, FORCE>(f1, F1, m1, omega, g1);
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) Pair2<R>::store(lam_out + (int64_t)i * g.plane + n0, m0[i], m1[i]);
+    if constexpr (FORCE) {
+#pragma unroll
+        for (int a = 0; a < St::D; ++a) {
+            R* p = gF + a * g.plane + n0;
+            R a0, a1;
+            Pair2<R>::load(p, a0, a1);
+            Pair2<R>::store(p, a0 + g0[a], a1 + g1[a]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <class St, class T, int COLL, bool FORCE>
 cudaError_t launch_update(const OpArgs& a)
@@ -464,6 +534,19 @@ template <class St, class T, int COLL>
 cudaError_t launch_adj(const OpArgs& a)
 {
     using R = typename Store<T>::Real;
+    if (a.g.nx % 2 == 0) {
+        const int pairs = a.g.nx / 2;
+        const dim3 bl(pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32, 1, 1);
+        const dim3 gr((pairs + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
+        if (a.force)
+            k_adj_step_pair<St, T, COLL, true><<<gr, bl, 0, a.stream>>>((const T*)a.src, (const R*)a.F,
+                                                                        (const R*)a.lam_in, (R*)a.lam_out, (R*)a.gF,
+                                                                        a.g, (R)a.omega);
+        else
+            k_adj_step_pair<St, T, COLL, false><<<gr, bl, 0, a.stream>>>((const T*)a.src, nullptr, (const R*)a.lam_in,
+                                                                         (R*)a.lam_out, nullptr, a.g, (R)a.omega);
+        return cudaGetLastError();
+    }
     const dim3 gr = node_grid(a.g), bl = node_block(a.g);
     if (a.force)
         k_adj_step<St, T, COLL, true><<<gr, bl, 0, a.stream>>>((const T*)a.src, (const R*)a.F, (const R*)a.lam_in,

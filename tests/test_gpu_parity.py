@@ -268,7 +268,11 @@ def test_learned_with_bgk_network_equals_bgk():
 @pytest.mark.parametrize("name,dims,coll,forced", [
     ("D2Q9", (9, 7, 1), "bgk", True), ("D2Q9", (9, 7, 1), "regularized", True),
     ("D3Q19", (5, 4, 3), "bgk", True), ("D3Q27", (5, 4, 3), "regularized", False),
-    ("D2Q9", (9, 7, 1), "none", False)])
+    ("D2Q9", (9, 7, 1), "none", False),
+    # even nx: the two-nodes-per-thread adjoint kernel
+    ("D2Q9", (8, 7, 1), "bgk", True), ("D2Q9", (2, 3, 1), "regularized", True),
+    ("D3Q19", (6, 4, 3), "regularized", True), ("D3Q27", (4, 4, 3), "bgk", True),
+    ("D2Q9", (10, 3, 1), "none", False)])
 def test_adjoint_fp64_matches_oracle(name, dims, coll, forced):
     d, c, w, _ = oracle.stencil(name)
     N = oracle.n_nodes(dims)
