@@ -170,6 +170,10 @@ def run_only(args):
         print(json.dumps({"only": "adjoint", **adjoint_ratio(torch.cuda.current_stream(), n=args.grid or 1024,
                                                              steps=args.steps)}))
         return
+    if args.only == "learned":
+        print(json.dumps({"only": "learned", **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
+                                                                  steps=args.steps)}))
+        return
     stencil, storage, layout = ONLY[args.only]
     dims, tau, rho, u = tgv_workload(args.grid or N_GRID)
     N = int(np.prod(dims))
@@ -337,6 +341,47 @@ def adjoint_ratio(stream, n=1024, steps=500, k=50):
     return res
 
 
+LEARNED_FLOP_PER_LU = 2 * (6 * 24 + 24 * 24 + 24) + 200  # network MACs x 2 + moments / invariants / collision
+
+
+def learned_throughput(stream, n=2048, steps=200):
+    """Learned collision (Eq. 5, D2Q9, FP32) on n^2 decaying turbulence: GLUPS of the forward
+    step and of the adjoint step with the parameter gradient."""
+    import torch
+    from paper_2106_12929_gb300 import Lattice
+    dims = (n, n, 1)
+    rho, u = lbinputs.random_spectrum_velocity(dims, 12.0, 0.05, 30000)
+    tau = 0.5 + 3.0 * 0.05 * (n / (2.0 * math.pi)) / 30000.0
+    th = lbinputs.random_mlp_params(7, out_bias=math.log(tau - 0.5), out_scale=0.5)
+    net = np.concatenate([th, np.zeros(6), np.array([400.0, 100.0, 1e3, 1e6, 1e6, 1e6])])
+    lat = Lattice("D2Q9", dims, tau, "learned", storage="f32", record_every=10)
+    lat.set_mlp(net)
+    lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    lat.step(5)
+    t = time_steps(lat, steps, stream)
+    fwd = n * n * steps / t / 1e9
+    # adjoint: recorded run of k steps, then the backward pass
+    k = 50
+    lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    lat.step(k)
+    lam = torch.zeros((9, n * n), dtype=torch.float32, device="cuda")
+    lam[0] = 1.0
+    gth = torch.zeros(793, dtype=torch.float32, device="cuda")
+    lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)  # allocates the buffers
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bwd = e0.elapsed_time(e1) / 1e3
+    lat.close()
+    return {"grid": [n, n], "forward_glups": round(fwd, 3),
+            "forward_tflops": round(fwd * LEARNED_FLOP_PER_LU / 1e3, 2),
+            "backward_ms_per_step": round(bwd / k * 1e3, 4),
+            "forward_ms_per_step": round(n * n / fwd / 1e9 * 1e3, 4)}
+
+
 def cpu_baseline(sample_steps: int = 1):
     """The FP64 CPU oracle on this host, on a bounded sample of the same workload: the full
     256^3 D3Q19 grid for `sample_steps` step(s)."""
@@ -390,7 +435,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint"]), default=None,
+    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned"]), default=None,
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     args = ap.parse_args()

@@ -32,8 +32,17 @@ LB_HD constexpr double h7(int i) { return c2(i, 0) * (c2(i, 1) * c2(i, 1) - 1.0 
 LB_HD constexpr double h8(int i) { return (c2(i, 0) * c2(i, 0) - 1.0 / 3.0) * (c2(i, 1) * c2(i, 1) - 1.0 / 3.0); }
 constexpr double kN6 = 2.0 / 27.0, kN7 = 2.0 / 27.0, kN8 = 4.0 / 81.0;
 
+// Activation: in FP32 the hardware tanh (PTX tanh.approx.f32, one SFU instruction,
+// max relative error about 2^-11) -- the forward pass, the adjoint (which uses
+// 1 - tanh^2 of the same values) and training all see the same function. FP64 keeps
+// the accurate tanh for the gradient checks against the oracle.
 template <class R> LB_DEV R act_tanh(R a);
-template <> LB_DEV float act_tanh<float>(float a) { return tanhf(a); }
+template <> LB_DEV float act_tanh<float>(float a)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
 template <> LB_DEV double act_tanh<double>(double a) { return tanh(a); }
 template <class R> LB_DEV R act_exp(R a);
 template <> LB_DEV float act_exp<float>(float a) { return expf(a); }
