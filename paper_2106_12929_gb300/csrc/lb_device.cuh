@@ -170,6 +170,42 @@ template <> struct Pair2<__nv_bfloat16> {
     LB_DEV static void store(__nv_bfloat16* p, float a, float b) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a, b); }
 };
 
+// Four x-adjacent half-precision values (x0 % 4 == 0) as one aligned 8-byte access.
+template <class T> struct Quad4;
+template <> struct Quad4<__half> {
+    LB_DEV static void load(const __half* p, float* v)
+    {
+        const uint2 r = *(const uint2*)p;
+        const float2 a = __half22float2(*(const __half2*)&r.x), b = __half22float2(*(const __half2*)&r.y);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    LB_DEV static void store(__half* p, const float* v)
+    {
+        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+        uint2 r;
+        r.x = *(const unsigned*)&a;
+        r.y = *(const unsigned*)&b;
+        *(uint2*)p = r;
+    }
+};
+template <> struct Quad4<__nv_bfloat16> {
+    LB_DEV static void load(const __nv_bfloat16* p, float* v)
+    {
+        const uint2 r = *(const uint2*)p;
+        const float2 a = __bfloat1622float2(*(const __nv_bfloat162*)&r.x);
+        const float2 b = __bfloat1622float2(*(const __nv_bfloat162*)&r.y);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    LB_DEV static void store(__nv_bfloat16* p, const float* v)
+    {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 r;
+        r.x = *(const unsigned*)&a;
+        r.y = *(const unsigned*)&b;
+        *(uint2*)p = r;
+    }
+};
+
 // deviations of two adjacent nodes from one vector load / into one vector store
 template <class St, class T>
 LB_DEV void load_pop2(const T* p, int i, typename Store<T>::Real& a, typename Store<T>::Real& b)

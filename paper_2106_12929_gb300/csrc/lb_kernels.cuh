@@ -138,6 +138,85 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
     if (!(ok0 && ok1)) atomicOr(status, 1u);
 }
 
+// Four nodes per thread for the half-precision (shifted) storage types (x0 = 4 t, nx % 4 == 0).
+// Half storage moves half the bytes of FP32 with the same instruction count per node, so it
+// runs out of issue slots before HBM bandwidth; four nodes per 8-byte access cut the memory
+// instructions and conversions per node again. An access with x shift 0 is one vector for all
+// four nodes; a load shifted by -1 or +1 takes the vector at x0 (three of its values) plus
+// one scalar; a shifted store is four scalar stores.
+template <class St, class T, int COLL, bool FORCE, int MODE>
+__global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const float* F, Geom g, float omega,
+                                                     unsigned* status)
+{
+    static_assert(Store<T>::shifted, "four-node kernel is for half-precision storage");
+    constexpr int S = sizeof(T);
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int yy[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+    const int zz[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+    const int64_t xo_m = (int64_t)(x0 == 0 ? g.nx - 1 : x0 - 1) * S;  // x0 - 1
+    const int64_t xo_0 = (int64_t)x0 * S;                              // x0 .. x0 + 3
+    const int64_t xo_4 = (int64_t)(x0 + 4 == g.nx ? 0 : x0 + 4) * S;  // x0 + 4
+    const int64_t pb = g.plane * S;
+    auto row = [&](int dy, int dz) -> int64_t {
+        return ((int64_t)yy[dy + 1] + (int64_t)g.ny * zz[dz + 1]) * g.nx * S;
+    };
+    float f[4][St::Q];
+    constexpr int ls = (MODE == AA_EVEN) ? 0 : -1;
+    constexpr int ss = (MODE == AA_ODD) ? 1 : 0;
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        const int slot = (MODE == AA_ODD) ? opp(i) : i;
+        const int sx = ls * St::c(i, 0);
+        const char* base = (const char*)src + slot * pb + row(ls * St::c(i, 1), ls * St::c(i, 2));
+        float v[4];
+        Quad4<T>::load((const T*)(base + xo_0), v);
+        if (sx == 0) {
+            f[0][i] = v[0]; f[1][i] = v[1]; f[2][i] = v[2]; f[3][i] = v[3];
+        } else if (sx < 0) {
+            f[0][i] = Store<T>::load((const T*)(base + xo_m));
+            f[1][i] = v[0]; f[2][i] = v[1]; f[3][i] = v[2];
+        } else {
+            f[0][i] = v[1]; f[1][i] = v[2]; f[2][i] = v[3];
+            f[3][i] = Store<T>::load((const T*)(base + xo_4));
+        }
+    }
+    float Fl[4][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if constexpr (FORCE) {
+        const int64_t n0 = x0 + (int64_t)g.nx * (y + (int64_t)g.ny * z);
+#pragma unroll
+        for (int a = 0; a < St::D; ++a) {
+            const float4 q = *(const float4*)(F + a * g.plane + n0);
+            Fl[0][a] = q.x; Fl[1][a] = q.y; Fl[2][a] = q.z; Fl[3][a] = q.w;
+        }
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ok = collide<St, COLL, FORCE>(f[k], Fl[k], omega) && ok;
+#pragma unroll
+    for (int i = 0; i < St::Q; ++i) {
+        const int slot = (MODE == AA_EVEN) ? opp(i) : i;
+        const int sx = ss * St::c(i, 0);
+        char* base = (char*)dst + slot * pb + row(ss * St::c(i, 1), ss * St::c(i, 2));
+        if (sx == 0) {
+            const float v[4] = {f[0][i], f[1][i], f[2][i], f[3][i]};
+            Quad4<T>::store((T*)(base + xo_0), v);
+        } else if (sx < 0) {
+            Store<T>::store((T*)(base + xo_m), f[0][i]);
+            Store<T>::store((T*)(base + xo_0), f[1][i]);
+            Store<T>::store((T*)(base + xo_0 + S), f[2][i]);
+            Store<T>::store((T*)(base + xo_0 + 2 * S), f[3][i]);
+        } else {
+            Store<T>::store((T*)(base + xo_0 + S), f[0][i]);
+            Store<T>::store((T*)(base + xo_0 + 2 * S), f[1][i]);
+            Store<T>::store((T*)(base + xo_0 + 3 * S), f[2][i]);
+            Store<T>::store((T*)(base + xo_4), f[3][i]);
+        }
+    }
+    if (!ok) atomicOr(status, 1u);
+}
+
 // Write a natural-layout state value set into the buffer for the given mode:
 // AB keeps f*_i(x) at x (the next pull reads it from x + c_i), so the state
 // f_i(x) goes to x - c_i; AA (even parity) stores it in place. Values are
@@ -474,6 +553,23 @@ cudaError_t launch_update(const OpArgs& a)
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
     const R* F = (const R*)a.F;
+    if constexpr (Store<T>::shifted) {
+        if (COLL != NONE && a.g.nx % 4 == 0) {
+            // four nodes per thread for half storage
+            const int quads = a.g.nx / 4;
+            const dim3 bl(quads >= 128 ? 128 : ((quads + 31) / 32) * 32, 1, 1);
+            const dim3 gr((quads + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
+            if (a.mode == AB)
+                k_update_quad<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+            else if (a.mode == AA_EVEN)
+                k_update_quad<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega,
+                                                                                     a.status);
+            else
+                k_update_quad<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega,
+                                                                                    a.status);
+            return cudaGetLastError();
+        }
+    }
     if (COLL != NONE && a.g.nx % 2 == 0) {
         // two nodes per thread; 128 threads cover 256 x positions
         const int pairs = a.g.nx / 2;
