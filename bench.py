@@ -40,8 +40,8 @@ U0 = 0.1 / math.sqrt(3.0)
 RE = 1600.0
 Q19 = 19
 BYTES_PER_LU = {  # algorithmic bytes per lattice update: read Q + write Q populations (+ force read)
-    ("D3Q19", "f32"): 2 * 19 * 4, ("D3Q19", "f16"): 2 * 19 * 2, ("D3Q19", "bf16"): 2 * 19 * 2,
-    ("D3Q19", "f64"): 2 * 19 * 8, ("D2Q9", "f32"): 2 * 9 * 4,
+    (st, sto): 2 * q * b for st, q in (("D2Q9", 9), ("D3Q19", 19), ("D3Q27", 27))
+    for sto, b in (("f64", 8), ("f32", 4), ("f16", 2), ("bf16", 2))
 }
 # DRAM traffic per launch of the D3Q19 FP32 AB stream-collide kernel at 256^3 from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
@@ -119,14 +119,22 @@ def dist_info():
     return world, rank, local
 
 
-def max_over_ranks(value: float, world: int):
+def max_over_ranks(value: float, world: int, device: str = "cuda"):
+    """Maximum of a per-rank value over all ranks (the slowest replica sets the time)."""
     if world <= 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(nodes_per_rank: int, steps: int, seconds_this_rank: float, world: int, device: str = "cuda"):
+    """Whole-job lattice updates per second: every rank advances its own replica of
+    nodes_per_rank nodes for `steps` steps; the job takes as long as the slowest rank."""
+    t = max_over_ranks(seconds_this_rank, world, device)
+    return world * nodes_per_rank * steps / t, t
 
 
 def barrier(world: int):
@@ -154,10 +162,24 @@ def tgv_workload(n=N_GRID):
     return dims, tau, rho, u
 
 
-ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout)
-    "ab_f32": ("D3Q19", "f32", "ab"), "aa_f32": ("D3Q19", "f32", "aa"), "ab_f16": ("D3Q19", "f16", "ab"),
-    "ab_bf16": ("D3Q19", "bf16", "ab"), "aa_f16": ("D3Q19", "f16", "aa"), "ab_f64": ("D3Q19", "f64", "ab"),
+ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, collision)
+    "ab_f32": ("D3Q19", "f32", "ab", "bgk"), "aa_f32": ("D3Q19", "f32", "aa", "bgk"),
+    "ab_f16": ("D3Q19", "f16", "ab", "bgk"), "ab_bf16": ("D3Q19", "bf16", "ab", "bgk"),
+    "aa_f16": ("D3Q19", "f16", "aa", "bgk"), "ab_f64": ("D3Q19", "f64", "ab", "bgk"),
+    "d3q27_reg_f32": ("D3Q27", "f32", "ab", "regularized"), "d3q27_reg_f16": ("D3Q27", "f16", "ab", "regularized"),
+    "d2q9_f32": ("D2Q9", "f32", "ab", "bgk"), "d2q9_f16": ("D2Q9", "f16", "ab", "bgk"),
 }
+
+
+def workload(stencil: str, n: int | None):
+    """(dims, tau, rho, u) of the benchmark flow of a velocity set: 3D Taylor-Green vortex
+    (Re 1600, Ma 0.1) for the 3D sets at n^3 (default 256), 2D Taylor-Green vortex
+    (u0 = 0.05, tau = 0.8) for D2Q9 at n^2 (default 4096)."""
+    if stencil == "D2Q9":
+        n = n or 4096
+        dims, rho, u = lbinputs.taylor_green_2d(n, u0=0.05)
+        return dims, 0.8, rho, u
+    return tgv_workload(n or N_GRID)
 
 
 def run_only(args):
@@ -174,10 +196,10 @@ def run_only(args):
         print(json.dumps({"only": "learned", **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
                                                                   steps=args.steps)}))
         return
-    stencil, storage, layout = ONLY[args.only]
-    dims, tau, rho, u = tgv_workload(args.grid or N_GRID)
+    stencil, storage, layout, coll = ONLY[args.only]
+    dims, tau, rho, u = workload(stencil, args.grid)
     N = int(np.prod(dims))
-    lat = Lattice(stencil, dims, tau, "bgk", storage=storage, layout=layout)
+    lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     lat.step(args.warmup)
     t = time_steps(lat, args.steps, torch.cuda.current_stream())
@@ -217,8 +239,8 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = lat.launch_count() - launches0
     lat.check()
-    t_max = max_over_ranks(t, world)
-    glups = world * N * args.steps / t_max / 1e9
+    lups, t_max = job_throughput(N, args.steps, t, world)
+    glups = lups / 1e9
 
     # roofline of the dominant kernel (one stream-collide launch per step)
     per_launch = t / args.steps
@@ -299,6 +321,17 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
             g * BYTES_PER_LU[("D3Q19", storage)] / measured_peak_hbm()[0], 4)
         lat.close()
     out["f16_over_f32_glups"] = round(out["d3q19_f16_ab_glups"] / glups_ab, 3)
+    for key in ("d3q27_reg_f32", "d3q27_reg_f16", "d2q9_f32", "d2q9_f16"):
+        st, sto, lay, coll = ONLY[key]
+        dims2, tau2, r2, u2 = workload(st, None)
+        lat = Lattice(st, dims2, tau2, coll, storage=sto, layout=lay)
+        lat.init_from_moments(torch.tensor(r2, device="cuda"), torch.tensor(u2, device="cuda"))
+        lat.step(4)
+        t = time_steps(lat, k, stream)
+        g = int(np.prod(dims2)) * k / t / 1e9
+        out[f"{key}_glups"] = round(g, 3)
+        out[f"{key}_hbm_frac"] = round(g * BYTES_PER_LU[(st, sto)] / measured_peak_hbm()[0], 4)
+        lat.close()
     out.update(adjoint_ratio(stream))
     return out
 

@@ -1,0 +1,49 @@
+"""The multi-GPU path of bench.py runs independent replicas (the lattice Boltzmann step
+needs no exchange between them): the job time is the maximum over ranks and the value
+counts every rank's updates. Checked with two gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    w, r, _ = bench.dist_info()
+    assert (w, r) == (world, rank)
+    seconds = [2.0, 3.0][rank]  # rank 1 is the slow replica
+    lups, t = bench.job_throughput(1000, 10, seconds, world, device="cpu")
+    out[rank] = (lups, t)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank():
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    for r in range(2):
+        lups, t = out[r]
+        assert t == pytest.approx(3.0)
+        assert lups == pytest.approx(2 * 1000 * 10 / 3.0)
