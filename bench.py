@@ -192,9 +192,9 @@ def run_only(args):
         print(json.dumps({"only": "adjoint", **adjoint_ratio(torch.cuda.current_stream(), n=args.grid or 1024,
                                                              steps=args.steps)}))
         return
-    if args.only == "learned":
-        print(json.dumps({"only": "learned", **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
-                                                                  steps=args.steps)}))
+    if args.only in ("learned", "learned_tc"):
+        print(json.dumps({"only": args.only, **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
+                                                                  steps=args.steps, tc=args.only == "learned_tc")}))
         return
     stencil, storage, layout, coll = ONLY[args.only]
     dims, tau, rho, u = workload(stencil, args.grid)
@@ -333,6 +333,11 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
         out[f"{key}_hbm_frac"] = round(g * BYTES_PER_LU[(st, sto)] / measured_peak_hbm()[0], 4)
         lat.close()
     out.update(adjoint_ratio(stream))
+    for tc in (False, True):
+        r = learned_throughput(stream, n=2048, steps=100, tc=tc)
+        key = "learned_tc" if tc else "learned_f32"
+        out[f"{key}_forward_glups"] = r["forward_glups"]
+        out[f"{key}_backward_ms_per_step"] = r["backward_ms_per_step"]
     return out
 
 
@@ -377,7 +382,7 @@ def adjoint_ratio(stream, n=1024, steps=500, k=50):
 LEARNED_FLOP_PER_LU = 2 * (6 * 24 + 24 * 24 + 24) + 200  # network MACs x 2 + moments / invariants / collision
 
 
-def learned_throughput(stream, n=2048, steps=200):
+def learned_throughput(stream, n=2048, steps=200, tc=False):
     """Learned collision (Eq. 5, D2Q9, FP32) on n^2 decaying turbulence: GLUPS of the forward
     step and of the adjoint step with the parameter gradient."""
     import torch
@@ -387,7 +392,7 @@ def learned_throughput(stream, n=2048, steps=200):
     tau = 0.5 + 3.0 * 0.05 * (n / (2.0 * math.pi)) / 30000.0
     th = lbinputs.random_mlp_params(7, out_bias=math.log(tau - 0.5), out_scale=0.5)
     net = np.concatenate([th, np.zeros(6), np.array([400.0, 100.0, 1e3, 1e6, 1e6, 1e6])])
-    lat = Lattice("D2Q9", dims, tau, "learned", storage="f32", record_every=10)
+    lat = Lattice("D2Q9", dims, tau, "learned", storage="f32", record_every=10, learned_tc=tc)
     lat.set_mlp(net)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     lat.step(5)
@@ -468,7 +473,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned"]), default=None,
+    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned", "learned_tc"]), default=None,
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     args = ap.parse_args()

@@ -92,9 +92,13 @@ typedef struct {
                              and returns LB_ERR_UNSTABLE if a node went bad; 0 (default) = never */
     int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
                              lb_step_adjoint can run backwards (AB layout only); 0 = off */
+    int learned_tc;       /* learned collision, FP32/FP16/BF16 storage: 1 = evaluate the network's two
+                             hidden layers on the tensor cores with BF16 operands and FP32
+                             accumulation (an inference option: lb_step_adjoint and training use
+                             the FP32 network); 0 (default) = FP32 arithmetic throughout */
 } lb_options;
 
-/* Fill *opt with the defaults listed above. */
+/* Fill *opt with the defaults listed above (learned_tc = 0). */
 LB_API void lb_default_options(lb_options* opt);
 
 /* Create a context: validate, allocate the population buffer(s) on opt->device and

@@ -69,6 +69,7 @@ struct lb_ctx {
     int aa_parity = 0;                 // AA: 0 natural (even), 1 odd
     void* F = nullptr;                 // force [D][plane], arithmetic type
     std::vector<double> net;           // learned network (805 values), passed to kernels by value
+    void* tc_table = nullptr;          // learned_tc: packed BF16 weight fragments on the device
     unsigned* status = nullptr;
     double* partials = nullptr;
     int64_t partials_cap = 0;
@@ -141,6 +142,7 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     a.omega = c->omega;
     a.status = c->status;
     a.stream = c->stream;
+    a.tc_table = c->tc_table;
     return a;
 }
 
@@ -148,7 +150,7 @@ lb_status launch(lb_ctx* c, const lb::OpArgs& a, const char* what)
 {
     cudaError_t e;
     if (a.coll == LB_LEARNED_MRT && (a.op == lb::OP_UPDATE || a.op == lb::OP_ADJ_STEP))
-        e = lb::run_learned_d2q9(a, c->net.data());
+        e = lb::run_learned_d2q9(a, c->net.data(), a.op == lb::OP_UPDATE && c->opt.learned_tc);
     else
         e = lb::run_op(c->stencil, a);
     c->launches += 1;
@@ -259,6 +261,7 @@ void lb_default_options(lb_options* o)
     o->device = -1;
     o->check_every = 0;
     o->record_every = 0;
+    o->learned_tc = 0;
 }
 
 lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau, lb_collision coll,
@@ -276,6 +279,9 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if ((int)o.storage < 0 || (int)o.storage > 3) return fail(LB_ERR_ARG, "unknown storage %d", (int)o.storage);
     if ((int)o.layout < 0 || (int)o.layout > 1) return fail(LB_ERR_ARG, "unknown layout %d", (int)o.layout);
     if (o.check_every < 0 || o.record_every < 0) return fail(LB_ERR_ARG, "negative check_every / record_every");
+    if (o.learned_tc != 0 && o.learned_tc != 1) return fail(LB_ERR_ARG, "learned_tc must be 0 or 1");
+    if (o.learned_tc && (coll != LB_LEARNED_MRT || o.storage == LB_F64))
+        return fail(LB_ERR_UNSUPPORTED, "learned_tc needs the learned collision with FP32 or half storage");
     const int D = stencil == LB_D2Q9 ? 2 : 3;
     for (int a = 0; a < 3; ++a)
         if (dims[a] < 1 || dims[a] > 65535) return fail(LB_ERR_ARG, "dims[%d] = %lld out of [1, 65535]", a, (long long)dims[a]);
@@ -340,7 +346,7 @@ void lb_destroy(lb_ctx* c)
     if (!c) return;
     DeviceGuard guard(c->device);
     cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
+    void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
                     c->gF, c->gtheta};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -423,6 +429,15 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
         v[(size_t)k] = f64 ? ((const double*)tmp.data())[k] : (double)((const float*)tmp.data())[k];
     for (double x : v)
         if (!std::isfinite(x)) return fail(LB_ERR_ARG, "network values must be finite");
+    if (c->opt.learned_tc) {
+        const size_t bytes = lb::learned_tc_table_bytes();
+        if (!c->tc_table && (s = alloc(c, &c->tc_table, (int64_t)bytes, "tensor-core weight table")) != LB_OK) return s;
+        std::vector<unsigned char> tab(bytes);
+        lb::learned_tc_pack(v.data(), tab.data());
+        // the previous table may still be read by queued steps: order the copy on the stream
+        LB_CUDA(c, cudaMemcpyAsync(c->tc_table, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream), "weight table");
+        LB_CUDA(c, cudaStreamSynchronize(c->stream), "weight table");
+    }
     c->net.swap(v);
     return LB_OK;
 }

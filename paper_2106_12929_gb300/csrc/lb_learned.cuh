@@ -13,7 +13,12 @@ static_assert(kNetTheta == 793, "6-24-24-1 network has 793 parameters");
 
 // forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
 // net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint)
-cudaError_t run_learned_d2q9(const OpArgs& a, const double* net);
+// tc = 1: forward step with the network's hidden layers on the tensor cores (BF16 x BF16 -> FP32)
+cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc = false);
+// Network weights for the tensor-core path, packed once per lb_set_mlp into a device table:
+// bytes needed, and the host-side packing into `out` (learned_tc_table_bytes() bytes).
+size_t learned_tc_table_bytes();
+void learned_tc_pack(const double* net, void* out);
 // out[6][N] <- the six network inputs (moment invariants) of every node of the state a.src
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // number of blocks of the learned adjoint launch (rows of the gradient partials)

@@ -42,6 +42,7 @@ struct OpArgs {
     void* lam_out = nullptr;        // adjoint: lambda^n
     void* gF = nullptr;             // adjoint: force gradient accumulator [D][plane], arithmetic type
     void* gth = nullptr;            // learned adjoint: per-block network-gradient partials
+    const void* tc_table = nullptr; // learned collision on tensor cores: packed weight table (device)
     Geom g{};
     double omega = 1.0;
     unsigned* status = nullptr;

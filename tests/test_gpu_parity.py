@@ -528,3 +528,28 @@ def test_half_storage_four_node_kernel(name, dims, storage):
         dev = np.max(np.abs(ref - w[:, None]) / w[:, None])
         tol = (2e-3 if storage == "f16" else 2e-2) * dev
         assert werr(gpu_pops(a), ref, w) <= tol
+
+
+# ------------------------------------------------------------------ learned collision on tensor cores
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_learned_tensor_core_option(storage):
+    name = "D2Q9"
+    dims = (130, 40, 1)  # two blocks of 128 lanes per row, the second one ragged
+    rho, u = lbinputs.random_moments(dims, seed=7, u_amp=0.05)
+    d, c, w, _ = oracle.stencil(name)
+    tau = 0.6
+    # zero output layer: z = b3 in both paths, so they differ only by FP32 rounding (which can
+    # flip a half-precision rounding: a few FP16 ulps); random network: BF16 activations
+    # change the higher-moment rate by ~1e-2 relative
+    same_tol = 1e-6 if storage == "f32" else 2e-4
+    for net, tol in ((_net(tau, out_scale=0.0), same_tol), (_net(tau, seed=12, out_scale=0.5), 1e-3)):
+        a = L(name, dims, tau, "learned", storage=storage)
+        b = L(name, dims, tau, "learned", storage=storage, learned_tc=True)
+        for lat in (a, b):
+            lat.set_mlp(net)
+            lat.init_from_moments(rho, u)
+            lat.step(10)
+        fa, fb = gpu_pops(a), gpu_pops(b)
+        assert werr(fa, fb, w) <= tol
+        if tol == 1e-3:
+            assert werr(fa, fb, w) > 0.0  # the BF16 network really ran
