@@ -85,7 +85,7 @@ struct lb_ctx {
     void* lam[2] = {nullptr, nullptr};
     void* gF = nullptr;        // force-gradient accumulator [D][plane]
     void* gtheta = nullptr;    // learned: per-block parameter gradient partials
-    int64_t gtheta_cap = 0;
+    int64_t gtheta_cap = 0;    // bytes
 };
 
 namespace {
@@ -709,12 +709,14 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     if (c->coll == LB_LEARNED_MRT) {
         nblk = lb::learned_adj_partial_count(c->g);
         const int64_t need = nblk * 793;
-        if (c->gtheta_cap < need) {
+        // block partials, then the chunk sums of the deterministic reduction
+        const int64_t bytes = need * real_bytes(c->opt.storage) + lb::learned_theta_chunk_doubles() * 8 + 256;
+        if (c->gtheta_cap < bytes) {
             if (c->gtheta) cudaFree(c->gtheta);
             c->gtheta = nullptr;
             c->gtheta_cap = 0;
-            if ((s = alloc(c, &c->gtheta, need * real_bytes(c->opt.storage), "parameter gradient")) != LB_OK) return s;
-            c->gtheta_cap = need;
+            if ((s = alloc(c, &c->gtheta, bytes, "parameter gradient")) != LB_OK) return s;
+            c->gtheta_cap = bytes;
         }
         LB_CUDA(c, cudaMemsetAsync(c->gtheta, 0, (size_t)(need * real_bytes(c->opt.storage)), c->stream), "gtheta clear");
     }
@@ -771,8 +773,10 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     if (gth) {
         Staged so;
         if ((s = stage_out_alloc(c, so, gth, 793, m, true, "grad_theta")) != LB_OK) return s;
-        LB_CUDA(c, lb::learned_reduce_theta(c->gtheta, nblk, f64, so.dev, mem_f64(m), c->stream), "grad_theta");
-        c->launches += 1;
+        const int64_t part_bytes = nblk * 793 * real_bytes(c->opt.storage);
+        double* chunk = (double*)((char*)c->gtheta + (part_bytes + 255) / 256 * 256);
+        LB_CUDA(c, lb::learned_reduce_theta(c->gtheta, nblk, f64, chunk, so.dev, mem_f64(m), c->stream), "grad_theta");
+        c->launches += 2;
         if ((s = stage_out_finish(c, so, gth, "grad_theta")) != LB_OK) return s;
     }
     return LB_OK;

@@ -394,19 +394,139 @@ __global__ void __launch_bounds__(128) k_learned_update_tc(const T* src, T* dst,
 // ---------------------------------------------------------------- adjoint
 constexpr int kAdjBlock = 128;
 
-// shared-memory staging of the per-node backprop vectors of one block
+// shared-memory staging of the per-node backprop vectors of one block (rows 16-byte
+// aligned so that four consecutive hidden units load as one vector)
+constexpr int kRow = 28;  // row stride: 16-byte aligned, and 8 consecutive rows hit distinct banks
 template <class R>
 struct AdjShared {
-    R ga1[kAdjBlock][kNetHidden + 1];
-    R ga2[kAdjBlock][kNetHidden + 1];
-    R h1[kAdjBlock][kNetHidden + 1];
-    R h2[kAdjBlock][kNetHidden + 1];
-    R x[kAdjBlock][kNetIn + 1];
+    R ga1[kAdjBlock][kRow];
+    R ga2[kAdjBlock][kRow];
+    R h1[kAdjBlock][kRow];
+    R h2[kAdjBlock][kRow];
+    R x[kAdjBlock][8];
     R gz[kAdjBlock];
+    R part[48][kRow];  // upper half of each reduction tile (24 products + 4 bias sums)
 };
 
+template <class R>
+LB_DEV void ld4(const R* p, R* v)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = *(const float4*)p;
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <class R>
+LB_DEV void st4(R* p, const R* v)
+{
+    if constexpr (sizeof(R) == 4) {
+        *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *(double2*)p = make_double2(v[0], v[1]);
+        *(double2*)(p + 2) = make_double2(v[2], v[3]);
+    }
+}
+
+// Sum the outer products of the block's nodes into the 793 parameter-gradient partials.
+// 48 register tiles: W1 4x6 (+ b1), W2 4x4 (+ b2 on the k0 = 0 tiles), W3 1x4 (+ b3). Each
+// tile's node range is split over two threads (96 of the block's 128); the upper half's 28
+// sums go through shared memory and are added to the lower half's in a fixed order, so the
+// result does not depend on timing. Every shared-memory vector load feeds several FMAs.
+template <class R>
+LB_DEV void block_theta_grad(AdjShared<R>& sh, int t, R* out)
+{
+    constexpr int oW1 = 0, ob1 = kNetHidden * kNetIn, oW2 = ob1 + kNetHidden;
+    constexpr int ob2 = oW2 + kNetHidden * kNetHidden, oW3 = ob2 + kNetHidden, ob3 = oW3 + kNetHidden;
+    const int tile = t % 48, half = t / 48;  // threads 96..127 only wait at the barrier
+    const int q0 = (half & 1) * (kAdjBlock / 2), q1 = q0 + kAdjBlock / 2;
+    R acc[24], accb[4];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) accb[k] = R(0);
+    if (half < 2) {
+        if (tile < 6) {
+            const int j0 = 4 * tile;
+            for (int q = q0; q < q1; ++q) {
+                R ga[4], xv[8];
+                ld4(&sh.ga1[q][j0], ga);
+                ld4(&sh.x[q][0], xv);
+                ld4(&sh.x[q][4], xv + 4);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    accb[a] += ga[a];
+#pragma unroll
+                    for (int m = 0; m < kNetIn; ++m) acc[a * kNetIn + m] += ga[a] * xv[m];
+                }
+            }
+        } else if (tile < 42) {
+            const int tt = tile - 6, j0 = 4 * (tt / 6), k0 = 4 * (tt % 6);
+            for (int q = q0; q < q1; ++q) {
+                R ga[4], hv[4];
+                ld4(&sh.ga2[q][j0], ga);
+                ld4(&sh.h1[q][k0], hv);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    accb[a] += ga[a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a * 4 + b] += ga[a] * hv[b];
+                }
+            }
+        } else {
+            const int k0 = 4 * (tile - 42);
+            for (int q = q0; q < q1; ++q) {
+                const R gq = sh.gz[q];
+                R hv[4];
+                ld4(&sh.h2[q][k0], hv);
+                accb[0] += gq;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[b] += gq * hv[b];
+            }
+        }
+    }
+    if (half == 1) {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) sh.part[tile][k] = acc[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh.part[tile][24 + k] = accb[k];
+    }
+    __syncthreads();
+    if (half != 0) return;
+    const R* up = sh.part[tile];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] += up[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) accb[k] += up[24 + k];
+    if (tile < 6) {
+        const int j0 = 4 * tile;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            out[ob1 + j0 + a] += accb[a];
+#pragma unroll
+            for (int m = 0; m < kNetIn; ++m) out[oW1 + (j0 + a) * kNetIn + m] += acc[a * kNetIn + m];
+        }
+    } else if (tile < 42) {
+        const int tt = tile - 6, j0 = 4 * (tt / 6), k0 = 4 * (tt % 6);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (k0 == 0) out[ob2 + j0 + a] += accb[a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) out[oW2 + (j0 + a) * kNetHidden + k0 + b] += acc[a * 4 + b];
+        }
+    } else {
+        const int k0 = 4 * (tile - 42);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) out[oW3 + k0 + b] += acc[b];
+        if (k0 == 0) out[ob3] += accb[0];
+    }
+}
+
 template <class T>
-__global__ void __launch_bounds__(kAdjBlock) k_learned_adjoint(const T* state, const typename Store<T>::Real* lam_in,
+__global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state, const typename Store<T>::Real* lam_in,
                                                                typename Store<T>::Real* lam_out, Geom g,
                                                                typename Store<T>::Real omega,
                                                                typename Store<T>::Real* gth_partials,
@@ -534,40 +654,18 @@ __global__ void __launch_bounds__(kAdjBlock) k_learned_adjoint(const T* state, c
     }
     // stage the outer-product factors and reduce them over the block's nodes
 #pragma unroll
-    for (int k = 0; k < kNetHidden; ++k) {
-        sh.ga1[t][k] = ga1[k];
-        sh.ga2[t][k] = ga2[k];
-        sh.h1[t][k] = s.h1[k];
-        sh.h2[t][k] = s.h2[k];
+    for (int k = 0; k < kNetHidden; k += 4) {
+        st4(&sh.ga1[t][k], ga1 + k);
+        st4(&sh.ga2[t][k], ga2 + k);
+        st4(&sh.h1[t][k], s.h1 + k);
+        st4(&sh.h2[t][k], s.h2 + k);
     }
 #pragma unroll
-    for (int m = 0; m < kNetIn; ++m) sh.x[t][m] = s.x[m];
+    for (int m = 0; m < 8; ++m) sh.x[t][m] = m < kNetIn ? s.x[m] : R(0);
     sh.gz[t] = gz;
     __syncthreads();
-    R* out = gth_partials + (int64_t)(blockIdx.x + (int64_t)gridDim.x * blockIdx.y) * kNetTheta;
-    for (int o = t; o < kNetTheta; o += kAdjBlock) {
-        R acc = R(0);
-        if (o < kNetHidden * kNetIn) {  // W1[j][m] += ga1_j x_m
-            const int j = o / kNetIn, m = o % kNetIn;
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga1[q][j] * sh.x[q][m];
-        } else if (o < kNetHidden * kNetIn + kNetHidden) {  // b1
-            const int j = o - kNetHidden * kNetIn;
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga1[q][j];
-        } else if (o < kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden) {  // W2[j][k] += ga2_j h1_k
-            const int r = o - (kNetHidden * kNetIn + kNetHidden);
-            const int j = r / kNetHidden, k = r % kNetHidden;
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga2[q][j] * sh.h1[q][k];
-        } else if (o < kNetHidden * kNetIn + 2 * kNetHidden + kNetHidden * kNetHidden) {  // b2
-            const int j = o - (kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden);
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.ga2[q][j];
-        } else if (o < kNetTheta - 1) {  // W3[k] += gz h2_k
-            const int k = o - (kNetHidden * kNetIn + 2 * kNetHidden + kNetHidden * kNetHidden);
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.gz[q] * sh.h2[q][k];
-        } else {  // b3
-            for (int q = 0; q < kAdjBlock; ++q) acc += sh.gz[q];
-        }
-        out[o] += acc;  // partials accumulate over the adjoint steps of one run
-    }
+    // partials accumulate over the adjoint steps of one run
+    block_theta_grad(sh, t, gth_partials + (int64_t)(blockIdx.x + (int64_t)gridDim.x * blockIdx.y) * kNetTheta);
 }
 
 template <class R>
@@ -638,24 +736,42 @@ int64_t learned_adj_partial_count(const Geom& g)
     return (int64_t)((g.nx + kAdjBlock - 1) / kAdjBlock) * g.ny;
 }
 
-// out[o] (+)= sum_b partials[b][o]: one thread per parameter, blocks summed in order
+// out[o] (+)= sum_b partials[b][o] in two deterministic passes: chunk c of the block
+// partials is summed in block order into chunk[c][o], then the chunks in chunk order.
+constexpr int kThetaChunks = 128;
+
 template <class P>
-__global__ void k_reduce_theta(const P* partials, int64_t nblk, void* out, int out_f64)
+__global__ void __launch_bounds__(256) k_reduce_theta_chunks(const P* partials, int64_t nblk, double* chunk)
+{
+    const int64_t per = (nblk + kThetaChunks - 1) / kThetaChunks;
+    const int64_t b0 = blockIdx.x * per, b1 = b0 + per < nblk ? b0 + per : nblk;
+    for (int o = threadIdx.x; o < kNetTheta; o += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t b = b0; b < b1; ++b) acc += (double)partials[b * kNetTheta + o];
+        chunk[(int64_t)blockIdx.x * kNetTheta + o] = acc;
+    }
+}
+
+__global__ void k_reduce_theta_final(const double* chunk, void* out, int out_f64)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= kNetTheta) return;
     double acc = 0.0;
-    for (int64_t b = 0; b < nblk; ++b) acc += (double)partials[b * kNetTheta + o];
+    for (int c = 0; c < kThetaChunks; ++c) acc += chunk[(int64_t)c * kNetTheta + o];
     if (out_f64) ((double*)out)[o] += acc;
     else ((float*)out)[o] += (float)acc;
 }
 
-cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, void* out, int out_f64,
-                                 cudaStream_t s)
+int64_t learned_theta_chunk_doubles() { return (int64_t)kThetaChunks * kNetTheta; }
+
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, double* chunk, void* out,
+                                 int out_f64, cudaStream_t s)
 {
-    const int threads = 128, blocks = (kNetTheta + threads - 1) / threads;
-    if (part_f64) k_reduce_theta<double><<<blocks, threads, 0, s>>>((const double*)partials, nblk, out, out_f64);
-    else k_reduce_theta<float><<<blocks, threads, 0, s>>>((const float*)partials, nblk, out, out_f64);
+    if (part_f64) k_reduce_theta_chunks<double><<<kThetaChunks, 256, 0, s>>>((const double*)partials, nblk, chunk);
+    else k_reduce_theta_chunks<float><<<kThetaChunks, 256, 0, s>>>((const float*)partials, nblk, chunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_theta_final<<<(kNetTheta + 127) / 128, 128, 0, s>>>(chunk, out, out_f64);
     return cudaGetLastError();
 }
 

@@ -23,9 +23,11 @@ void learned_tc_pack(const double* net, void* out);
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // number of blocks of the learned adjoint launch (rows of the gradient partials)
 int64_t learned_adj_partial_count(const Geom& g);
-// out[793] (+)= sum over blocks of partials[block][793]
-cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, void* out, int out_f64,
-                                 cudaStream_t s);
+// out[793] (+)= sum over blocks of partials[block][793] (two deterministic passes through
+// `chunk`, learned_theta_chunk_doubles() doubles of scratch)
+int64_t learned_theta_chunk_doubles();
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, double* chunk, void* out,
+                                 int out_f64, cudaStream_t s);
 
 struct LossEq6Args {
     OpArgs a;                    // state, geometry, stream
