@@ -46,7 +46,7 @@ BYTES_PER_LU = {  # algorithmic bytes per lattice update: read Q + write Q popul
 # DRAM traffic per launch of the D3Q19 FP32 AB stream-collide kernel at 256^3 from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
 # with the listed hash; the hash is recomputed at run time and the figure dropped if it differs.
-NCU_TRAFFIC = {"kernel_hash": "c672bab261fe9581", "bytes_per_launch": 2493946112}  # ncu of --only ab_f32, 256^3
+NCU_TRAFFIC = {"kernel_hash": "b420f2d20a67a374", "bytes_per_launch": 2493391616}  # ncu of --only ab_f32, 256^3
 KERNEL_SOURCES = ["lb_device.cuh", "lb_collide.cuh", "lb_kernels.cuh"]
 
 
@@ -168,6 +168,7 @@ ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, col
     "aa_f16": ("D3Q19", "f16", "aa", "bgk"), "ab_f64": ("D3Q19", "f64", "ab", "bgk"),
     "d3q27_reg_f32": ("D3Q27", "f32", "ab", "regularized"), "d3q27_reg_f16": ("D3Q27", "f16", "ab", "regularized"),
     "d2q9_f32": ("D2Q9", "f32", "ab", "bgk"), "d2q9_f16": ("D2Q9", "f16", "ab", "bgk"),
+    "tgv2d_64_f64": ("D2Q9", "f64", "ab", "bgk"),
 }
 
 
@@ -199,13 +200,14 @@ def run_only(args):
     stencil, storage, layout, coll = ONLY[args.only]
     dims, tau, rho, u = workload(stencil, args.grid)
     N = int(np.prod(dims))
-    lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout)
+    lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout, graphs=not args.no_graphs)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     lat.step(args.warmup)
     t = time_steps(lat, args.steps, torch.cuda.current_stream())
     lat.check()
     g = N * args.steps / t / 1e9
-    print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "glups": round(g, 3),
+    print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "graphs": not args.no_graphs,
+                      "glups": round(g, 3),
                       "hbm_frac": round(g * BYTES_PER_LU[(stencil, storage)] / measured_peak_hbm()[0], 4)}))
 
 
@@ -476,6 +478,7 @@ def main():
     ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned", "learned_tc"]), default=None,
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
+    ap.add_argument("--no-graphs", action="store_true", help="--only: one launch per kernel instead of graph replay")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -96,9 +96,12 @@ typedef struct {
                              hidden layers on the tensor cores with BF16 operands and FP32
                              accumulation (an inference option: lb_step_adjoint and training use
                              the FP32 network); 0 (default) = FP32 arithmetic throughout */
+    int graphs;           /* 1 (default): lb_step(n >= 2) without checkpoints captures two steps once
+                             into a CUDA graph and replays it (one launch per pair of steps instead
+                             of one per kernel; same kernels, same results); 0 = direct launches */
 } lb_options;
 
-/* Fill *opt with the defaults listed above (learned_tc = 0). */
+/* Fill *opt with the defaults listed above (learned_tc = 0, graphs = 1). */
 LB_API void lb_default_options(lb_options* opt);
 
 /* Create a context: validate, allocate the population buffer(s) on opt->device and

@@ -86,6 +86,12 @@ struct lb_ctx {
     void* gF = nullptr;        // force-gradient accumulator [D][plane]
     void* gtheta = nullptr;    // learned: per-block parameter gradient partials
     int64_t gtheta_cap = 0;    // bytes
+
+    // CUDA graph of a two-step cycle, replayed by lb_step when nothing is recorded
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t cycle = nullptr;
+    void* cycle_state = nullptr;  // state buffer the cycle starts from (and returns to)
+    bool graphs = true;
 };
 
 namespace {
@@ -228,6 +234,13 @@ lb_status ensure_partials(lb_ctx* c, int64_t count)
     return s;
 }
 
+void drop_cycle(lb_ctx* c)
+{
+    if (c->cycle) cudaGraphExecDestroy(c->cycle);
+    c->cycle = nullptr;
+    c->cycle_state = nullptr;
+}
+
 void reset_recording(lb_ctx* c)
 {
     c->recording = false;
@@ -262,6 +275,7 @@ void lb_default_options(lb_options* o)
     o->check_every = 0;
     o->record_every = 0;
     o->learned_tc = 0;
+    o->graphs = 1;
 }
 
 lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau, lb_collision coll,
@@ -280,6 +294,7 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if ((int)o.layout < 0 || (int)o.layout > 1) return fail(LB_ERR_ARG, "unknown layout %d", (int)o.layout);
     if (o.check_every < 0 || o.record_every < 0) return fail(LB_ERR_ARG, "negative check_every / record_every");
     if (o.learned_tc != 0 && o.learned_tc != 1) return fail(LB_ERR_ARG, "learned_tc must be 0 or 1");
+    if (o.graphs != 0 && o.graphs != 1) return fail(LB_ERR_ARG, "graphs must be 0 or 1");
     if (o.learned_tc && (coll != LB_LEARNED_MRT || o.storage == LB_F64))
         return fail(LB_ERR_UNSUPPORTED, "learned_tc needs the learned collision with FP32 or half storage");
     const int D = stencil == LB_D2Q9 ? 2 : 3;
@@ -346,6 +361,8 @@ void lb_destroy(lb_ctx* c)
     if (!c) return;
     DeviceGuard guard(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->cycle) cudaGraphExecDestroy(c->cycle);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
                     c->gF, c->gtheta};
     for (void* p : ptrs)
@@ -382,6 +399,7 @@ lb_status lb_set_force(lb_ctx* c, const void* F, lb_mem m)
 {
     lb_status s = check_ctx(c);
     if (s != LB_OK) return s;
+    drop_cycle(c);  // the force pointer (or its absence) is baked into the captured steps
     if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
     if (F && c->coll == LB_LEARNED_MRT) return fail(LB_ERR_UNSUPPORTED, "the learned collision takes no force");
     DeviceGuard guard(c->device);
@@ -439,6 +457,7 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
         LB_CUDA(c, cudaStreamSynchronize(c->stream), "weight table");
     }
     c->net.swap(v);
+    drop_cycle(c);  // the network is a by-value kernel argument of the captured steps
     return LB_OK;
 }
 
@@ -488,6 +507,52 @@ lb_status lb_check(lb_ctx* c)
     return LB_OK;
 }
 
+// Capture two consecutive steps (AB: A -> B -> A; AA: even, odd) into a graph on a private
+// stream. Returns false (and leaves direct launches in charge) if capture is not possible.
+static bool build_cycle(lb_ctx* c)
+{
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_stream = nullptr;
+        return false;
+    }
+    drop_cycle(c);
+    void* start = c->state;
+    const int parity = c->aa_parity;
+    const int64_t steps0 = c->steps, launches0 = c->launches;
+    cudaStream_t user = c->stream;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->stream = c->cap_stream;
+    bool ok = step_once(c) == LB_OK && step_once(c) == LB_OK;
+    c->stream = user;
+    cudaGraph_t graph = nullptr;
+    const bool ended = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess;
+    // the captured launches did not run: restore the bookkeeping
+    c->state = start;
+    c->aa_parity = parity;
+    c->steps = steps0;
+    c->launches = launches0;
+    c->failed = false;
+    if (!ok || !ended || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const bool inst = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cudaGraphDestroy(graph);
+    if (!inst) {
+        cudaGetLastError();
+        return false;
+    }
+    c->cycle = exec;
+    c->cycle_state = start;
+    return true;
+}
+
 lb_status lb_step(lb_ctx* c, int64_t n)
 {
     lb_status s = check_ctx(c);
@@ -497,9 +562,27 @@ lb_status lb_step(lb_ctx* c, int64_t n)
     DeviceGuard guard(c->device);
     if (c->opt.record_every > 0 && !c->recording && n > 0)
         if ((s = record_begin(c)) != LB_OK) return s;
-    for (int64_t t = 0; t < n; ++t) {
+    // without recording, pairs of steps replay a captured two-step graph
+    const bool use_graph = c->graphs && c->opt.graphs && c->opt.record_every == 0 && n >= 2;
+    for (int64_t t = 0; t < n;) {
+        const int64_t until_check = c->opt.check_every > 0 ? c->opt.check_every - t % c->opt.check_every : n - t;
+        const bool even_start = c->opt.layout == LB_LAYOUT_AB || c->aa_parity == 0;
+        if (use_graph && n - t >= 2 && until_check >= 2 && even_start) {
+            if (!c->cycle || c->cycle_state != c->state)
+                if (!build_cycle(c)) c->graphs = false;
+            if (c->cycle) {
+                LB_CUDA(c, cudaGraphLaunch(c->cycle, c->stream), "step graph");
+                c->steps += 2;
+                c->launches += 2;
+                t += 2;
+                if (c->opt.check_every > 0 && t % c->opt.check_every == 0)
+                    if ((s = lb_check(c)) != LB_OK) return s;
+                continue;
+            }
+        }
         if ((s = step_once(c)) != LB_OK) return s;
-        if (c->opt.check_every > 0 && (t + 1) % c->opt.check_every == 0)
+        ++t;
+        if (c->opt.check_every > 0 && t % c->opt.check_every == 0)
             if ((s = lb_check(c)) != LB_OK) return s;
     }
     if (c->opt.check_every > 0 && n % c->opt.check_every != 0) return lb_check(c);

@@ -47,13 +47,14 @@ class Lattice:
     storage: "f64" | "f32" | "f16" | "bf16" (the half types store f_i - w_i);
     layout: "ab" (two buffers) | "aa" (in place); record_every > 0 keeps
     checkpoints for ``step_adjoint``; learned_tc runs the learned collision's network
-    on the tensor cores (BF16 operands, FP32 accumulation; forward only). The context
-    runs on torch's current CUDA stream at construction time.
+    on the tensor cores (BF16 operands, FP32 accumulation; forward only); graphs
+    replays ``step(n)`` as captured two-step CUDA graphs (off: one launch per kernel).
+    The context runs on torch's current CUDA stream at construction time.
     """
 
     def __init__(self, stencil: str, dims, tau: float, collision: str = "bgk", storage: str = "f32",
                  layout: str = "ab", device: int | None = None, stream=None, check_every: int = 0,
-                 record_every: int = 0, learned_tc: bool = False):
+                 record_every: int = 0, learned_tc: bool = False, graphs: bool = True):
         self._lib = _lib.load()
         self.stencil = stencil
         self.dims = tuple(int(v) for v in dims)
@@ -81,6 +82,7 @@ class Lattice:
         opt.check_every = check_every
         opt.record_every = record_every
         opt.learned_tc = int(bool(learned_tc))
+        opt.graphs = int(bool(graphs))
         dims_arr = (ctypes.c_int64 * 3)(*self.dims)
         h = ctypes.c_void_p()
         _lib.check(self._lib.lb_create(ctypes.byref(h), _lib.STENCIL[stencil], dims_arr, ctypes.c_double(tau),

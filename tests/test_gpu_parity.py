@@ -553,3 +553,38 @@ def test_learned_tensor_core_option(storage):
         assert werr(fa, fb, w) <= tol
         if tol == 1e-3:
             assert werr(fa, fb, w) > 0.0  # the BF16 network really ran
+
+
+# ------------------------------------------------------------------ graph replay of step pairs
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("coll,storage", [("bgk", "f32"), ("regularized", "f16"), ("learned", "f32")])
+def test_graph_replay_equals_single_steps(layout, coll, storage):
+    """lb_step(n) replays a captured two-step graph; lb_step(1) launches directly. Same bits."""
+    name = "D2Q9"
+    dims = (48, 20, 1)
+    rho, u = lbinputs.random_moments(dims, seed=3, u_amp=0.05)
+    F = lbinputs.random_field((2, 960), seed=4, amp=1e-4)
+    a = L(name, dims, 0.6, coll, storage=storage, layout=layout)
+    b = L(name, dims, 0.6, coll, storage=storage, layout=layout)
+    for lat in (a, b):
+        if coll == "learned":
+            lat.set_mlp(_net(0.6, seed=3))
+        else:
+            lat.set_force(F)
+        lat.init_from_moments(rho, u)
+    a.step(7)           # 3 graph replays + 1 direct step
+    for _ in range(7):
+        b.step(1)
+    np.testing.assert_array_equal(gpu_pops(a), gpu_pops(b))
+    assert a.launch_count() - b.launch_count() == 0
+    # changing the force (or the network) must not replay a stale graph
+    if coll == "learned":
+        a.set_mlp(_net(0.6, seed=4))
+        b.set_mlp(_net(0.6, seed=4))
+    else:
+        a.set_force(2 * F)
+        b.set_force(2 * F)
+    a.step(4)
+    for _ in range(4):
+        b.step(1)
+    np.testing.assert_array_equal(gpu_pops(a), gpu_pops(b))

@@ -65,9 +65,11 @@ def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
     (dict(stencil=1, dims=(4, 4, 4), coll=2), 6),   # learned collision is D2Q9 only
     (dict(storage=5), 1),
     (dict(layout=1, record_every=5), 6),    # recording needs the AB layout
+    (dict(graphs=2), 1),
+    (dict(learned_tc=1), 6),                # tensor-core network needs the learned collision
 ])
 def test_create_rejects_bad_arguments_without_gpu(lib, kw, expect):
-    opt_keys = {"storage", "layout", "record_every", "check_every"}
+    opt_keys = {"storage", "layout", "record_every", "check_every", "graphs", "learned_tc"}
     opt = {k: v for k, v in kw.items() if k in opt_keys}
     args = {k: v for k, v in kw.items() if k not in opt_keys}
     rc, h = _create(lib, **args, **opt)
