@@ -8,7 +8,9 @@ multiply-add); this module only compiles it and marshals numpy arrays.
 Conventions: a population array is ``f[Q][N]`` (FP64, natural layout, the
 pre-collision state of Eq. 1), a vector field ``u[d][N]``, nodes ordered x fastest.
 Collision kinds: ``"bgk"`` (Eq. 2), ``"regularized"``, ``"learned"`` (Eq. 5, D2Q9),
-``"none"`` (streaming only). Stencils: ``"D2Q9"``, ``"D3Q19"``, ``"D3Q27"``.
+``"none"`` (streaming only), ``"trt"`` (two relaxation times), ``"kbc"`` (entropic,
+D2Q9 and D3Q27), ``"mrt"`` (Eq. 5 with fixed rates, D2Q9). ``params``: TRT
+``[Lambda]`` (default 1/4), MRT ``[tau_6, tau_7, tau_8]`` (default 1, 1, 1). Stencils: ``"D2Q9"``, ``"D3Q19"``, ``"D3Q27"``.
 """
 from __future__ import annotations
 
@@ -26,7 +28,8 @@ _lock = threading.Lock()
 _lib = None
 
 STENCILS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3}
+COLLISIONS = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6}
+N_PARAMS = {"trt": 1, "mrt": 3}
 N_THETA = 793
 N_MLP = N_THETA + 12
 
@@ -115,25 +118,33 @@ def init_eq(name, dims, rho, u):
     return f
 
 
-def step(name, dims, tau, collision, f, nsteps=1, F=None, mlp=None):
+def _cpar(collision, mlp, params):
+    if collision == "learned":
+        return None if mlp is None else _arr(mlp, (N_MLP,))
+    if params is None:
+        return None
+    return _arr(params, (N_PARAMS[collision],))
+
+
+def step(name, dims, tau, collision, f, nsteps=1, F=None, mlp=None, params=None):
     """Return f^{n+nsteps} from f^n by iterating Eq. 1 (collide, then push-stream)."""
     d, _, w, _ = stencil(name)
     N = n_nodes(dims)
     out = _arr(f, (len(w), N)).copy()
     F = None if F is None else _arr(F, (d, N))
-    mlp = None if mlp is None else _arr(mlp, (N_MLP,))
+    mlp = _cpar(collision, mlp, params)
     _check(_load().ora_step(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
                             COLLISIONS[collision], _p(F), _p(mlp), _p(out), ctypes.c_int64(nsteps)), "step")
     return out
 
 
-def collide_node(name, tau, collision, f, F=None, mlp=None):
+def collide_node(name, tau, collision, f, F=None, mlp=None, params=None):
     """Post-collision populations of a single node (f[Q] -> f*[Q])."""
     d, _, w, _ = stencil(name)
     f = _arr(f, (len(w),))
     out = np.zeros(len(w))
     F = None if F is None else _arr(F, (d,))
-    mlp = None if mlp is None else _arr(mlp, (N_MLP,))
+    mlp = _cpar(collision, mlp, params)
     _check(_load().ora_collide_node(STENCILS[name], ctypes.c_double(tau), COLLISIONS[collision], _p(f), _p(F),
                                     _p(mlp), _p(out)), "collide_node")
     return out

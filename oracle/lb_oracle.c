@@ -18,6 +18,11 @@
  *   Eq. 5  moment-space collision Omega = -M^-1 S^-1 (M f - m^eq) with
  *          conserved rates 1, shear tau_n = nu/c_s^2 + 1/2, higher-moment rates
  *          tau = exp(net) + 1/2 from a per-node network of local moments (Sec. 3.1).
+ *   Sec. 2.1 further collision models the paper lists by citation only:
+ *          two-relaxation-time (Ginzburg 2008), moment-space MRT with fixed rates
+ *          (Eq. 5 with constant higher-moment relaxation times), and the entropic
+ *          KBC model (Karlin, Boesch & Chikatamarla 2014). Their definitions are
+ *          written out at collide_node.
  *   Eq. 6  training loss from velocity, vorticity and energy mismatch.
  *   Sec. 3.2 gradients through the solver (here: the discrete adjoint, by hand).
  * Readings where the paper is silent (stencil order, Guo forcing, Hermite moment
@@ -40,6 +45,9 @@
 #define ORA_REG 1
 #define ORA_LEARNED 2
 #define ORA_NONE 3
+#define ORA_TRT 4
+#define ORA_KBC 5
+#define ORA_MRT 6
 
 #define NH 24                 /* hidden width of the per-node network */
 #define NIN 6                 /* number of network inputs (moment invariants) */
@@ -315,8 +323,21 @@ typedef struct {
     double tau;
     int coll;
     const double* mlp; /* NMLP doubles, learned collision only */
-    const mrt_t* mt;   /* learned collision only */
+    const mrt_t* mt;   /* learned collision and MRT only */
+    double tau_minus;  /* TRT: relaxation time of the antisymmetric part */
+    double tau_g[3];   /* MRT: relaxation times of the three higher (ghost) moments */
 } params_t;
+
+/* 1D functions dual to the monomials 1, c, c^2 on the nodes c in {-1, 0, 1}:
+ * sum_c c^b phi_a(c) = (a == b). Their products give, on D2Q9 and D3Q27 (full
+ * tensor-product sets), the population vector that carries exactly one natural
+ * (raw) moment sum_i cx^a cy^b cz^c f_i and none of the others. */
+static double phi1d(int a, int c)
+{
+    if (a == 0) return c == 0 ? 1.0 : 0.0;
+    if (a == 1) return 0.5 * c;
+    return c == 0 ? -1.0 : 0.5;
+}
 
 static void collide_node(const params_t* P, const double* f, const double* F, double* out)
 {
@@ -361,6 +382,93 @@ static void collide_node(const params_t* P, const double* f, const double* F, do
             }
             out[i] = feq[i] + (1.0 - omega) * s->w[i] * (ca / cs2 + qp / (2.0 * cs2 * cs2)) + S[i];
         }
+    } else if (P->coll == ORA_TRT) {
+        /* Two-relaxation-time model (Ginzburg 2008): split every population pair (i, opp i)
+         * into its symmetric and antisymmetric halves,
+         *   g+_i = (g_i + g_opp(i))/2,  g-_i = (g_i - g_opp(i))/2,
+         * relax the symmetric non-equilibrium part with 1/tau (which sets the viscosity)
+         * and the antisymmetric one with 1/tau_minus, and split the Guo source the same
+         * way with prefactors (1 - omega+/2) and (1 - omega-/2):
+         *   f*_i = f_i - (f+_i - feq+_i)/tau - (f-_i - feq-_i)/tau_minus
+         *          + (1 - 1/(2 tau)) S+_i + (1 - 1/(2 tau_minus)) S-_i.
+         * tau_minus follows from the "magic" product Lambda = (tau - 1/2)(tau_minus - 1/2). */
+        double om_p = 1.0 / P->tau, om_m = 1.0 / P->tau_minus, S0[27];
+        if (F) {
+            /* S0 = the source without its prefactor (guo_source with omega = 0) */
+            guo_source(s, 0.0, u, F, S0);
+        } else {
+            for (i = 0; i < s->q; ++i) S0[i] = 0.0;
+        }
+        for (i = 0; i < s->q; ++i) {
+            int o = s->opp[i];
+            double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+            double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+            double sp = 0.5 * (S0[i] + S0[o]), sm = 0.5 * (S0[i] - S0[o]);
+            out[i] = f[i] - om_p * (fp - ep) - om_m * (fm - em) + (1.0 - 0.5 * om_p) * sp + (1.0 - 0.5 * om_m) * sm;
+        }
+    } else if (P->coll == ORA_KBC) {
+        /* Entropic KBC model (Karlin, Boesch & Chikatamarla 2014), no force, D2Q9 / D3Q27.
+         * f = k + s + h in natural (raw) moments: k carries rho and rho u, s the deviatoric
+         * (trace-free) second moments, h everything else (trace, third and higher orders).
+         * With D = f - f^eq: Ds = the population vector whose natural moments are the
+         * deviatoric second moments of D (and no other), Dh = D - Ds (Dk = 0). Then
+         *   f* = f - beta (2 Ds + gamma Dh),  beta = 1/(2 tau),
+         *   gamma = 1/beta - (2 - 1/beta) <Ds|Dh> / <Dh|Dh>,  <X|Y> = sum_i X_i Y_i / feq_i,
+         * the gamma that minimises the quadratic entropy estimate <D*|D*> of the result.
+         * Reading: the ratio's denominator is <Dh|Dh> + 1e-6 <Ds|Ds>. As Dh -> 0 along a
+         * fixed direction the unregularised gamma Dh tends to a finite, direction-dependent
+         * limit, so rounding noise in a vanishing Dh would decide the result; the term
+         * keeps gamma Dh -> 0 there and changes gamma by a relative 1e-6 <Ds|Ds>/<Dh|Dh>
+         * elsewhere. gamma = 2 (plain BGK) when D = 0. */
+        double D[27], Ds[27], M2[3][3], tr = 0.0, sh = 0.0, hh = 0.0, ss = 0.0, beta = 0.5 / P->tau, gam, den;
+        for (i = 0; i < s->q; ++i) D[i] = f[i] - feq[i];
+        for (a = 0; a < s->d; ++a)
+            for (b = 0; b < s->d; ++b) {
+                double acc = 0.0;
+                for (i = 0; i < s->q; ++i) acc += s->c[i][a] * s->c[i][b] * D[i];
+                M2[a][b] = acc;
+            }
+        for (a = 0; a < s->d; ++a) tr += M2[a][a];
+        for (a = 0; a < s->d; ++a) M2[a][a] -= tr / s->d;
+        for (i = 0; i < s->q; ++i) {
+            double acc = 0.0;
+            for (a = 0; a < s->d; ++a)
+                for (b = 0; b < s->d; ++b) {
+                    /* exponents of the monomial c_a c_b in each axis */
+                    int e[3] = {0, 0, 0}, k;
+                    double prod = 1.0;
+                    if (b < a) continue; /* each off-diagonal moment once */
+                    e[a] += 1; e[b] += 1;
+                    for (k = 0; k < 3; ++k) prod *= phi1d(e[k], s->c[i][k]);
+                    acc += M2[a][b] * prod;
+                }
+            Ds[i] = acc;
+        }
+        for (i = 0; i < s->q; ++i) {
+            double h = D[i] - Ds[i];
+            sh += Ds[i] * h / feq[i];
+            hh += h * h / feq[i];
+            ss += Ds[i] * Ds[i] / feq[i];
+        }
+        den = hh + 1e-6 * ss;
+        gam = den > 0.0 ? 1.0 / beta - (2.0 - 1.0 / beta) * sh / den : 2.0;
+        for (i = 0; i < s->q; ++i) out[i] = f[i] - beta * (2.0 * Ds[i] + gam * (D[i] - Ds[i]));
+    } else if (P->coll == ORA_MRT) {
+        /* Eq. 5 with fixed rates: conserved rows 1, stress rows 1/tau, the three higher
+         * (ghost) rows 1/tau_g[k]; D2Q9, no force. */
+        const mrt_t* mt = P->mt;
+        double m[9], meq[9], om[9];
+        for (a = 0; a < 9; ++a) {
+            double rate = a < 3 ? 1.0 : (a < 6 ? 1.0 / P->tau : 1.0 / P->tau_g[a - 6]);
+            m[a] = 0.0; meq[a] = 0.0;
+            for (i = 0; i < 9; ++i) { m[a] += mt->M[a][i] * f[i]; meq[a] += mt->M[a][i] * feq[i]; }
+            om[a] = rate * (m[a] - meq[a]);
+        }
+        for (i = 0; i < 9; ++i) {
+            double acc = 0.0;
+            for (a = 0; a < 9; ++a) acc += mt->Minv[i][a] * om[a];
+            out[i] = f[i] - acc;
+        }
     } else { /* ORA_LEARNED, D2Q9, no force: Eq. 5 */
         const mrt_t* mt = P->mt;
         double m[9], meq[9], rate[9], I[NIN], om[9];
@@ -385,16 +493,38 @@ static void collide_node(const params_t* P, const double* f, const double* F, do
     }
 }
 
-static int make_params(params_t* P, const stencil_t* s, mrt_t* mt, double tau, int coll, const double* mlp,
+/* cpar: the collision's parameters. Learned: the NMLP network values. TRT: cpar[0] =
+ * Lambda (default 1/4 when cpar is NULL). MRT: cpar[0..2] = tau_g of the three higher
+ * moments (default 1 each). Others: unused. */
+static int make_params(params_t* P, const stencil_t* s, mrt_t* mt, double tau, int coll, const double* cpar,
                        const double* F)
 {
-    P->s = s; P->tau = tau; P->coll = coll; P->mlp = mlp; P->mt = NULL;
+    int k;
+    P->s = s; P->tau = tau; P->coll = coll; P->mlp = NULL; P->mt = NULL;
+    P->tau_minus = tau;
+    P->tau_g[0] = P->tau_g[1] = P->tau_g[2] = 1.0;
     if (!(tau > 0.5)) return ORA_ERR_ARG;
-    if (coll < 0 || coll > 3) return ORA_ERR_ARG;
+    if (coll < 0 || coll > 6) return ORA_ERR_ARG;
     if (coll == ORA_LEARNED) {
-        if (s->q != 9 || !mlp || F) return ORA_ERR_ARG;
+        if (s->q != 9 || !cpar || F) return ORA_ERR_ARG;
+        if (mrt_setup(s, mt)) return ORA_ERR_ARG;
+        P->mlp = cpar;
+        P->mt = mt;
+    } else if (coll == ORA_TRT) {
+        double lam = cpar ? cpar[0] : 0.25;
+        if (!(lam > 0.0)) return ORA_ERR_ARG;
+        P->tau_minus = 0.5 + lam / (tau - 0.5);
+    } else if (coll == ORA_KBC) {
+        if (F || (s->q != 9 && s->q != 27)) return ORA_ERR_ARG;
+    } else if (coll == ORA_MRT) {
+        if (s->q != 9 || F) return ORA_ERR_ARG;
         if (mrt_setup(s, mt)) return ORA_ERR_ARG;
         P->mt = mt;
+        if (cpar)
+            for (k = 0; k < 3; ++k) {
+                if (!(cpar[k] > 0.5)) return ORA_ERR_ARG;
+                P->tau_g[k] = cpar[k];
+            }
     }
     return ORA_OK;
 }
@@ -760,6 +890,7 @@ int ora_adjoint(int st, const int64_t* dims, double tau, int coll, const double*
     int64_t N, QN, t, n;
     double *states, *mu;
     if (stencil_get(st, &s) || check_dims(&s, dims) || nsteps < 0) return ORA_ERR_ARG;
+    if (coll > ORA_NONE) return ORA_ERR_ARG; /* no adjoint of TRT, KBC or MRT */
     if (make_params(&P, &s, &mt, tau, coll, mlp, F)) return ORA_ERR_ARG;
     N = dims[0] * dims[1] * dims[2];
     QN = (int64_t)s.q * N;
