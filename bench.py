@@ -169,6 +169,10 @@ ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, col
     "d3q27_reg_f32": ("D3Q27", "f32", "ab", "regularized"), "d3q27_reg_f16": ("D3Q27", "f16", "ab", "regularized"),
     "d2q9_f32": ("D2Q9", "f32", "ab", "bgk"), "d2q9_f16": ("D2Q9", "f16", "ab", "bgk"),
     "tgv2d_64_f64": ("D2Q9", "f64", "ab", "bgk"),
+    "d3q19_trt_f32": ("D3Q19", "f32", "ab", "trt"), "d3q19_trt_f16": ("D3Q19", "f16", "ab", "trt"),
+    "d3q27_kbc_f32": ("D3Q27", "f32", "ab", "kbc"), "d3q27_kbc_f16": ("D3Q27", "f16", "ab", "kbc"),
+    "d2q9_kbc_f32": ("D2Q9", "f32", "ab", "kbc"), "d2q9_mrt_f32": ("D2Q9", "f32", "ab", "mrt"),
+    "d2q9_trt_f32": ("D2Q9", "f32", "ab", "trt"),
 }
 
 

@@ -56,8 +56,28 @@ typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_stencil;
  *                   the three higher rows with 1/(exp(z) + 1/2), z = a per-node
  *                   6-24-24-1 tanh network of local moment invariants (Sec. 3.1).
  *                   No body force.
- *   LB_NONE         streaming only (f* = f); the force is ignored. For tests. */
-typedef enum { LB_BGK = 0, LB_REGULARIZED = 1, LB_LEARNED_MRT = 2, LB_NONE = 3 } lb_collision;
+ *   LB_NONE         streaming only (f* = f); the force is ignored. For tests.
+ * Further models the paper lists by citation (Sec. 2.1); no adjoint, no recording:
+ *   LB_TRT          two relaxation times (Ginzburg): the symmetric half of f - f^eq of
+ *                   each pair (i, opposite i) relaxes with 1/tau, the antisymmetric half
+ *                   with 1/tau_minus, tau_minus = 1/2 + Lambda/(tau - 1/2); Lambda = 1/4
+ *                   unless set by lb_set_relaxation. Guo source split the same way. Any set.
+ *   LB_KBC          entropic KBC (Karlin, Boesch & Chikatamarla): f - f^eq = Ds + Dh with
+ *                   Ds the trace-free second natural moments; f* = f - beta (2 Ds + gamma Dh),
+ *                   beta = 1/(2 tau), gamma = 1/beta - (2 - 1/beta) <Ds|Dh> / (<Dh|Dh> +
+ *                   1e-6 <Ds|Ds>), <X|Y> = sum X_i Y_i / f^eq_i. D2Q9 and D3Q27; no force.
+ *   LB_MRT          Eq. 5 with fixed rates on D2Q9: stress moments relax with 1/tau, the
+ *                   three higher Hermite moments with 1/tau_6, 1/tau_7, 1/tau_8 (1 unless
+ *                   set by lb_set_relaxation). No force. */
+typedef enum {
+    LB_BGK = 0,
+    LB_REGULARIZED = 1,
+    LB_LEARNED_MRT = 2,
+    LB_NONE = 3,
+    LB_TRT = 4,
+    LB_KBC = 5,
+    LB_MRT = 6
+} lb_collision;
 
 /* Storage of the populations in device memory. Arithmetic is FP64 for LB_F64 and
  * FP32 otherwise. The half types store the shifted value f_i - w_i, rounded to
@@ -132,6 +152,14 @@ LB_API lb_status lb_set_force(lb_ctx* ctx, const void* F, lb_mem mem);
  * the fixed input shift[6] and scale[6] (input k is (I_k - shift_k) scale_k).
  * Only valid for LB_LEARNED_MRT contexts. */
 LB_API lb_status lb_set_mlp(lb_ctx* ctx, const void* params, int64_t n_params, lb_mem mem);
+
+/* Further relaxation parameters (host memory, copied): LB_TRT n = 1, params[0] =
+ * Lambda = (tau - 1/2)(tau_minus - 1/2) > 0 (1/4 by default; (tau - 1/2)^2 gives BGK);
+ * LB_MRT n = 3, params = tau_6, tau_7, tau_8 > 1/2, the relaxation times of the higher
+ * moments (cx^2 - 1/3) cy, cx (cy^2 - 1/3), (cx^2 - 1/3)(cy^2 - 1/3) (1, 1, 1 by default;
+ * all equal to tau gives BGK). LB_ERR_STATE for other collisions, LB_ERR_ARG for a
+ * wrong count or value. Applies from the next lb_step. */
+LB_API lb_status lb_set_relaxation(lb_ctx* ctx, const double* params, int n);
 
 /* Advance n >= 0 steps of Eq. 1 (one fused kernel launch per step). */
 LB_API lb_status lb_step(lb_ctx* ctx, int64_t n);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblb.so")
 
 # enums of include/lb.h
 STENCIL = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISION = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3}
+COLLISION = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 LAYOUT = {"ab": 0, "aa": 1}
 MEM = {"host_f64": 0, "device_f64": 1, "host_f32": 2, "device_f32": 3}
@@ -57,6 +57,7 @@ _SIGNATURES = {
     "lb_init_from_moments": (_INT, [_P, _P, _P, _INT]),
     "lb_set_force": (_INT, [_P, _P, _INT]),
     "lb_set_mlp": (_INT, [_P, _P, _I64, _INT]),
+    "lb_set_relaxation": (_INT, [_P, _P, _INT]),
     "lb_step": (_INT, [_P, _I64]),
     "lb_moments": (_INT, [_P, _P, _P, _INT]),
     "lb_reduce": (_INT, [_P, ctypes.POINTER(_D)]),

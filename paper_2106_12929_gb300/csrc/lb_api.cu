@@ -59,6 +59,7 @@ struct lb_ctx {
     int64_t N = 0, plane = 0;
     double tau = 1.0, omega = 1.0;
     int coll = LB_BGK;
+    double relax[3] = {0.25, 0.0, 0.0};  // lb_set_relaxation values (TRT: Lambda; MRT: three tau_g)
     lb_options opt{};
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -146,6 +147,13 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     a.F = c->F;
     a.g = c->g;
     a.omega = c->omega;
+    if (c->coll == LB_TRT) {
+        a.rx[0] = 1.0 / (0.5 + c->relax[0] / (c->tau - 0.5));  // 1 / tau_minus
+    } else if (c->coll == LB_KBC) {
+        a.rx[0] = 2.0 * c->tau;  // 1 / beta
+    } else if (c->coll == LB_MRT) {
+        for (int k = 0; k < 3; ++k) a.rx[k] = 1.0 / c->relax[k];
+    }
     a.status = c->status;
     a.stream = c->stream;
     a.tc_table = c->tc_table;
@@ -285,7 +293,7 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     *out = nullptr;
     if (!dims) return fail(LB_ERR_ARG, "dims is null");
     if ((int)stencil < 0 || (int)stencil > 2) return fail(LB_ERR_ARG, "unknown stencil %d", (int)stencil);
-    if ((int)coll < 0 || (int)coll > 3) return fail(LB_ERR_ARG, "unknown collision %d", (int)coll);
+    if ((int)coll < 0 || (int)coll > 6) return fail(LB_ERR_ARG, "unknown collision %d", (int)coll);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_ERR_ARG, "tau must be a finite number > 1/2 (got %g)", tau);
     lb_options o;
     lb_default_options(&o);
@@ -305,8 +313,13 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if (N >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "grid of %lld nodes exceeds 2^31 - 1", (long long)N);
     if (coll == LB_LEARNED_MRT && stencil != LB_D2Q9)
         return fail(LB_ERR_UNSUPPORTED, "the learned collision is defined for D2Q9 only");
+    if (coll == LB_MRT && stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "MRT is provided for D2Q9 only");
+    if (coll == LB_KBC && stencil == LB_D3Q19)
+        return fail(LB_ERR_UNSUPPORTED, "KBC needs a tensor-product velocity set (D2Q9 or D3Q27)");
     if (o.record_every > 0 && o.layout != LB_LAYOUT_AB)
         return fail(LB_ERR_UNSUPPORTED, "recording for the adjoint needs the AB layout");
+    if (o.record_every > 0 && coll > LB_NONE)
+        return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
 
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(LB_ERR_CUDA, "no CUDA device");
@@ -326,6 +339,7 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     c->tau = tau;
     c->omega = 1.0 / tau;
     c->coll = coll;
+    if (coll == LB_MRT) c->relax[0] = c->relax[1] = c->relax[2] = 1.0;
     c->opt = o;
     c->device = dev;
     c->stream = (cudaStream_t)o.cuda_stream;
@@ -401,7 +415,8 @@ lb_status lb_set_force(lb_ctx* c, const void* F, lb_mem m)
     if (s != LB_OK) return s;
     drop_cycle(c);  // the force pointer (or its absence) is baked into the captured steps
     if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
-    if (F && c->coll == LB_LEARNED_MRT) return fail(LB_ERR_UNSUPPORTED, "the learned collision takes no force");
+    if (F && (c->coll == LB_LEARNED_MRT || c->coll == LB_KBC || c->coll == LB_MRT))
+        return fail(LB_ERR_UNSUPPORTED, "the learned, KBC and MRT collisions take no force");
     DeviceGuard guard(c->device);
     if (!F) {
         if (c->F) {
@@ -458,6 +473,24 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
     }
     c->net.swap(v);
     drop_cycle(c);  // the network is a by-value kernel argument of the captured steps
+    return LB_OK;
+}
+
+lb_status lb_set_relaxation(lb_ctx* c, const double* params, int n)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (c->coll != LB_TRT && c->coll != LB_MRT)
+        return fail(LB_ERR_STATE, "only the TRT and MRT collisions take further relaxation parameters");
+    const int need = c->coll == LB_TRT ? 1 : 3;
+    if (!params || n != need) return fail(LB_ERR_ARG, "need %d value(s), got %d", need, n);
+    for (int k = 0; k < n; ++k) {
+        if (!std::isfinite(params[k])) return fail(LB_ERR_ARG, "relaxation parameters must be finite");
+        if (c->coll == LB_TRT && !(params[k] > 0.0)) return fail(LB_ERR_ARG, "Lambda must be > 0");
+        if (c->coll == LB_MRT && !(params[k] > 0.5)) return fail(LB_ERR_ARG, "relaxation times must be > 1/2");
+    }
+    for (int k = 0; k < n; ++k) c->relax[k] = params[k];
+    drop_cycle(c);  // the rates are by-value kernel arguments of the captured steps
     return LB_OK;
 }
 
@@ -776,6 +809,7 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     if (n != c->steps) return fail(LB_ERR_STATE, "n = %lld but %lld steps were recorded", (long long)n, (long long)c->steps);
     if (n > 0 && !c->recording) return fail(LB_ERR_STATE, "no recorded run");
     if (gth && c->coll != LB_LEARNED_MRT) return fail(LB_ERR_ARG, "grad_theta needs the learned collision");
+    if (c->coll > LB_NONE) return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
     DeviceGuard guard(c->device);
     const int f64 = c->opt.storage == LB_F64;
     const int64_t rb = real_pop_bytes(c);

@@ -1,5 +1,7 @@
 // Per-node collision in registers: moments (Eq. 4), second-order equilibrium
-// (Eq. 3), BGK (Eq. 2), regularized (Latt & Chopard) and the Guo body-force source.
+// (Eq. 3), BGK (Eq. 2), regularized (Latt & Chopard), two relaxation times (Ginzburg),
+// entropic KBC (Karlin, Boesch & Chikatamarla), fixed-rate moment-space MRT (Eq. 5
+// with constant higher-moment times) and the Guo body-force source.
 // R is the arithmetic type (double or float). All values are deviations from rest,
 // delta_i = f_i - w_i (so rho - 1 = sum delta, rho u = sum c delta + F/2); the
 // arrays d[Q] are replaced by their post-collision deviations.
@@ -9,7 +11,23 @@
 
 namespace lb {
 
-enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3 };
+enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3, TRT = 4, KBC = 5, MRT = 6 };
+
+// Relaxation rates of one collision. omega = 1/tau sets the shear viscosity for every
+// model; p holds the model's other constants: TRT p[0] = 1/tau_minus; KBC p[0] = 2 tau
+// (= 1/beta); MRT p[0..2] = the rates of the three higher Hermite moments.
+template <class R>
+struct Relax {
+    R omega;
+    R p[3];
+};
+
+// collision model available for this velocity set (KBC needs a full tensor-product set)
+template <class St>
+constexpr bool coll_supported(int coll)
+{
+    return coll == KBC ? (St::Q == 9 || St::Q == 27) : coll == MRT ? St::Q == 9 : coll != LEARNED;
+}
 
 // 1/x rounded to nearest (FP32: the hardware reciprocal with IEEE rounding, not a division)
 LB_DEV float recip(float x) { return __frcp_rn(x); }
@@ -81,15 +99,130 @@ LB_DEV R guo_source(int i, const NodeMoments<St, R>& m, const R* F, R pre)
 // In-place collision of one node (f holds the deviations delta). Returns false if
 // the density is not a positive finite number (the caller raises the status flag).
 template <class St, int COLL, bool FORCE, class R>
-LB_DEV bool collide(R* f, const R* F, R omega)
+LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
 {
     if constexpr (COLL == NONE) {
         return true;
     } else {
+        const R omega = rx.omega;
         NodeMoments<St, R> m = node_moments<St, FORCE>(f, F);
         R feq[St::Q];
         const R pre = R(1) - R(0.5) * omega;
-        if constexpr (COLL == BGK) {
+        if constexpr (COLL == TRT) {
+            // symmetric half of f - f^eq relaxed by omega, antisymmetric half by omega_minus;
+            // the Guo source split the same way: its even part w [9 (c.u)(c.F) - 3 u.F] gets
+            // (1 - omega/2), its odd part 3 w c.F gets (1 - omega_minus/2)
+            equilibrium<St>(m, feq);
+            const R om_m = rx.p[0];
+            f[0] = f[0] - omega * (f[0] - feq[0]);
+            if constexpr (FORCE) f[0] += guo_source<St>(0, m, F, pre);
+#pragma unroll
+            for (int i = 1; i < St::Q; i += 2) {
+                const int o = i + 1;  // opp(i)
+                const R ni = f[i] - feq[i], no = f[o] - feq[o];
+                const R np = R(0.5) * (ni + no), nm = R(0.5) * (ni - no);
+                R vi = f[i] - omega * np - om_m * nm;
+                R vo = f[o] - omega * np + om_m * nm;
+                if constexpr (FORCE) {
+                    const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
+                    const R cF = cdotu<St>(i, F[0], F[1], St::D == 3 ? F[2] : R(0));
+                    const R uF = m.ux * F[0] + m.uy * F[1] + (St::D == 3 ? m.uz * F[2] : R(0));
+                    const R ev = pre * R(St::w(i)) * (R(9) * cu * cF - R(3) * uF);
+                    const R od = (R(1) - R(0.5) * om_m) * R(St::w(i)) * (R(3) * cF);
+                    vi += ev + od;
+                    vo += ev - od;
+                }
+                f[i] = vi;
+                f[o] = vo;
+            }
+        } else if constexpr (COLL == KBC) {
+            // D = f - f^eq = Ds + Dh: Ds carries the trace-free second natural moments of D
+            // (axis velocities: Mdev_aa / 2, edge velocities: c_a c_b M_ab / 4, rest and
+            // corners: 0), Dh the rest. f* = f - beta (2 Ds + gamma Dh), beta = omega/2,
+            // gamma = 1/beta - (2 - 1/beta) <Ds|Dh> / (<Dh|Dh> + 1e-6 <Ds|Ds>) with
+            // <X|Y> = sum X_i Y_i / f^eq_i.
+            static_assert(St::Q == 9 || St::Q == 27, "KBC needs D2Q9 or D3Q27");
+            equilibrium<St>(m, feq);
+            R D[St::Q];
+            R mxx = R(0), myy = R(0), mzz = R(0), mxy = R(0), mxz = R(0), myz = R(0);
+#pragma unroll
+            for (int i = 0; i < St::Q; ++i) {
+                D[i] = f[i] - feq[i];
+                const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
+                if (cx) mxx += D[i];
+                if (cy) myy += D[i];
+                if (St::D == 3 && cz) mzz += D[i];
+                if (cx && cy) mxy += (cx == cy) ? D[i] : -D[i];
+                if (St::D == 3 && cx && cz) mxz += (cx == cz) ? D[i] : -D[i];
+                if (St::D == 3 && cy && cz) myz += (cy == cz) ? D[i] : -D[i];
+            }
+            const R third = R(1) / R(St::D);
+            const R tr = (mxx + myy + mzz) * third;
+            const R dxx = R(0.5) * (mxx - tr), dyy = R(0.5) * (myy - tr), dzz = R(0.5) * (mzz - tr);
+            R Ds[St::Q];
+            R sh = R(0), hh = R(0), ss = R(0);
+#pragma unroll
+            for (int i = 0; i < St::Q; ++i) {
+                const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
+                const int nz = (cx != 0) + (cy != 0) + (cz != 0);
+                R s = R(0);
+                if (nz == 1) s = cx ? dxx : (cy ? dyy : dzz);
+                if (nz == 2) {
+                    if (cx && cy) s = (cx == cy) ? R(0.25) * mxy : R(-0.25) * mxy;
+                    else if (cx && cz) s = (cx == cz) ? R(0.25) * mxz : R(-0.25) * mxz;
+                    else s = (cy == cz) ? R(0.25) * myz : R(-0.25) * myz;
+                }
+                Ds[i] = s;
+                const R h = D[i] - s;
+                const R ie = recip(R(St::w(i)) + feq[i]);
+                sh += s * h * ie;
+                hh += h * h * ie;
+                ss += s * s * ie;
+            }
+            const R beta = R(0.5) * omega, ib = rx.p[0];  // p[0] = 1/beta = 2 tau
+            const R den = hh + R(1e-6) * ss;
+            const R gamma = den > R(0) ? ib - (R(2) - ib) * sh * recip(den) : R(2);
+#pragma unroll
+            for (int i = 0; i < St::Q; ++i) f[i] = f[i] - beta * (R(2) * Ds[i] + gamma * (D[i] - Ds[i]));
+        } else if constexpr (COLL == MRT) {
+            // D2Q9 Hermite moments of D = f - f^eq: stress (order 2) relaxed by omega, the
+            // three higher moments (cx^2 - 1/3) cy, cx (cy^2 - 1/3), (cx^2 - 1/3)(cy^2 - 1/3)
+            // by p[0..2]; f* = f - sum_a rate_a w_i H_a(c_i) m_a / |H_a|_w^2
+            static_assert(St::Q == 9, "MRT is D2Q9 only");
+            equilibrium<St>(m, feq);
+            R D[9];
+            R pxx = R(0), pyy = R(0), pxy = R(0), g6 = R(0), g7 = R(0), g8 = R(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                D[i] = f[i] - feq[i];
+                const int cx = St::c(i, 0), cy = St::c(i, 1);
+                const R hx = cx ? R(2.0 / 3.0) : R(-1.0 / 3.0), hy = cy ? R(2.0 / 3.0) : R(-1.0 / 3.0);
+                if (cx) pxx += D[i];
+                if (cy) pyy += D[i];
+                if (cx && cy) pxy += (cx == cy) ? D[i] : -D[i];
+                if (cy) g6 += cy > 0 ? hx * D[i] : -hx * D[i];
+                if (cx) g7 += cx > 0 ? hy * D[i] : -hy * D[i];
+                g8 += hx * hy * D[i];
+            }
+            // |H|_w^2: (cx^2 - 1/3) cy and cx (cy^2 - 1/3): 2/27; (cx^2 - 1/3)(cy^2 - 1/3): 4/81
+            g6 *= rx.p[0] * R(27.0 / 2.0);
+            g7 *= rx.p[1] * R(27.0 / 2.0);
+            g8 *= rx.p[2] * R(81.0 / 4.0);
+            const R tr = pxx + pyy;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int cx = St::c(i, 0), cy = St::c(i, 1);
+                const R hx = cx ? R(2.0 / 3.0) : R(-1.0 / 3.0), hy = cy ? R(2.0 / 3.0) : R(-1.0 / 3.0);
+                R qp = -tr * R(1.0 / 3.0);
+                if (cx) qp += pxx;
+                if (cy) qp += pyy;
+                if (cx && cy) qp += (cx == cy) ? R(2) * pxy : R(-2) * pxy;
+                R ghost = hx * hy * g8;
+                if (cy) ghost += cy > 0 ? hx * g6 : -hx * g6;
+                if (cx) ghost += cx > 0 ? hy * g7 : -hy * g7;
+                f[i] = f[i] - R(St::w(i)) * (omega * R(4.5) * qp + ghost);
+            }
+        } else if constexpr (COLL == BGK) {
             // f* = f - omega (f - f^eq) (+ S), Eq. 2 as written: the non-equilibrium part is
             // formed first. Near omega = 2 the forms (1 - omega) f + omega f^eq and
             // f^eq + (1 - omega)(f - f^eq) lose FP32 accuracy (3-20x the TGV energy error

@@ -54,7 +54,7 @@ LB_DEV void load_force(const R* F, const Geom& g, int n, R* Fl)
 // ------------------------------------------------------------------ step (K1/K2)
 template <class St, class T, int COLL, bool FORCE, int MODE>
 __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
-                                                typename Store<T>::Real omega, unsigned* status)
+                                                Relax<typename Store<T>::Real> rx, unsigned* status)
 {
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     load_node<St, MODE, RAW>(src, g, nb, id.n, f);
     R Fl[3] = {R(0), R(0), R(0)};
     if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
-    bool ok = collide<St, COLL, FORCE>(f, Fl, omega);
+    bool ok = collide<St, COLL, FORCE>(f, Fl, rx);
     store_node<St, MODE, RAW>(dst, g, nb, id.n, f);
     if (!ok) atomicOr(status, 1u);
 }
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
 // halves the memory instructions and conversions per node.
 template <class St, class T, int COLL, bool FORCE, int MODE>
 __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
-                                                     typename Store<T>::Real omega, unsigned* status)
+                                                     Relax<typename Store<T>::Real> rx, unsigned* status)
 {
     using R = typename Store<T>::Real;
     constexpr int S = sizeof(T);
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
         Pair2<R>::load(F + g.plane + n0, F0[1], F1[1]);
         if (St::D == 3) Pair2<R>::load(F + 2 * g.plane + n0, F0[2], F1[2]);
     }
-    const bool ok0 = collide<St, COLL, FORCE>(f0, F0, omega);
-    const bool ok1 = collide<St, COLL, FORCE>(f1, F1, omega);
+    const bool ok0 = collide<St, COLL, FORCE>(f0, F0, rx);
+    const bool ok1 = collide<St, COLL, FORCE>(f1, F1, rx);
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_EVEN) ? opp(i) : i;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
 // four nodes; a load shifted by -1 or +1 takes the vector at x0 (three of its values) plus
 // one scalar; a shifted store is four scalar stores.
 template <class St, class T, int COLL, bool FORCE, int MODE>
-__global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const float* F, Geom g, float omega,
+__global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const float* F, Geom g, Relax<float> rx,
                                                      unsigned* status)
 {
     static_assert(Store<T>::shifted, "four-node kernel is for half-precision storage");
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const
     }
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ok = collide<St, COLL, FORCE>(f[k], Fl[k], omega) && ok;
+    for (int k = 0; k < 4; ++k) ok = collide<St, COLL, FORCE>(f[k], Fl[k], rx) && ok;
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_EVEN) ? opp(i) : i;
@@ -546,6 +546,12 @@ __global__ void __launch_bounds__(128) k_adj_step_pair(const T* state, const typ
 }
 
 // ------------------------------------------------------------------ dispatch
+template <class R>
+inline Relax<R> relax_of(const OpArgs& a)
+{
+    return {(R)a.omega, {(R)a.rx[0], (R)a.rx[1], (R)a.rx[2]}};
+}
+
 template <class St, class T, int COLL, bool FORCE>
 cudaError_t launch_update(const OpArgs& a)
 {
@@ -553,6 +559,7 @@ cudaError_t launch_update(const OpArgs& a)
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
     const R* F = (const R*)a.F;
+    const Relax<R> rx = relax_of<R>(a);
     if constexpr (Store<T>::shifted) {
         if (COLL != NONE && a.g.nx % 4 == 0) {
             // four nodes per thread for half storage
@@ -560,12 +567,12 @@ cudaError_t launch_update(const OpArgs& a)
             const dim3 bl(quads >= 128 ? 128 : ((quads + 31) / 32) * 32, 1, 1);
             const dim3 gr((quads + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
             if (a.mode == AB)
-                k_update_quad<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+                k_update_quad<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
             else if (a.mode == AA_EVEN)
-                k_update_quad<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega,
+                k_update_quad<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx,
                                                                                      a.status);
             else
-                k_update_quad<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega,
+                k_update_quad<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx,
                                                                                     a.status);
             return cudaGetLastError();
         }
@@ -576,18 +583,18 @@ cudaError_t launch_update(const OpArgs& a)
         const dim3 bl(pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32, 1, 1);
         const dim3 gr((pairs + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
         if (a.mode == AB)
-            k_update_pair<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+            k_update_pair<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
         else if (a.mode == AA_EVEN)
-            k_update_pair<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+            k_update_pair<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
         else
-            k_update_pair<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+            k_update_pair<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
         return cudaGetLastError();
     }
     const dim3 gr = node_grid(a.g), bl = node_block(a.g);
-    if (a.mode == AB) k_update<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+    if (a.mode == AB) k_update<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
     else if (a.mode == AA_EVEN)
-        k_update<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
-    else k_update<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, (R)a.omega, a.status);
+        k_update<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
+    else k_update<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
     return cudaGetLastError();
 }
 
@@ -661,6 +668,13 @@ cudaError_t run_op_typed(const OpArgs& a)
         case BGK: return a.force ? launch_update<St, T, BGK, true>(a) : launch_update<St, T, BGK, false>(a);
         case REG: return a.force ? launch_update<St, T, REG, true>(a) : launch_update<St, T, REG, false>(a);
         case NONE: return launch_update<St, T, NONE, false>(a);
+        case TRT: return a.force ? launch_update<St, T, TRT, true>(a) : launch_update<St, T, TRT, false>(a);
+        case KBC:
+            if constexpr (coll_supported<St>(KBC)) return a.force ? cudaErrorInvalidValue : launch_update<St, T, KBC, false>(a);
+            return cudaErrorInvalidValue;
+        case MRT:
+            if constexpr (coll_supported<St>(MRT)) return a.force ? cudaErrorInvalidValue : launch_update<St, T, MRT, false>(a);
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
         }
     }

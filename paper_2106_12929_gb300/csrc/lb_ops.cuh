@@ -45,6 +45,7 @@ struct OpArgs {
     const void* tc_table = nullptr; // learned collision on tensor cores: packed weight table (device)
     Geom g{};
     double omega = 1.0;
+    double rx[3] = {0.0, 0.0, 0.0};  // further constants of the collision (lb_collide.cuh, Relax)
     unsigned* status = nullptr;
     double* partials = nullptr;
     cudaStream_t stream = nullptr;

@@ -43,7 +43,7 @@ class Lattice:
     """One periodic lattice advanced by liblb on one GPU.
 
     stencil: "D2Q9" | "D3Q19" | "D3Q27"; dims: (nx, ny, nz) with nz = 1 in 2D;
-    tau > 1/2; collision: "bgk" | "regularized" | "learned" | "none";
+    tau > 1/2; collision: "bgk" | "regularized" | "learned" | "none" | "trt" | "kbc" | "mrt";
     storage: "f64" | "f32" | "f16" | "bf16" (the half types store f_i - w_i);
     layout: "ab" (two buffers) | "aa" (in place); record_every > 0 keeps
     checkpoints for ``step_adjoint``; learned_tc runs the learned collision's network
@@ -144,6 +144,12 @@ class Lattice:
     def set_mlp(self, params):
         t = _to_tensor(params)
         _lib.check(self._lib.lb_set_mlp(self._h, t.data_ptr(), t.numel(), _mem_code(t)), "lb_set_mlp")
+        return self
+
+    def set_relaxation(self, params):
+        """TRT: [Lambda]; MRT: [tau_6, tau_7, tau_8] (see lb_set_relaxation)."""
+        v = (ctypes.c_double * len(params))(*[float(x) for x in params])
+        _lib.check(self._lib.lb_set_relaxation(self._h, v, len(params)), "lb_set_relaxation")
         return self
 
     def set_populations(self, f):
