@@ -204,13 +204,15 @@ def run_only(args):
     stencil, storage, layout, coll = ONLY[args.only]
     dims, tau, rho, u = workload(stencil, args.grid)
     N = int(np.prod(dims))
-    lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout, graphs=not args.no_graphs)
+    lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout, graphs=not args.no_graphs,
+                  nodes_per_thread=args.nodes_per_thread)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     lat.step(args.warmup)
     t = time_steps(lat, args.steps, torch.cuda.current_stream())
     lat.check()
     g = N * args.steps / t / 1e9
     print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "graphs": not args.no_graphs,
+                      "nodes_per_thread": args.nodes_per_thread,
                       "glups": round(g, 3),
                       "hbm_frac": round(g * BYTES_PER_LU[(stencil, storage)] / measured_peak_hbm()[0], 4)}))
 
@@ -483,6 +485,8 @@ def main():
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     ap.add_argument("--no-graphs", action="store_true", help="--only: one launch per kernel instead of graph replay")
+    ap.add_argument("--nodes-per-thread", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="--only: stream-collide launch shape (0 = chosen from the grid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -119,9 +119,15 @@ typedef struct {
     int graphs;           /* 1 (default): lb_step(n >= 2) without checkpoints captures two steps once
                              into a CUDA graph and replays it (one launch per pair of steps instead
                              of one per kernel; same kernels, same results); 0 = direct launches */
+    int nodes_per_thread; /* shape of the stream-collide launch: 0 (default) = chosen from the grid
+                             (one node per thread in 32-thread blocks when the grid has fewer rows
+                             than SMs, else four per thread for half storage, two otherwise);
+                             1, 2 or 4 = forced, falling back to the next smaller shape the grid
+                             allows (2 needs an even nx; 4 needs half storage and nx % 4 == 0).
+                             Every shape gives bit-identical results */
 } lb_options;
 
-/* Fill *opt with the defaults listed above (learned_tc = 0, graphs = 1). */
+/* Fill *opt with the defaults listed above (learned_tc = 0, graphs = 1, nodes_per_thread = 0). */
 LB_API void lb_default_options(lb_options* opt);
 
 /* Create a context: validate, allocate the population buffer(s) on opt->device and

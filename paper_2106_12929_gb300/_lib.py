@@ -39,7 +39,7 @@ class LBError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("layout", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("check_every", ctypes.c_int), ("record_every", ctypes.c_int),
-                ("learned_tc", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("learned_tc", ctypes.c_int), ("graphs", ctypes.c_int), ("nodes_per_thread", ctypes.c_int)]
 
 
 _lock = threading.Lock()

@@ -62,6 +62,7 @@ struct lb_ctx {
     double relax[3] = {0.25, 0.0, 0.0};  // lb_set_relaxation values (TRT: Lambda; MRT: three tau_g)
     lb_options opt{};
     int device = 0;
+    int sms = 0;  // multiprocessors of the device
     cudaStream_t stream = nullptr;
     lb::Geom g{};
 
@@ -147,6 +148,8 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     a.F = c->F;
     a.g = c->g;
     a.omega = c->omega;
+    a.npt = c->opt.nodes_per_thread;
+    a.sms = c->sms;
     if (c->coll == LB_TRT) {
         a.rx[0] = 1.0 / (0.5 + c->relax[0] / (c->tau - 0.5));  // 1 / tau_minus
     } else if (c->coll == LB_KBC) {
@@ -284,6 +287,7 @@ void lb_default_options(lb_options* o)
     o->record_every = 0;
     o->learned_tc = 0;
     o->graphs = 1;
+    o->nodes_per_thread = 0;
 }
 
 lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau, lb_collision coll,
@@ -303,6 +307,8 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if (o.check_every < 0 || o.record_every < 0) return fail(LB_ERR_ARG, "negative check_every / record_every");
     if (o.learned_tc != 0 && o.learned_tc != 1) return fail(LB_ERR_ARG, "learned_tc must be 0 or 1");
     if (o.graphs != 0 && o.graphs != 1) return fail(LB_ERR_ARG, "graphs must be 0 or 1");
+    if (o.nodes_per_thread != 0 && o.nodes_per_thread != 1 && o.nodes_per_thread != 2 && o.nodes_per_thread != 4)
+        return fail(LB_ERR_ARG, "nodes_per_thread must be 0, 1, 2 or 4");
     if (o.learned_tc && (coll != LB_LEARNED_MRT || o.storage == LB_F64))
         return fail(LB_ERR_UNSUPPORTED, "learned_tc needs the learned collision with FP32 or half storage");
     const int D = stencil == LB_D2Q9 ? 2 : 3;
@@ -342,6 +348,7 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if (coll == LB_MRT) c->relax[0] = c->relax[1] = c->relax[2] = 1.0;
     c->opt = o;
     c->device = dev;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c->sms = 0;
     c->stream = (cudaStream_t)o.cuda_stream;
     c->g.nx = (int)dims[0];
     c->g.ny = (int)dims[1];

@@ -32,6 +32,9 @@ constexpr bool coll_supported(int coll)
 // 1/x rounded to nearest (FP32: the hardware reciprocal with IEEE rounding, not a division)
 LB_DEV float recip(float x) { return __frcp_rn(x); }
 LB_DEV double recip(double x) { return 1.0 / x; }
+// 1/x where a few ulp suffice (FP32: the fast approximate division intrinsic)
+LB_DEV float recip_fast(float x) { return __fdividef(1.0f, x); }
+LB_DEV double recip_fast(double x) { return 1.0 / x; }
 
 template <class St, class R>
 struct NodeMoments {
@@ -159,31 +162,54 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
             const R third = R(1) / R(St::D);
             const R tr = (mxx + myy + mzz) * third;
             const R dxx = R(0.5) * (mxx - tr), dyy = R(0.5) * (myy - tr), dzz = R(0.5) * (mzz - tr);
+            // entropic weights 1/f^eq_i = 1/(w_i rho P_i), P_i = 1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u.
+            // An opposite pair has P = A +- B (A = 1 + 4.5 (c.u)^2 - 1.5 u.u, B = 3 c.u), so one
+            // reciprocal 1/(A^2 - B^2) serves both: 1/P_i = (A - B)/(A^2 - B^2), 1/P_opp = (A + B)/(...).
+            const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+            const R irho = recip_fast(m.rho);
+            R ie[St::Q];
+            ie[0] = irho * R(1.0 / St::w(0)) * recip_fast(R(1) - uu15);
+#pragma unroll
+            for (int i = 1; i < St::Q; i += 2) {
+                const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
+                const R A = R(1) - uu15 + R(4.5) * cu * cu, B = R(3) * cu;
+                const R r = irho * R(1.0 / St::w(i)) * recip_fast(A * A - B * B);  // w_i = w_opp(i)
+                ie[i] = (A - B) * r;
+                ie[i + 1] = (A + B) * r;
+            }
             R Ds[St::Q];
             R sh = R(0), hh = R(0), ss = R(0);
 #pragma unroll
             for (int i = 0; i < St::Q; ++i) {
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
                 const int nz = (cx != 0) + (cy != 0) + (cz != 0);
-                R s = R(0);
-                if (nz == 1) s = cx ? dxx : (cy ? dyy : dzz);
-                if (nz == 2) {
-                    if (cx && cy) s = (cx == cy) ? R(0.25) * mxy : R(-0.25) * mxy;
+                if (nz == 1 || nz == 2) {
+                    R s;
+                    if (nz == 1) s = cx ? dxx : (cy ? dyy : dzz);
+                    else if (cx && cy) s = (cx == cy) ? R(0.25) * mxy : R(-0.25) * mxy;
                     else if (cx && cz) s = (cx == cz) ? R(0.25) * mxz : R(-0.25) * mxz;
                     else s = (cy == cz) ? R(0.25) * myz : R(-0.25) * myz;
+                    Ds[i] = s;
+                    const R h = D[i] - s;
+                    const R si = s * ie[i];
+                    sh += si * h;
+                    ss += si * s;
+                    hh += h * h * ie[i];
+                } else {
+                    Ds[i] = R(0);
+                    hh += D[i] * D[i] * ie[i];
                 }
-                Ds[i] = s;
-                const R h = D[i] - s;
-                const R ie = recip(R(St::w(i)) + feq[i]);
-                sh += s * h * ie;
-                hh += h * h * ie;
-                ss += s * s * ie;
             }
             const R beta = R(0.5) * omega, ib = rx.p[0];  // p[0] = 1/beta = 2 tau
             const R den = hh + R(1e-6) * ss;
             const R gamma = den > R(0) ? ib - (R(2) - ib) * sh * recip(den) : R(2);
+            const R bg = beta * gamma, b2 = R(2) * beta;
 #pragma unroll
-            for (int i = 0; i < St::Q; ++i) f[i] = f[i] - beta * (R(2) * Ds[i] + gamma * (D[i] - Ds[i]));
+            for (int i = 0; i < St::Q; ++i) {
+                const int nz = (St::c(i, 0) != 0) + (St::c(i, 1) != 0) + (St::c(i, 2) != 0);
+                if (nz == 1 || nz == 2) f[i] = f[i] - (b2 * Ds[i] + bg * (D[i] - Ds[i]));
+                else f[i] = f[i] - bg * D[i];
+            }
         } else if constexpr (COLL == MRT) {
             // D2Q9 Hermite moments of D = f - f^eq: stress (order 2) relaxed by omega, the
             // three higher moments (cx^2 - 1/3) cy, cx (cy^2 - 1/3), (cx^2 - 1/3)(cy^2 - 1/3)

@@ -552,6 +552,34 @@ inline Relax<R> relax_of(const OpArgs& a)
     return {(R)a.omega, {(R)a.rx[0], (R)a.rx[1], (R)a.rx[2]}};
 }
 
+// the two-nodes-per-thread grid (up to 256 x positions per block, one block row per (y, z))
+// would leave SMs without a block. Measured on 152 SMs: D2Q9 FP64 64^2 6.1 us per step with
+// one node per thread in 32-thread blocks against 9.2 us with two; D2Q9 FP32 256^2 (256 rows)
+// is 1-2 % faster with two.
+inline bool small_grid(const OpArgs& a)
+{
+    const int64_t blocks = (int64_t)((a.g.nx + 255) / 256) * a.g.ny * a.g.nz;
+    return a.sms > 0 && blocks < (int64_t)a.sms;
+}
+
+// nodes per thread of the stream-collide launch: the requested shape (a.npt), or from the
+// grid when a.npt == 0, lowered to what nx and the storage allow
+template <class St, class T, int COLL>
+inline int update_shape(const OpArgs& a)
+{
+    if (COLL == NONE) return 1;  // streaming only: stored values move untouched, one per thread
+    int npt = a.npt;
+    if (npt == 0) {
+        // four per thread for half storage, except D3Q27 KBC, whose 27 entropic weights per
+        // node make four nodes too many live registers
+        const bool quad_ok = Store<T>::shifted && !(St::Q == 27 && COLL == KBC);
+        npt = small_grid(a) ? 1 : (quad_ok ? 4 : 2);
+    }
+    if (npt == 4 && !(Store<T>::shifted && a.g.nx % 4 == 0)) npt = 2;
+    if (npt == 2 && a.g.nx % 2 != 0) npt = 1;
+    return npt;
+}
+
 template <class St, class T, int COLL, bool FORCE>
 cudaError_t launch_update(const OpArgs& a)
 {
@@ -560,8 +588,9 @@ cudaError_t launch_update(const OpArgs& a)
     T* dst = (T*)a.dst;
     const R* F = (const R*)a.F;
     const Relax<R> rx = relax_of<R>(a);
+    const int npt = update_shape<St, T, COLL>(a);
     if constexpr (Store<T>::shifted) {
-        if (COLL != NONE && a.g.nx % 4 == 0) {
+        if (npt == 4) {
             // four nodes per thread for half storage
             const int quads = a.g.nx / 4;
             const dim3 bl(quads >= 128 ? 128 : ((quads + 31) / 32) * 32, 1, 1);
@@ -577,7 +606,7 @@ cudaError_t launch_update(const OpArgs& a)
             return cudaGetLastError();
         }
     }
-    if (COLL != NONE && a.g.nx % 2 == 0) {
+    if (npt == 2) {
         // two nodes per thread; 128 threads cover 256 x positions
         const int pairs = a.g.nx / 2;
         const dim3 bl(pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32, 1, 1);
@@ -590,7 +619,10 @@ cudaError_t launch_update(const OpArgs& a)
             k_update_pair<St, T, COLL, FORCE, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
         return cudaGetLastError();
     }
-    const dim3 gr = node_grid(a.g), bl = node_block(a.g);
+    // one node per thread; on a grid too small to give every SM two rows, 32-thread blocks
+    // spread the nodes over more SMs (the FP64 collision is ALU-bound on this part)
+    const dim3 bl = small_grid(a) ? dim3(32, 1, 1) : node_block(a.g);
+    const dim3 gr((a.g.nx + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
     if (a.mode == AB) k_update<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
     else if (a.mode == AA_EVEN)
         k_update<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);

@@ -46,6 +46,8 @@ struct OpArgs {
     Geom g{};
     double omega = 1.0;
     double rx[3] = {0.0, 0.0, 0.0};  // further constants of the collision (lb_collide.cuh, Relax)
+    int npt = 0;                     // stream-collide nodes per thread: 0 = from the grid, 1, 2, 4
+    int sms = 0;                     // multiprocessors of the device
     unsigned* status = nullptr;
     double* partials = nullptr;
     cudaStream_t stream = nullptr;

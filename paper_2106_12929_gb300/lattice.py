@@ -48,13 +48,15 @@ class Lattice:
     layout: "ab" (two buffers) | "aa" (in place); record_every > 0 keeps
     checkpoints for ``step_adjoint``; learned_tc runs the learned collision's network
     on the tensor cores (BF16 operands, FP32 accumulation; forward only); graphs
-    replays ``step(n)`` as captured two-step CUDA graphs (off: one launch per kernel).
+    replays ``step(n)`` as captured two-step CUDA graphs (off: one launch per kernel);
+    nodes_per_thread forces the stream-collide launch shape (0: chosen from the grid).
     The context runs on torch's current CUDA stream at construction time.
     """
 
     def __init__(self, stencil: str, dims, tau: float, collision: str = "bgk", storage: str = "f32",
                  layout: str = "ab", device: int | None = None, stream=None, check_every: int = 0,
-                 record_every: int = 0, learned_tc: bool = False, graphs: bool = True):
+                 record_every: int = 0, learned_tc: bool = False, graphs: bool = True,
+                 nodes_per_thread: int = 0):
         self._lib = _lib.load()
         self.stencil = stencil
         self.dims = tuple(int(v) for v in dims)
@@ -83,6 +85,7 @@ class Lattice:
         opt.record_every = record_every
         opt.learned_tc = int(bool(learned_tc))
         opt.graphs = int(bool(graphs))
+        opt.nodes_per_thread = int(nodes_per_thread)
         dims_arr = (ctypes.c_int64 * 3)(*self.dims)
         h = ctypes.c_void_p()
         _lib.check(self._lib.lb_create(ctypes.byref(h), _lib.STENCIL[stencil], dims_arr, ctypes.c_double(tau),

@@ -13,7 +13,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-# odd nx: one node per thread; even nx: two per thread; nx % 4 == 0 with half storage: four
+# grids with odd and even nx, one and several blocks per row; the launch shape (nodes per
+# thread) is forced by the tests' npt parameter
 TINY = {"D2Q9": [(5, 4, 1), (6, 5, 1), (33, 5, 1), (2, 3, 1), (8, 3, 1)],
         "D3Q19": [(5, 4, 3), (6, 5, 3), (2, 3, 3)],
         "D3Q27": [(5, 4, 3), (4, 5, 3), (7, 6, 5), (2, 2, 3)]}
@@ -51,8 +52,8 @@ def near_eq(name, dims, seed, eps=0.05):
     return oracle.init_eq(name, dims, rho, u) + eps * 0.1 * w[:, None] * lbinputs.random_field((len(w), N), seed + 1)
 
 
-def make(name, dims, tau, coll, params, storage, layout="ab"):
-    lat = L(name, dims, tau, coll, storage=storage, layout=layout)
+def make(name, dims, tau, coll, params, storage, layout="ab", npt=0):
+    lat = L(name, dims, tau, coll, storage=storage, layout=layout, nodes_per_thread=npt)
     if params is not None:
         lat.set_relaxation(params)
     return lat
@@ -60,13 +61,14 @@ def make(name, dims, tau, coll, params, storage, layout="ab"):
 
 @pytest.mark.parametrize("name,coll,params,forced", CASES)
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_fp64_matches_oracle(name, coll, params, forced, layout):
+@pytest.mark.parametrize("npt", [1, 2])
+def test_fp64_matches_oracle(name, coll, params, forced, layout, npt):
     d, c, w, _ = oracle.stencil(name)
     for dims in TINY[name]:
         N = oracle.n_nodes(dims)
         f0 = near_eq(name, dims, seed=71)
         F = lbinputs.random_field((d, N), seed=72, amp=1e-3) if forced else None
-        lat = make(name, dims, 0.62, coll, params, "f64", layout)
+        lat = make(name, dims, 0.62, coll, params, "f64", layout, npt)
         if forced:
             lat.set_force(F)
         lat.set_populations(f0)
@@ -84,7 +86,8 @@ def test_fp64_matches_oracle(name, coll, params, forced, layout):
     ("D2Q9", 64, "kbc", None, 0.52), ("D3Q19", 48, "trt", [3.0 / 16.0], None), ("D3Q27", 24, "kbc", None, 0.55),
     ("D3Q27", 24, "trt", None, 0.55)])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_fp32_100_steps_within_1e_5(name, n, coll, params, tau, layout):
+@pytest.mark.parametrize("npt", [1, 2])
+def test_fp32_100_steps_within_1e_5(name, n, coll, params, tau, layout, npt):
     d, c, w, _ = oracle.stencil(name)
     if name == "D2Q9":
         dims, rho, u = lbinputs.taylor_green_2d(n, u0=0.05)
@@ -93,7 +96,7 @@ def test_fp32_100_steps_within_1e_5(name, n, coll, params, tau, layout):
         dims, rho, u = lbinputs.taylor_green_3d(n, u0=u0)
         if tau is None:
             tau = lbinputs.tau_from_reynolds(1600.0, u0, n)
-    lat = make(name, dims, tau, coll, params, "f32", layout)
+    lat = make(name, dims, tau, coll, params, "f32", layout, npt)
     lat.init_from_moments(rho, u)
     lat.step(100)
     ref = oracle.step(name, dims, tau, coll, oracle.init_eq(name, dims, rho, u), nsteps=100, params=params)
@@ -102,11 +105,12 @@ def test_fp32_100_steps_within_1e_5(name, n, coll, params, tau, layout):
 
 @pytest.mark.parametrize("coll,params", [("trt", None), ("kbc", None), ("mrt", [0.9, 0.9, 1.2])])
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
-def test_half_storage_tracks_oracle(coll, params, storage, tol):
+@pytest.mark.parametrize("npt", [1, 4])
+def test_half_storage_tracks_oracle(coll, params, storage, tol, npt):
     name = "D2Q9"
     d, c, w, _ = oracle.stencil(name)
     dims, rho, u = lbinputs.taylor_green_2d(64, u0=0.05)
-    lat = make(name, dims, 0.8, coll, params, storage)
+    lat = make(name, dims, 0.8, coll, params, storage, npt=npt)
     lat.init_from_moments(rho, u)
     lat.step(50)
     ref = oracle.step(name, dims, 0.8, coll, oracle.init_eq(name, dims, rho, u), nsteps=50, params=params)

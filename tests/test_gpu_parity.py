@@ -16,7 +16,8 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 STENCILS = ["D2Q9", "D3Q19", "D3Q27"]
-# odd nx runs the one-node-per-thread kernel, even nx the two-nodes-per-thread one
+# odd and even nx, ragged rows; the stream-collide launch shape is forced by the npt
+# parameter where a test has one (the default picks one node per thread on grids this small)
 TINY = {"D2Q9": [(5, 4, 1), (6, 5, 1), (33, 5, 1), (2, 3, 1), (258, 3, 1)],
         "D3Q19": [(5, 4, 3), (6, 5, 3), (7, 6, 5), (2, 3, 3)],
         "D3Q27": [(5, 4, 3), (4, 5, 3), (7, 6, 5), (2, 2, 3)]}
@@ -90,13 +91,14 @@ def test_streaming_half_storage_moves_values_unchanged(name, storage):
 @pytest.mark.parametrize("coll", ["bgk", "regularized"])
 @pytest.mark.parametrize("forced", [False, True])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_collision_fp64_matches_oracle(name, coll, forced, layout):
+@pytest.mark.parametrize("npt", [1, 2])
+def test_collision_fp64_matches_oracle(name, coll, forced, layout, npt):
     d, c, w, _ = oracle.stencil(name)
     for dims in TINY[name][:4]:
         N = oracle.n_nodes(dims)
         f0 = near_eq(name, dims, seed=11)
         F = lbinputs.random_field((d, N), seed=12, amp=1e-3) if forced else None
-        lat = L(name, dims, 0.67, coll, storage="f64", layout=layout)
+        lat = L(name, dims, 0.67, coll, storage="f64", layout=layout, nodes_per_thread=npt)
         if forced:
             lat.set_force(F)
         lat.set_populations(f0)
@@ -133,7 +135,8 @@ def test_aa_matches_ab_bit_exact(name, which):
 @pytest.mark.parametrize("name,n,coll,tau", [("D2Q9", 64, "bgk", 0.8), ("D3Q19", 64, "bgk", None),
                                              ("D3Q27", 24, "regularized", 0.55)])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_fp32_100_steps_within_1e_5(name, n, coll, tau, layout):
+@pytest.mark.parametrize("npt", [1, 2])
+def test_fp32_100_steps_within_1e_5(name, n, coll, tau, layout, npt):
     d, c, w, _ = oracle.stencil(name)
     if name == "D2Q9":
         dims, rho, u = lbinputs.taylor_green_2d(n, u0=0.05)
@@ -142,7 +145,7 @@ def test_fp32_100_steps_within_1e_5(name, n, coll, tau, layout):
         dims, rho, u = lbinputs.taylor_green_3d(n, u0=u0)
         if tau is None:
             tau = lbinputs.tau_from_reynolds(1600.0, u0, n)
-    lat = L(name, dims, tau, coll, storage="f32", layout=layout)
+    lat = L(name, dims, tau, coll, storage="f32", layout=layout, nodes_per_thread=npt)
     lat.init_from_moments(rho, u)
     lat.step(100)
     ref = oracle.step(name, dims, tau, coll, oracle.init_eq(name, dims, rho, u), nsteps=100)
@@ -201,11 +204,12 @@ def test_init_from_device_fp32_arrays():
 
 # ------------------------------------------------------------------ half-precision storage
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
-def test_half_storage_tracks_oracle(storage, tol):
+@pytest.mark.parametrize("npt", [1, 2, 4])
+def test_half_storage_tracks_oracle(storage, tol, npt):
     name = "D2Q9"
     d, c, w, _ = oracle.stencil(name)
     dims, rho, u = lbinputs.taylor_green_2d(64, u0=0.05)
-    lat = L(name, dims, 0.8, "bgk", storage=storage)
+    lat = L(name, dims, 0.8, "bgk", storage=storage, nodes_per_thread=npt)
     lat.init_from_moments(rho, u)
     lat.step(50)
     ref = oracle.step(name, dims, 0.8, "bgk", oracle.init_eq(name, dims, rho, u), nsteps=50)
@@ -588,3 +592,37 @@ def test_graph_replay_equals_single_steps(layout, coll, storage):
     for _ in range(4):
         b.step(1)
     np.testing.assert_array_equal(gpu_pops(a), gpu_pops(b))
+
+
+# ------------------------------------------------------------------ launch shapes
+@pytest.mark.parametrize("name,dims", [("D2Q9", (12, 5, 1)), ("D3Q19", (8, 5, 3)), ("D3Q27", (8, 3, 4))])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_launch_shapes_are_bit_identical(name, dims, storage, layout):
+    """One, two and four nodes per thread (and the automatic choice) run the same per-node
+    arithmetic. The compiler may contract a multiply and an add into one FMA differently in
+    the three kernels, so the states agree to the last bits of the arithmetic type after a
+    few steps: FP64 1e-14, FP32 1e-6, half storage one quantisation step of the stored
+    deviation (1e-4), all relative to w_i."""
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    f0 = near_eq(name, dims, seed=101)
+    F = lbinputs.random_field((d, N), seed=102, amp=1e-3)
+    colls = [("bgk", True), ("regularized", True), ("trt", True), ("none", False)]
+    if name != "D3Q19":
+        colls.append(("kbc", False))
+    if name == "D2Q9":
+        colls.append(("mrt", False))
+    for coll, forced in colls:
+        out = []
+        for npt in (0, 1, 2, 4):
+            lat = L(name, dims, 0.6, coll, storage=storage, layout=layout, nodes_per_thread=npt)
+            if forced:
+                lat.set_force(F)
+            lat.set_populations(f0)
+            lat.step(3)
+            out.append(gpu_pops(lat))
+            lat.close()
+        tol = {"f64": 1e-14, "f32": 1e-6}.get(storage, 1e-4)
+        for o in out[1:]:
+            assert werr(o, out[0], w) <= tol, coll

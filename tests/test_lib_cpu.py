@@ -66,6 +66,7 @@ def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
     (dict(storage=5), 1),
     (dict(layout=1, record_every=5), 6),    # recording needs the AB layout
     (dict(graphs=2), 1),
+    (dict(nodes_per_thread=3), 1),
     (dict(coll=7), 1),
     (dict(stencil=1, dims=(4, 4, 4), coll=5), 6),  # KBC needs D2Q9 or D3Q27
     (dict(stencil=2, dims=(4, 4, 4), coll=6), 6),  # MRT is D2Q9 only
@@ -73,7 +74,7 @@ def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
     (dict(learned_tc=1), 6),                # tensor-core network needs the learned collision
 ])
 def test_create_rejects_bad_arguments_without_gpu(lib, kw, expect):
-    opt_keys = {"storage", "layout", "record_every", "check_every", "graphs", "learned_tc"}
+    opt_keys = {"storage", "layout", "record_every", "check_every", "graphs", "learned_tc", "nodes_per_thread"}
     opt = {k: v for k, v in kw.items() if k in opt_keys}
     args = {k: v for k, v in kw.items() if k not in opt_keys}
     rc, h = _create(lib, **args, **opt)
