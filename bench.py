@@ -329,7 +329,8 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
             g * BYTES_PER_LU[("D3Q19", storage)] / measured_peak_hbm()[0], 4)
         lat.close()
     out["f16_over_f32_glups"] = round(out["d3q19_f16_ab_glups"] / glups_ab, 3)
-    for key in ("d3q27_reg_f32", "d3q27_reg_f16", "d2q9_f32", "d2q9_f16"):
+    for key in ("d3q27_reg_f32", "d3q27_reg_f16", "d2q9_f32", "d2q9_f16", "d3q19_trt_f32", "d3q27_kbc_f32",
+                "d3q27_kbc_f16", "d2q9_kbc_f32", "d2q9_mrt_f32"):
         st, sto, lay, coll = ONLY[key]
         dims2, tau2, r2, u2 = workload(st, None)
         lat = Lattice(st, dims2, tau2, coll, storage=sto, layout=lay)
