@@ -55,7 +55,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            for name in ("ora_stencil", "ora_init_eq", "ora_step", "ora_collide_node", "ora_moments",
+            for name in ("ora_stencil", "ora_init_eq", "ora_step", "ora_step_walls", "ora_collide_node", "ora_moments",
                          "ora_reduce", "ora_adjoint", "ora_seed_moments", "ora_loss_energy",
                          "ora_loss_eq6", "ora_vorticity", "ora_mlp_omega", "ora_invariants",
                          "ora_guo_source", "ora_num_threads"):
@@ -135,6 +135,25 @@ def step(name, dims, tau, collision, f, nsteps=1, F=None, mlp=None, params=None)
     mlp = _cpar(collision, mlp, params)
     _check(_load().ora_step(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
                             COLLISIONS[collision], _p(F), _p(mlp), _p(out), ctypes.c_int64(nsteps)), "step")
+    return out
+
+
+def step_walls(name, dims, tau, collision, f, mask, nsteps=1, F=None, wall_u=None, params=None, mlp=None):
+    """Like ``step`` with solid nodes (mask[N] nonzero) and halfway bounce-back; wall_u[d][N]
+    is the velocity of each solid node (moving walls) or None."""
+    d, _, w, _ = stencil(name)
+    N = n_nodes(dims)
+    out = _arr(f, (len(w), N)).copy()
+    F = None if F is None else _arr(F, (d, N))
+    m = np.ascontiguousarray(np.asarray(mask).reshape(N) != 0, dtype=np.uint8)
+    wu = None
+    if wall_u is not None:
+        wu = np.zeros((3, N))
+        wu[:d] = _arr(wall_u, (d, N))
+    _check(_load().ora_step_walls(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
+                                  COLLISIONS[collision], _p(F), _p(_cpar(collision, mlp, params)),
+                                  m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _p(wu), _p(out),
+                                  ctypes.c_int64(nsteps)), "step_walls")
     return out
 
 

@@ -591,6 +591,60 @@ int ora_step(int st, const int64_t* dims, double tau, int coll, const double* F,
     return ORA_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 with solid nodes: halfway bounce-back (the paper lists boundary      */
+/* conditions without formulas, Sec. 2.2; textbook form, Krueger et al. 2016, */
+/* Ladd's moving-wall term). A fluid node collides and pushes f*_i to x + c_i; */
+/* where x + c_i is solid, the population returns to x in the opposite slot:  */
+/*   f_opp(i)(x, t + 1) = f*_i(x, t) - 2 w_i (c_i . u_w) / c_s^2,             */
+/* with u_w the wall velocity stored at the solid node x + c_i (wall density  */
+/* taken as 1). Solid nodes do not collide; they hold the rest equilibrium    */
+/* w_i. mask[N]: nonzero = solid. wall_u[3][N] (or NULL = resting walls).     */
+/* ------------------------------------------------------------------------ */
+int ora_step_walls(int st, const int64_t* dims, double tau, int coll, const double* F, const double* cpar,
+                   const unsigned char* mask, const double* wall_u, double* f, int64_t nsteps)
+{
+    stencil_t s;
+    mrt_t mt;
+    params_t P;
+    int64_t N, t, n;
+    double* g;
+    if (!mask) return ORA_ERR_ARG;
+    if (stencil_get(st, &s) || check_dims(&s, dims)) return ORA_ERR_ARG;
+    if (make_params(&P, &s, &mt, tau, coll, cpar, F)) return ORA_ERR_ARG;
+    N = dims[0] * dims[1] * dims[2];
+    g = (double*)malloc(sizeof(double) * (size_t)s.q * (size_t)N);
+    if (!g) return ORA_ERR_OOM;
+    for (t = 0; t < nsteps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (n = 0; n < N; ++n) {
+            double fl[27], out[27], Fl[3];
+            int i, a;
+            if (mask[n]) {
+                for (i = 0; i < s.q; ++i) g[(int64_t)i * N + n] = s.w[i];
+                continue;
+            }
+            gather(&s, f, N, n, fl);
+            if (F) node_force(&s, F, N, n, Fl);
+            collide_node(&P, fl, F ? Fl : NULL, out);
+            for (i = 0; i < s.q; ++i) {
+                int64_t y = shifted_node(dims, n, s.c[i][0], s.c[i][1], s.c[i][2]);
+                if (mask[y]) {
+                    double cu = 0.0;
+                    if (wall_u)
+                        for (a = 0; a < s.d; ++a) cu += s.c[i][a] * wall_u[(int64_t)a * N + y];
+                    g[(int64_t)s.opp[i] * N + n] = out[i] - 2.0 * s.w[i] * cu / cs2;
+                } else {
+                    g[(int64_t)i * N + y] = out[i];
+                }
+            }
+        }
+        memcpy(f, g, sizeof(double) * (size_t)s.q * (size_t)N);
+    }
+    free(g);
+    return ORA_OK;
+}
+
 /* f_i = f_i^eq(rho, u) at every node (equilibrium initialisation) */
 int ora_init_eq(int st, const int64_t* dims, const double* rho, const double* u, double* f)
 {
