@@ -173,7 +173,9 @@ ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, col
     "d3q27_kbc_f32": ("D3Q27", "f32", "ab", "kbc"), "d3q27_kbc_f16": ("D3Q27", "f16", "ab", "kbc"),
     "d2q9_kbc_f32": ("D2Q9", "f32", "ab", "kbc"), "d2q9_mrt_f32": ("D2Q9", "f32", "ab", "mrt"),
     "d2q9_trt_f32": ("D2Q9", "f32", "ab", "trt"),
+    "d3q19_duct_f32": ("D3Q19", "f32", "ab", "bgk"), "d3q19_duct_f16": ("D3Q19", "f16", "ab", "bgk"),
 }
+DUCT = ("d3q19_duct_f32", "d3q19_duct_f16")  # walls: duct with a sphere (radius n/8), driven by F_x
 
 
 def workload(stencil: str, n: int | None):
@@ -207,14 +209,22 @@ def run_only(args):
     lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout, graphs=not args.no_graphs,
                   nodes_per_thread=args.nodes_per_thread)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    if args.only in DUCT:
+        F = np.zeros((3, N))
+        F[0] = 1e-6
+        lat.set_force(torch.tensor(F, dtype=torch.float32, device="cuda"))
+        lat.set_solid(lbinputs.duct_with_obstacle(dims, radius=dims[0] / 8.0))
     lat.step(args.warmup)
     t = time_steps(lat, args.steps, torch.cuda.current_stream())
     lat.check()
     g = N * args.steps / t / 1e9
+    bpl = BYTES_PER_LU[(stencil, storage)]
+    if args.only in DUCT:  # + force read (arithmetic type) + the 4-byte link word of every node
+        bpl += 3 * (8 if storage == "f64" else 4) + 4
     print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "graphs": not args.no_graphs,
                       "nodes_per_thread": args.nodes_per_thread,
                       "glups": round(g, 3),
-                      "hbm_frac": round(g * BYTES_PER_LU[(stencil, storage)] / measured_peak_hbm()[0], 4)}))
+                      "hbm_frac": round(g * bpl / measured_peak_hbm()[0], 4)}))
 
 
 def run_ours(args):

@@ -167,6 +167,18 @@ LB_API lb_status lb_set_mlp(lb_ctx* ctx, const void* params, int64_t n_params, l
  * wrong count or value. Applies from the next lb_step. */
 LB_API lb_status lb_set_relaxation(lb_ctx* ctx, const double* params, int n);
 
+/* Solid nodes with halfway bounce-back (the paper lists boundary conditions without
+ * formulas, Sec. 2.2; textbook form with Ladd's moving-wall term). mask: N bytes in x-fastest
+ * node order, nonzero = solid, on the host or the device as mem says (the element type of
+ * mem applies to wall_u only). A fluid node's population that would stream into a solid
+ * node returns to it in the opposite direction at the next step:
+ *   f_opp(i)(x, t + 1) = f*_i(x, t) - 2 w_i (c_i . u_w) / c_s^2,
+ * u_w = wall_u at the solid node x + c_i (wall density 1; wall_u [d][N] or NULL = resting
+ * walls). Solid nodes do not collide; their exposed state is the rest equilibrium f_i = w_i.
+ * mask NULL removes all walls. AB layout only, not with the learned collision or recording
+ * (LB_ERR_UNSUPPORTED). With walls every step runs one node per thread. Copies both arrays. */
+LB_API lb_status lb_set_solid(lb_ctx* ctx, const void* mask, const void* wall_u, lb_mem mem);
+
 /* Advance n >= 0 steps of Eq. 1 (one fused kernel launch per step). */
 LB_API lb_status lb_step(lb_ctx* ctx, int64_t n);
 

@@ -13,7 +13,9 @@ Workloads (the paper runs analytic or seeded flows only; Sec. 2.2, 3.1, 3.3):
   * doubly periodic shear layer (Sec. 3.1 training flow);
   * random-phase decaying isotropic turbulence with E(k) ~ k^4 exp(-2 (k/k0)^2)
     (Sec. 3.1 transfer flow);
-  * a smooth seeded body-force field and near-equilibrium random populations.
+  * a smooth seeded body-force field and near-equilibrium random populations;
+  * solid masks for walls: a seeded random obstacle field and a duct with a cylinder or
+    sphere.
 """
 from __future__ import annotations
 
@@ -220,3 +222,27 @@ def random_mlp_params(seed: int, n_in: int = 6, n_hidden: int = 24, out_bias: fl
     w3 = xavier(1, n_hidden).ravel() * out_scale
     b3 = np.array([out_bias])
     return np.concatenate([w1.ravel(), b1, w2.ravel(), b2, w3, b3])
+
+
+def random_solid_mask(dims, seed: int, fraction: float = 0.2):
+    """Seeded random solid mask (uint8 [N], x fastest): each node solid with the given
+    probability (obstacle fields for tests)."""
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(dims))
+    return (rng.uniform(0.0, 1.0, size=n) < fraction).astype(np.uint8)
+
+
+def duct_with_obstacle(dims, radius: float, center=None):
+    """Solid mask (uint8 [N], x fastest) of a duct: walls on the planes y = 0, y = ny - 1 (and
+    z = 0, z = nz - 1 in 3D), periodic along x, plus a cylinder (2D) or sphere (3D) of the
+    given radius centred at `center` (default: a quarter of the length, mid-section)."""
+    nx, ny, nz = (int(v) for v in dims)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy, cz = center if center is not None else (nx / 4.0, (ny - 1) / 2.0, (nz - 1) / 2.0)
+    m = (y == 0) | (y == ny - 1)
+    if nz > 1:
+        m |= (z == 0) | (z == nz - 1)
+        m |= (x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2 <= radius ** 2
+    else:
+        m |= (x - cx) ** 2 + (y - cy) ** 2 <= radius ** 2
+    return m.reshape(-1).astype(np.uint8)

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "lb_set_force": (_INT, [_P, _P, _INT]),
     "lb_set_mlp": (_INT, [_P, _P, _I64, _INT]),
     "lb_set_relaxation": (_INT, [_P, _P, _INT]),
+    "lb_set_solid": (_INT, [_P, _P, _P, _INT]),
     "lb_step": (_INT, [_P, _I64]),
     "lb_moments": (_INT, [_P, _P, _P, _INT]),
     "lb_reduce": (_INT, [_P, ctypes.POINTER(_D)]),

@@ -70,6 +70,8 @@ struct lb_ctx {
     void* state = nullptr;             // buffer holding the current state
     int aa_parity = 0;                 // AA: 0 natural (even), 1 odd
     void* F = nullptr;                 // force [D][plane], arithmetic type
+    void* links = nullptr;             // bounce-back links [plane] (uint32), see lb::Geom
+    void* wall_u = nullptr;            // wall velocity [D][plane], arithmetic type
     std::vector<double> net;           // learned network (805 values), passed to kernels by value
     void* tc_table = nullptr;          // learned_tc: packed BF16 weight fragments on the device
     unsigned* status = nullptr;
@@ -385,7 +387,7 @@ void lb_destroy(lb_ctx* c)
     if (c->cycle) cudaGraphExecDestroy(c->cycle);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
-                    c->gF, c->gtheta};
+                    c->gF, c->gtheta, c->links, c->wall_u};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->ckpt)
@@ -481,6 +483,95 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
     c->net.swap(v);
     drop_cycle(c);  // the network is a by-value kernel argument of the captured steps
     return LB_OK;
+}
+
+lb_status lb_set_solid(lb_ctx* c, const void* mask, const void* wall_u, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
+    if (!mask && wall_u) return fail(LB_ERR_ARG, "a wall velocity needs a mask");
+    if (mask) {
+        if (c->opt.layout != LB_LAYOUT_AB) return fail(LB_ERR_UNSUPPORTED, "walls need the AB layout");
+        if (c->coll == LB_LEARNED_MRT) return fail(LB_ERR_UNSUPPORTED, "the learned collision has no walls");
+        if (c->opt.record_every > 0) return fail(LB_ERR_UNSUPPORTED, "no adjoint with walls");
+    }
+    DeviceGuard guard(c->device);
+    drop_cycle(c);  // the link table is a by-value kernel argument of the captured steps
+    // With walls the buffer holds reflected values in the slots of solid nodes, so a node
+    // that turns fluid would pull stale values. Replacing walls therefore keeps the exposed
+    // state (solid nodes at rest) and writes it back under the new geometry.
+    void* keep = nullptr;
+    if (c->links) {
+        cudaError_t e = cudaMallocAsync(&keep, (size_t)(c->Q * c->N * 8), c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ERR_OOM, "keeping the state across the wall change: %s", cudaGetErrorString(e));
+        }
+        lb::OpArgs a = base_args(c, lb::OP_GET);
+        a.out0 = keep;
+        a.io_f64 = 1;
+        if ((s = launch(c, a, "keep state")) != LB_OK) return s;
+    }
+    auto restore = [&]() -> lb_status {
+        if (!keep) return LB_OK;
+        lb::OpArgs a = base_args(c, lb::OP_SET);
+        a.dst = c->state;
+        a.in0 = keep;
+        a.io_f64 = 1;
+        lb_status r = launch(c, a, "restore state");
+        cudaFreeAsync(keep, c->stream);
+        keep = nullptr;
+        return r;
+    };
+    if (!mask) {
+        c->g.links = nullptr;
+        c->g.wall_u = nullptr;
+        if ((s = restore()) != LB_OK) return s;
+        cudaStreamSynchronize(c->stream);
+        if (c->links) cudaFree(c->links);
+        if (c->wall_u) cudaFree(c->wall_u);
+        c->links = c->wall_u = nullptr;
+        return LB_OK;
+    }
+    if (!c->links && (s = alloc(c, &c->links, c->plane * 4, "bounce-back links")) != LB_OK) return s;
+    // the mask: N bytes, on the host or the device as mem says
+    const void* dmask = mask;
+    void* tmp = nullptr;
+    if (mem_host(m)) {
+        cudaError_t e = cudaMallocAsync(&tmp, (size_t)c->N, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ERR_OOM, "staging the mask: %s", cudaGetErrorString(e));
+        }
+        LB_CUDA(c, cudaMemcpyAsync(tmp, mask, (size_t)c->N, cudaMemcpyHostToDevice, c->stream), "mask copy");
+        dmask = tmp;
+    }
+    lb::OpArgs a = base_args(c, lb::OP_LINKS);
+    a.mode = lb::AB;
+    a.in0 = dmask;
+    a.out0 = c->links;
+    s = launch(c, a, "bounce-back links");
+    if (tmp) cudaFreeAsync(tmp, c->stream);
+    if (s != LB_OK) return s;
+    if (wall_u) {
+        const int64_t bytes = (int64_t)c->D * c->plane * real_bytes(c->opt.storage);
+        if (!c->wall_u && (s = alloc(c, &c->wall_u, bytes, "wall velocity")) != LB_OK) return s;
+        LB_CUDA(c, cudaMemsetAsync(c->wall_u, 0, (size_t)bytes, c->stream), "wall velocity clear");
+        Staged sw;
+        if ((s = stage_in(c, sw, wall_u, c->N * c->D, m, "wall velocity")) != LB_OK) return s;
+        LB_CUDA(c, lb::convert_copy(sw.dev, mem_f64(m), c->wall_u, c->opt.storage == LB_F64, c->N, c->N, c->plane,
+                                    c->D, 0, c->stream),
+                "wall velocity copy");
+        c->launches += 1;
+    } else if (c->wall_u) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->wall_u);
+        c->wall_u = nullptr;
+    }
+    c->g.links = (const unsigned*)c->links;
+    c->g.wall_u = c->wall_u;
+    return restore();
 }
 
 lb_status lb_set_relaxation(lb_ctx* c, const double* params, int n)
@@ -817,6 +908,7 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     if (n > 0 && !c->recording) return fail(LB_ERR_STATE, "no recorded run");
     if (gth && c->coll != LB_LEARNED_MRT) return fail(LB_ERR_ARG, "grad_theta needs the learned collision");
     if (c->coll > LB_NONE) return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
+    if (c->links) return fail(LB_ERR_UNSUPPORTED, "no adjoint with walls");
     DeviceGuard guard(c->device);
     const int f64 = c->opt.storage == LB_F64;
     const int64_t rb = real_pop_bytes(c);

@@ -234,7 +234,16 @@ LB_DEV void store_pop2(T* p, int i, typename Store<T>::Real a, typename Store<T>
 struct Geom {
     int nx, ny, nz;
     int64_t plane;  // element stride between population planes (>= N, padded)
+    // solid nodes (halfway bounce-back): links[n] bit i (1 <= i < Q) set when x - c_i is
+    // solid, bit 31 when n itself is; nullptr = no walls. wall_u: [D][plane] velocity of
+    // each solid node in the arithmetic type, or nullptr (resting walls).
+    const unsigned* links = nullptr;
+    const void* wall_u = nullptr;
 };
+constexpr unsigned kSolidBit = 1u << 31;
+
+// the exposed state of a solid node is the rest equilibrium f_i = w_i
+LB_DEV bool solid_node(const Geom& g, int n) { return g.links && (g.links[n] & kSolidBit); }
 
 // Node coordinates and the wrapped +/-1 neighbours along each axis, plus the byte
 // offsets of the populations around the node for an element size S: per thread the
@@ -299,6 +308,12 @@ enum Mode { AB = 0, AA_EVEN = 1, AA_ODD = 2 };
 template <class St, int MODE, bool RAW = false, class T>
 LB_DEV void load_node(const T* buf, const Geom& g, const Nbr& nb, int n, typename Store<T>::Real* f)
 {
+    using R = typename Store<T>::Real;
+    if (solid_node(g, n)) {
+#pragma unroll
+        for (int i = 0; i < St::Q; ++i) f[i] = (RAW && !Store<T>::shifted) ? R(St::w(i)) : R(0);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_ODD) ? opp(i) : i;
@@ -326,6 +341,11 @@ LB_DEV void store_node(T* buf, const Geom& g, const Nbr& nb, int n, const typena
 template <class St, int MODE, class T>
 LB_DEV void load_node_f64(const T* buf, const Geom& g, const Nbr& nb, int n, double* f)
 {
+    if (solid_node(g, n)) {
+#pragma unroll
+        for (int i = 0; i < St::Q; ++i) f[i] = St::w(i);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_ODD) ? opp(i) : i;

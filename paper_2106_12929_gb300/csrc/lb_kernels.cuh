@@ -59,6 +59,10 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     using R = typename Store<T>::Real;
     NodeIdx id = node_index(g);
     if (!id.valid) return;
+    // halfway bounce-back (AB only): a solid node is skipped; its slots are written by
+    // the fluid nodes whose populations reflect off it
+    const unsigned lk = g.links ? g.links[id.n] : 0u;
+    if (lk & kSolidBit) return;
     Nbr nb = make_nbr<sizeof(T)>(g, id.x, id.y, id.z);
     R f[St::Q];
     constexpr bool RAW = COLL == NONE;  // streaming only: move the stored values untouched
@@ -67,7 +71,43 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
     bool ok = collide<St, COLL, FORCE>(f, Fl, rx);
     store_node<St, MODE, RAW>(dst, g, nb, id.n, f);
+    if (MODE == AB && lk) {
+        // x - c_i solid: next step pulls f_i(x) from slot i of that node, which receives
+        // f*_opp(i)(x) + 2 w_i (c_i . u_wall) / c_s^2 (moving-wall term; wall density 1)
+        const R* Wu = (const R*)g.wall_u;
+#pragma unroll
+        for (int i = 1; i < St::Q; ++i) {
+            if (!((lk >> i) & 1u)) continue;
+            const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
+            R v = f[opp(i)];
+            if (Wu) {
+                const int m = nb.node(g, -cx, -cy, -cz);
+                R cu = R(0);
+                if (cx) cu += cx > 0 ? Wu[m] : -Wu[m];
+                if (cy) cu += cy > 0 ? Wu[g.plane + m] : -Wu[g.plane + m];
+                if (St::D == 3 && cz) cu += cz > 0 ? Wu[2 * g.plane + m] : -Wu[2 * g.plane + m];
+                v += R(6.0 * St::w(i)) * cu;
+            }
+            T* p = at(dst, nb, i, -cx, -cy, -cz);
+            if constexpr (RAW) store_raw<St>(p, i, v);
+            else store_pop<St>(p, i, v);
+        }
+    }
     if (!ok) atomicOr(status, 1u);
+}
+
+// links[n] of every node from a solid mask (uint8, nonzero = solid)
+template <class St>
+__global__ void k_build_links(const unsigned char* mask, Geom g, unsigned* links)
+{
+    NodeIdx id = node_index(g);
+    if (!id.valid) return;
+    Nbr nb = make_nbr<1>(g, id.x, id.y, id.z);
+    unsigned lk = mask[id.n] ? kSolidBit : 0u;
+#pragma unroll
+    for (int i = 1; i < St::Q; ++i)
+        if (mask[nb.node(g, -St::c(i, 0), -St::c(i, 1), -St::c(i, 2))]) lk |= 1u << i;
+    links[id.n] = lk;
 }
 
 // Two nodes per thread (x0 = 2 t and x0 + 1; nx even). An access whose x shift is 0
@@ -568,6 +608,7 @@ template <class St, class T, int COLL>
 inline int update_shape(const OpArgs& a)
 {
     if (COLL == NONE) return 1;  // streaming only: stored values move untouched, one per thread
+    if (a.g.links) return 1;     // walls: the bounce-back writes live in the one-node kernel
     int npt = a.npt;
     if (npt == 0) {
         // four per thread for half storage, except D3Q27 KBC, whose 27 entropic weights per
@@ -655,6 +696,10 @@ cudaError_t launch_state_op(const OpArgs& a)
     case OP_ADJ_SEED:
         k_adj_seed<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.in0, a.in1, a.out0,
                                                                 a.out1, a.io_f64);
+        break;
+    case OP_LINKS:
+        if (MODE != AB) return cudaErrorInvalidValue;
+        k_build_links<St><<<gr, bl, 0, a.stream>>>((const unsigned char*)a.in0, a.g, (unsigned*)a.out0);
         break;
     case OP_LOSS_ENERGY:
         k_loss_energy<St, T, MODE, FORCE><<<gr, bl, 0, a.stream>>>((const T*)a.src, F, a.g, a.in0, a.out0, a.out1,

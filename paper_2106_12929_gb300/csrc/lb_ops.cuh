@@ -19,6 +19,7 @@ enum Op {
     OP_ADJ_SEED = 6,        // out0 <- lambda from (in0 = dL/drho or null, in1 = dL/du); gF += direct part
     OP_ADJ_STEP = 7,        // lam_out <- J^T S^T lam_in at state src; gF += force part
     OP_LOSS_ENERGY = 8,     // per-node energy loss seed (in0 = e*), partials[block] = sum of squares
+    OP_LINKS = 9,           // out0 <- bounce-back links of every node from the solid mask in0 (uint8)
 };
 
 // storage codes match lb_storage

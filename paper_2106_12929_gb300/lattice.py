@@ -155,6 +155,29 @@ class Lattice:
         _lib.check(self._lib.lb_set_relaxation(self._h, v, len(params)), "lb_set_relaxation")
         return self
 
+    def set_solid(self, mask, wall_u=None):
+        """Solid nodes (mask[N] nonzero) with halfway bounce-back; wall_u[d][N] moves them
+        (float32/float64, like the other arrays); mask None removes all walls."""
+        if mask is None:
+            _lib.check(self._lib.lb_set_solid(self._h, None, None, _lib.MEM["host_f64"]), "lb_set_solid")
+            return self
+        if isinstance(mask, torch.Tensor):
+            mt = (mask != 0).to(torch.uint8).contiguous()
+        else:
+            mt = torch.from_numpy(np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0).astype(np.uint8))
+        if mt.numel() != self.N:
+            raise ValueError(f"mask needs {self.N} entries")
+        if wall_u is not None:
+            wu = _to_tensor(wall_u).to(mt.device)
+            code = _mem_code(wu)
+        else:
+            wu = None
+            code = _lib.MEM["device_f64" if mt.is_cuda else "host_f64"]
+        _lib.check(self._lib.lb_set_solid(self._h, mt.data_ptr(), None if wu is None else wu.data_ptr(), code),
+                   "lb_set_solid")
+        self._keep = (mt, wu)
+        return self
+
     def set_populations(self, f):
         t = _to_tensor(f)
         _lib.check(self._lib.lb_set_populations(self._h, t.data_ptr(), _mem_code(t)), "lb_set_populations")
