@@ -246,3 +246,22 @@ def duct_with_obstacle(dims, radius: float, center=None):
     else:
         m |= (x - cx) ** 2 + (y - cy) ** 2 <= radius ** 2
     return m.reshape(-1).astype(np.uint8)
+
+
+def random_mlp3_params(seed: int, n_in: int = 6, n_hidden: int = 53, out_bias=0.0, out_scale: float = 0.0):
+    """Seeded Xavier-uniform parameters of an n_in -> n_hidden (tanh) -> 3 network.
+
+    Flat layout: W1[n_hidden][n_in], b1[n_hidden], W2[3][n_hidden], b2[3]. The output layer
+    is scaled by ``out_scale`` and its biases set to ``out_bias`` (a scalar or three values).
+    """
+    rng = np.random.default_rng(seed)
+
+    def xavier(fan_out, fan_in):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-lim, lim, size=(fan_out, fan_in))
+
+    w1 = xavier(n_hidden, n_in)
+    b1 = np.zeros(n_hidden)
+    w2 = xavier(3, n_hidden) * out_scale
+    b2 = np.broadcast_to(np.asarray(out_bias, dtype=np.float64), (3,)).copy()
+    return np.concatenate([w1.ravel(), b1, w2.ravel(), b2])

@@ -9,7 +9,8 @@ Conventions: a population array is ``f[Q][N]`` (FP64, natural layout, the
 pre-collision state of Eq. 1), a vector field ``u[d][N]``, nodes ordered x fastest.
 Collision kinds: ``"bgk"`` (Eq. 2), ``"regularized"``, ``"learned"`` (Eq. 5, D2Q9),
 ``"none"`` (streaming only), ``"trt"`` (two relaxation times), ``"kbc"`` (entropic,
-D2Q9 and D3Q27), ``"mrt"`` (Eq. 5 with fixed rates, D2Q9). ``params``: TRT
+D2Q9 and D3Q27), ``"mrt"`` (Eq. 5 with fixed rates, D2Q9), ``"learned3"`` (Eq. 5 with a
+one-hidden-layer network giving three higher-moment rates, D2Q9). ``params``: TRT
 ``[Lambda]`` (default 1/4), MRT ``[tau_6, tau_7, tau_8]`` (default 1, 1, 1). Stencils: ``"D2Q9"``, ``"D3Q19"``, ``"D3Q27"``.
 """
 from __future__ import annotations
@@ -28,10 +29,12 @@ _lock = threading.Lock()
 _lib = None
 
 STENCILS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6}
+COLLISIONS = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6, "learned3": 7}
 N_PARAMS = {"trt": 1, "mrt": 3}
 N_THETA = 793
 N_MLP = N_THETA + 12
+N_THETA3 = 533  # one hidden layer of 53 units, three outputs
+N_MLP3 = N_THETA3 + 12
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
 _i64_p = ctypes.POINTER(ctypes.c_int64)
@@ -121,6 +124,8 @@ def init_eq(name, dims, rho, u):
 def _cpar(collision, mlp, params):
     if collision == "learned":
         return None if mlp is None else _arr(mlp, (N_MLP,))
+    if collision == "learned3":
+        return None if mlp is None else _arr(mlp, (N_MLP3,))
     if params is None:
         return None
     return _arr(params, (N_PARAMS[collision],))
@@ -211,9 +216,11 @@ def adjoint(name, dims, tau, collision, f0, nsteps, lam_T, F=None, mlp=None, wan
     f0 = _arr(f0, (len(w), N))
     lam = _arr(lam_T, (len(w), N)).copy()
     F = None if F is None else _arr(F, (d, N))
-    mlp = None if mlp is None else _arr(mlp, (N_MLP,))
+    mlp = _cpar(collision, mlp, None)
     gF = np.zeros((d, N)) if F is not None else None
-    gth = np.zeros(N_THETA) if want_theta or collision == "learned" else None
+    gth = None
+    if want_theta or collision in ("learned", "learned3"):
+        gth = np.zeros(N_THETA3 if collision == "learned3" else N_THETA)
     _check(_load().ora_adjoint(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
                                COLLISIONS[collision], _p(F), _p(mlp), _p(f0), ctypes.c_int64(nsteps), _p(lam),
                                _p(gF), _p(gth)), "adjoint")

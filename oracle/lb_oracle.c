@@ -23,6 +23,8 @@
  *          (Eq. 5 with constant higher-moment relaxation times), and the entropic
  *          KBC model (Karlin, Boesch & Chikatamarla 2014). Their definitions are
  *          written out at collide_node.
+ *          A second network follows the shape Sec. 3.1 describes: one hidden layer
+ *          and three outputs, one relaxation time exp(z_n) + 1/2 per higher moment.
  *   Eq. 6  training loss from velocity, vorticity and energy mismatch.
  *   Sec. 3.2 gradients through the solver (here: the discrete adjoint, by hand).
  * Readings where the paper is silent (stencil order, Guo forcing, Hermite moment
@@ -48,11 +50,15 @@
 #define ORA_TRT 4
 #define ORA_KBC 5
 #define ORA_MRT 6
+#define ORA_LEARNED3 7
 
 #define NH 24                 /* hidden width of the per-node network */
 #define NIN 6                 /* number of network inputs (moment invariants) */
 #define NTHETA (NH * NIN + NH + NH * NH + NH + NH + 1) /* 793 */
 #define NMLP (NTHETA + 2 * NIN) /* parameters + input shift[6] + input scale[6] */
+#define NH3 53                  /* hidden width of the one-hidden-layer, three-output network */
+#define NTHETA3 (NH3 * NIN + NH3 + 3 * NH3 + 3) /* 533 */
+#define NMLP3 (NTHETA3 + 2 * NIN)
 
 typedef struct {
     int d, q;
@@ -297,6 +303,38 @@ static double mlp_forward(const double* p, const double* inv, mlp_cache_t* cc)
     return z;
 }
 
+/* The one-hidden-layer network of Sec. 3.1's description: the same six standardised
+ * inputs, NH3 tanh units, three outputs z[0..2]; tau_n = exp(z_n) + 1/2 for the higher
+ * moments in the order the paper lists them, N (4th order, our row 8) and J = (J0, J1)
+ * (3rd order, our rows 6 and 7). Layout: W1[NH3][6], b1[NH3], W2[3][NH3], b2[3],
+ * shift[6], scale[6]. */
+typedef struct {
+    double x[NIN];
+    double h[NH3];
+    double z[3];
+} mlp3_cache_t;
+
+static void mlp3_forward(const double* p, const double* inv, mlp3_cache_t* cc)
+{
+    const double *W1 = p, *b1 = W1 + NH3 * NIN, *W2 = b1 + NH3, *b2 = W2 + 3 * NH3, *shift = b2 + 3,
+                 *scale = shift + NIN;
+    int j, k, o;
+    for (k = 0; k < NIN; ++k) cc->x[k] = (inv[k] - shift[k]) * scale[k];
+    for (j = 0; j < NH3; ++j) {
+        double a = b1[j];
+        for (k = 0; k < NIN; ++k) a += W1[j * NIN + k] * cc->x[k];
+        cc->h[j] = tanh(a);
+    }
+    for (o = 0; o < 3; ++o) {
+        double a = b2[o];
+        for (j = 0; j < NH3; ++j) a += W2[o * NH3 + j] * cc->h[j];
+        cc->z[o] = a;
+    }
+}
+
+/* ghost row (6, 7, 8) of each output of the three-output network: N -> 8, J0 -> 6, J1 -> 7 */
+static const int out_row[3] = {8, 6, 7};
+
 /* invariants of the local state used as network inputs:
  *  I1 = rho - 1, I2 = |u|^2/cs2, I3 = tr Pi^neq / cs2, I4 = Pi^neq:Pi^neq / cs2^2,
  *  I5 = u.Pi^neq.u / cs2^2, I6 = sum_g (m_g - m_g^eq)^2 / |H_g|_w^2.
@@ -469,21 +507,26 @@ static void collide_node(const params_t* P, const double* f, const double* F, do
             for (a = 0; a < 9; ++a) acc += mt->Minv[i][a] * om[a];
             out[i] = f[i] - acc;
         }
-    } else { /* ORA_LEARNED, D2Q9, no force: Eq. 5 */
+    } else { /* ORA_LEARNED / ORA_LEARNED3, D2Q9, no force: Eq. 5 */
         const mrt_t* mt = P->mt;
         double m[9], meq[9], rate[9], I[NIN], om[9];
-        mlp_cache_t cc;
-        double z, taug;
         for (a = 0; a < 9; ++a) {
             m[a] = 0.0; meq[a] = 0.0;
             for (i = 0; i < 9; ++i) { m[a] += mt->M[a][i] * f[i]; meq[a] += mt->M[a][i] * feq[i]; }
         }
         invariants(mt, rho, u, m, meq, I);
-        z = mlp_forward(P->mlp, I, &cc);
-        taug = exp(z) + 0.5;
         for (a = 0; a < 3; ++a) rate[a] = 1.0;          /* conserved: tau = 1 */
         for (a = 3; a < 6; ++a) rate[a] = 1.0 / P->tau; /* stress: tau_n = nu/cs2 + 1/2 */
-        for (a = 6; a < 9; ++a) rate[a] = 1.0 / taug;   /* higher moments from the network */
+        if (P->coll == ORA_LEARNED) {
+            mlp_cache_t cc;
+            double taug = exp(mlp_forward(P->mlp, I, &cc)) + 0.5;
+            for (a = 6; a < 9; ++a) rate[a] = 1.0 / taug; /* higher moments from the network */
+        } else {
+            mlp3_cache_t c3;
+            int o;
+            mlp3_forward(P->mlp, I, &c3);
+            for (o = 0; o < 3; ++o) rate[out_row[o]] = 1.0 / (exp(c3.z[o]) + 0.5);
+        }
         for (a = 0; a < 9; ++a) om[a] = rate[a] * (m[a] - meq[a]);
         for (i = 0; i < 9; ++i) {
             double acc = 0.0;
@@ -504,8 +547,8 @@ static int make_params(params_t* P, const stencil_t* s, mrt_t* mt, double tau, i
     P->tau_minus = tau;
     P->tau_g[0] = P->tau_g[1] = P->tau_g[2] = 1.0;
     if (!(tau > 0.5)) return ORA_ERR_ARG;
-    if (coll < 0 || coll > 6) return ORA_ERR_ARG;
-    if (coll == ORA_LEARNED) {
+    if (coll < 0 || coll > 7) return ORA_ERR_ARG;
+    if (coll == ORA_LEARNED || coll == ORA_LEARNED3) {
         if (s->q != 9 || !cpar || F) return ORA_ERR_ARG;
         if (mrt_setup(s, mt)) return ORA_ERR_ARG;
         P->mlp = cpar;
@@ -823,27 +866,30 @@ static void adjoint_node(const params_t* P, const double* f, const double* F, co
                 if (F) gFl[a] += -0.5 * A[a]; /* a1 = -F/2 */
             }
         }
-    } else { /* learned Eq. 5, D2Q9, no force */
+    } else { /* learned Eq. 5 (one shared or three separate higher-moment rates), D2Q9, no force */
         const mrt_t* mt = P->mt;
         const double* p = P->mlp;
-        const double *W1 = p, *W2 = W1 + NH * NIN + NH, *W3 = W2 + NH * NH + NH, *scale = W3 + NH + 1 + NIN;
-        double *gW1 = gth, *gb1 = gW1 + NH * NIN, *gW2 = gb1 + NH, *gb2 = gW2 + NH * NH, *gW3 = gb2 + NH,
-               *gb3 = gW3 + NH;
         double feq[9], m[9], meq[9], I[NIN], nu[9], gm[9], gI[NIN], gx[NIN];
-        double ga2[NH], ga1[NH], gh1[NH];
-        double z, ez, taug, omg, kappa, gz, gP[3];
+        double rate_g[3], ez_g[3], kap[3], gP[3];
         mlp_cache_t cc;
-        int j, k;
+        mlp3_cache_t c3;
+        int j, k, o;
         equilibrium(s, rho, u, feq);
         for (a = 0; a < 9; ++a) {
             m[a] = 0.0; meq[a] = 0.0;
             for (i = 0; i < 9; ++i) { m[a] += mt->M[a][i] * f[i]; meq[a] += mt->M[a][i] * feq[i]; }
         }
         invariants(mt, rho, u, m, meq, I);
-        z = mlp_forward(p, I, &cc);
-        ez = exp(z);
-        taug = ez + 0.5;
-        omg = 1.0 / taug;
+        if (P->coll == ORA_LEARNED) {
+            double ez = exp(mlp_forward(p, I, &cc));
+            for (a = 0; a < 3; ++a) { ez_g[a] = ez; rate_g[a] = 1.0 / (ez + 0.5); }
+        } else {
+            mlp3_forward(p, I, &c3);
+            for (o = 0; o < 3; ++o) {
+                ez_g[out_row[o] - 6] = exp(c3.z[o]);
+                rate_g[out_row[o] - 6] = 1.0 / (exp(c3.z[o]) + 0.5);
+            }
+        }
         /* f*_i = f_i - sum_a Minv[i][a] omega_a (m_a - meq_a); nu_a = sum_i mu_i Minv[i][a] */
         for (a = 0; a < 9; ++a) {
             nu[a] = 0.0;
@@ -852,32 +898,59 @@ static void adjoint_node(const params_t* P, const double* f, const double* F, co
         }
         /* stress rows: -omega_s nu_a (m_a - meq_a); meq_3 = rho ux^2, meq_4 = rho ux uy, meq_5 = rho uy^2 */
         gP[0] = -omega * nu[3]; gP[1] = -omega * nu[4]; gP[2] = -omega * nu[5];
-        /* ghost rows (meq_g = 0 for the second-order equilibrium on D2Q9) */
-        kappa = 0.0;
-        for (a = 6; a < 9; ++a) { gm[a] += -omg * nu[a]; kappa += -nu[a] * (m[a] - meq[a]); }
+        /* ghost rows (meq_g = 0 for the second-order equilibrium on D2Q9); kap = d L / d omega_g */
+        for (a = 6; a < 9; ++a) { gm[a] += -rate_g[a - 6] * nu[a]; kap[a - 6] = -nu[a] * (m[a] - meq[a]); }
         /* omega_g = 1/(e^z + 1/2): d omega_g / dz = -e^z / (e^z + 1/2)^2 */
-        gz = kappa * (-ez / (taug * taug));
-        /* back through the network */
-        gb3[0] += gz;
-        for (k = 0; k < NH; ++k) {
-            gW3[k] += gz * cc.h2[k];
-            ga2[k] = gz * W3[k] * (1.0 - cc.h2[k] * cc.h2[k]);
-            gb2[k] += ga2[k];
-        }
-        for (j = 0; j < NH; ++j)
-            for (k = 0; k < NH; ++k) gW2[j * NH + k] += ga2[j] * cc.h1[k];
-        for (k = 0; k < NH; ++k) {
-            gh1[k] = 0.0;
-            for (j = 0; j < NH; ++j) gh1[k] += W2[j * NH + k] * ga2[j];
-            ga1[k] = gh1[k] * (1.0 - cc.h1[k] * cc.h1[k]);
-            gb1[k] += ga1[k];
-        }
-        for (j = 0; j < NH; ++j)
-            for (k = 0; k < NIN; ++k) gW1[j * NIN + k] += ga1[j] * cc.x[k];
-        for (k = 0; k < NIN; ++k) {
-            gx[k] = 0.0;
-            for (j = 0; j < NH; ++j) gx[k] += W1[j * NIN + k] * ga1[j];
-            gI[k] = gx[k] * scale[k];
+        if (P->coll == ORA_LEARNED) {
+            const double *W1 = p, *W2 = W1 + NH * NIN + NH, *W3 = W2 + NH * NH + NH, *scale = W3 + NH + 1 + NIN;
+            double *gW1 = gth, *gb1 = gW1 + NH * NIN, *gW2 = gb1 + NH, *gb2 = gW2 + NH * NH, *gW3 = gb2 + NH,
+                   *gb3 = gW3 + NH;
+            double ga2[NH], ga1[NH], gh1[NH], gz = 0.0;
+            for (a = 0; a < 3; ++a) gz += kap[a] * (-ez_g[a] * rate_g[a] * rate_g[a]);
+            /* back through the network */
+            gb3[0] += gz;
+            for (k = 0; k < NH; ++k) {
+                gW3[k] += gz * cc.h2[k];
+                ga2[k] = gz * W3[k] * (1.0 - cc.h2[k] * cc.h2[k]);
+                gb2[k] += ga2[k];
+            }
+            for (j = 0; j < NH; ++j)
+                for (k = 0; k < NH; ++k) gW2[j * NH + k] += ga2[j] * cc.h1[k];
+            for (k = 0; k < NH; ++k) {
+                gh1[k] = 0.0;
+                for (j = 0; j < NH; ++j) gh1[k] += W2[j * NH + k] * ga2[j];
+                ga1[k] = gh1[k] * (1.0 - cc.h1[k] * cc.h1[k]);
+                gb1[k] += ga1[k];
+            }
+            for (j = 0; j < NH; ++j)
+                for (k = 0; k < NIN; ++k) gW1[j * NIN + k] += ga1[j] * cc.x[k];
+            for (k = 0; k < NIN; ++k) {
+                gx[k] = 0.0;
+                for (j = 0; j < NH; ++j) gx[k] += W1[j * NIN + k] * ga1[j];
+                gI[k] = gx[k] * scale[k];
+            }
+        } else {
+            const double *W1 = p, *W2 = W1 + NH3 * NIN + NH3, *scale = W2 + 3 * NH3 + 3 + NIN;
+            double *gW1 = gth, *gb1 = gW1 + NH3 * NIN, *gW2 = gb1 + NH3, *gb2 = gW2 + 3 * NH3;
+            double gz[3], ga1[NH3];
+            for (o = 0; o < 3; ++o) {
+                const int g = out_row[o] - 6;
+                gz[o] = kap[g] * (-ez_g[g] * rate_g[g] * rate_g[g]);
+                gb2[o] += gz[o];
+                for (j = 0; j < NH3; ++j) gW2[o * NH3 + j] += gz[o] * c3.h[j];
+            }
+            for (j = 0; j < NH3; ++j) {
+                double acc = 0.0;
+                for (o = 0; o < 3; ++o) acc += W2[o * NH3 + j] * gz[o];
+                ga1[j] = acc * (1.0 - c3.h[j] * c3.h[j]);
+                gb1[j] += ga1[j];
+                for (k = 0; k < NIN; ++k) gW1[j * NIN + k] += ga1[j] * c3.x[k];
+            }
+            for (k = 0; k < NIN; ++k) {
+                gx[k] = 0.0;
+                for (j = 0; j < NH3; ++j) gx[k] += W1[j * NIN + k] * ga1[j];
+                gI[k] = gx[k] * scale[k];
+            }
         }
         /* back through the invariants */
         {
@@ -909,7 +982,7 @@ static void adjoint_node(const params_t* P, const double* f, const double* F, co
         }
     }
     /* Guo source (BGK and regularized): S_i(u, F) */
-    if (F && P->coll != ORA_LEARNED) {
+    if (F && P->coll != ORA_LEARNED && P->coll != ORA_LEARNED3) {
         for (i = 0; i < s->q; ++i) {
             double cu = s->c[i][0] * u[0] + s->c[i][1] * u[1] + s->c[i][2] * u[2];
             double cF = s->c[i][0] * F[0] + s->c[i][1] * F[1] + s->c[i][2] * F[2];
@@ -944,7 +1017,7 @@ int ora_adjoint(int st, const int64_t* dims, double tau, int coll, const double*
     int64_t N, QN, t, n;
     double *states, *mu;
     if (stencil_get(st, &s) || check_dims(&s, dims) || nsteps < 0) return ORA_ERR_ARG;
-    if (coll > ORA_NONE) return ORA_ERR_ARG; /* no adjoint of TRT, KBC or MRT */
+    if (coll == ORA_TRT || coll == ORA_KBC || coll == ORA_MRT) return ORA_ERR_ARG; /* no adjoint of these */
     if (make_params(&P, &s, &mt, tau, coll, mlp, F)) return ORA_ERR_ARG;
     N = dims[0] * dims[1] * dims[2];
     QN = (int64_t)s.q * N;

@@ -41,10 +41,11 @@ def _fd_check(name, dims, tau, coll, nsteps, F=None, mlp=None, seed=0, rtol=1e-6
         an = float((gF * dF).sum())
         assert abs(fd - an) <= rtol * max(abs(fd), 1e-12), (fd, an)
     if mlp is not None:
-        dth = lbinputs.random_field(793, seed + 5)
+        nth = len(gth)  # trained parameters (the input shift / scale follow them)
+        dth = lbinputs.random_field(nth, seed + 5)
         ht = 1e-5
-        mp = mlp.copy(); mp[:793] += ht * dth
-        mm = mlp.copy(); mm[:793] -= ht * dth
+        mp = mlp.copy(); mp[:nth] += ht * dth
+        mm = mlp.copy(); mm[:nth] -= ht * dth
         fd = (L(f0, F, mp) - L(f0, F, mm)) / (2 * ht)
         an = float((gth * dth).sum())
         assert abs(fd - an) <= 1e2 * rtol * max(abs(fd), 1e-12), (fd, an)
@@ -74,6 +75,15 @@ def _mlp(seed, tau):
 
 def test_learned_adjoint_matches_finite_differences():
     _fd_check("D2Q9", (5, 4, 1), 0.6, "learned", nsteps=3, mlp=_mlp(7, 0.6), seed=300, rtol=2e-6)
+
+
+def _mlp3(seed, tau):
+    th = lbinputs.random_mlp3_params(seed, out_bias=math.log(tau - 0.5), out_scale=0.5)
+    return np.concatenate([th, np.zeros(6), np.array([50.0, 100.0, 300.0, 1e5, 1e5, 1e5])])
+
+
+def test_learned3_adjoint_matches_finite_differences():
+    _fd_check("D2Q9", (5, 4, 1), 0.6, "learned3", nsteps=3, mlp=_mlp3(9, 0.6), seed=310, rtol=2e-6)
 
 
 @pytest.mark.parametrize("name,dims", [("D2Q9", (5, 4, 1)), ("D3Q27", (3, 2, 3))])
