@@ -58,7 +58,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            for name in ("ora_stencil", "ora_init_eq", "ora_step", "ora_step_walls", "ora_collide_node", "ora_moments",
+            for name in ("ora_stencil", "ora_init_eq", "ora_step", "ora_step_walls", "ora_step_ushift", "ora_collide_node", "ora_moments",
                          "ora_reduce", "ora_adjoint", "ora_seed_moments", "ora_loss_energy",
                          "ora_loss_eq6", "ora_vorticity", "ora_mlp_omega", "ora_invariants",
                          "ora_guo_source", "ora_num_threads"):
@@ -140,6 +140,17 @@ def step(name, dims, tau, collision, f, nsteps=1, F=None, mlp=None, params=None)
     mlp = _cpar(collision, mlp, params)
     _check(_load().ora_step(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
                             COLLISIONS[collision], _p(F), _p(mlp), _p(out), ctypes.c_int64(nsteps)), "step")
+    return out
+
+
+def step_ushift(name, dims, tau, f, du, nsteps=1):
+    """Return the state after ``nsteps`` BGK steps whose equilibrium is taken at u + du
+    (the velocity-shift forcing of Sec. 3.2), du[d][N] held fixed."""
+    d, _, w, _ = stencil(name)
+    N = n_nodes(dims)
+    out = _arr(f, (len(w), N)).copy()
+    _check(_load().ora_step_ushift(STENCILS[name], _dims(dims).ctypes.data_as(_i64_p), ctypes.c_double(tau),
+                                   _p(_arr(du, (d, N))), _p(out), ctypes.c_int64(nsteps)), "step_ushift")
     return out
 
 

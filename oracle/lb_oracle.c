@@ -635,6 +635,41 @@ int ora_step(int st, const int64_t* dims, double tau, int coll, const double* F,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Velocity-shift forcing of Sec. 3.2: a BGK step (Eq. 2) whose equilibrium   */
+/* is expanded around the locally shifted velocity u + du,                    */
+/*   f*_i = f_i - (f_i - f^eq_i(rho, u + du)) / tau,  u = sum_i c_i f_i / rho, */
+/* then streaming as in ora_step. du[d][N] is given (held fixed over the      */
+/* nsteps steps; Sec. 3.2 recomputes it from the state every step).           */
+/* ------------------------------------------------------------------------ */
+int ora_step_ushift(int st, const int64_t* dims, double tau, const double* du, double* f, int64_t nsteps)
+{
+    stencil_t s;
+    int64_t N, t, n;
+    double* g;
+    if (stencil_get(st, &s) || check_dims(&s, dims) || !du || !(tau > 0.5)) return ORA_ERR_ARG;
+    N = dims[0] * dims[1] * dims[2];
+    g = (double*)malloc(sizeof(double) * (size_t)s.q * (size_t)N);
+    if (!g) return ORA_ERR_OOM;
+    for (t = 0; t < nsteps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (n = 0; n < N; ++n) {
+            double fl[27], feq[27], rho, u[3], us[3], omega = 1.0 / tau;
+            int i, a;
+            gather(&s, f, N, n, fl);
+            node_moments(&s, fl, NULL, &rho, u);
+            for (a = 0; a < 3; ++a) us[a] = u[a] + (a < s.d ? du[(int64_t)a * N + n] : 0.0);
+            equilibrium(&s, rho, us, feq);
+            for (i = 0; i < s.q; ++i)
+                g[(int64_t)i * N + shifted_node(dims, n, s.c[i][0], s.c[i][1], s.c[i][2])] =
+                    fl[i] - omega * (fl[i] - feq[i]);
+        }
+        memcpy(f, g, sizeof(double) * (size_t)s.q * (size_t)N);
+    }
+    free(g);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. 1 with solid nodes: halfway bounce-back (the paper lists boundary      */
 /* conditions without formulas, Sec. 2.2; textbook form, Krueger et al. 2016, */
 /* Ladd's moving-wall term). A fluid node collides and pushes f*_i to x + c_i; */
