@@ -199,9 +199,11 @@ def run_only(args):
         print(json.dumps({"only": "adjoint", **adjoint_ratio(torch.cuda.current_stream(), n=args.grid or 1024,
                                                              steps=args.steps)}))
         return
-    if args.only in ("learned", "learned_tc"):
+    if args.only in ("learned", "learned_tc", "learned3"):
         print(json.dumps({"only": args.only, **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
-                                                                  steps=args.steps, tc=args.only == "learned_tc")}))
+                                                                  steps=args.steps, tc=args.only == "learned_tc",
+                                                                  net="learned3" if args.only == "learned3"
+                                                                  else "learned")}))
         return
     stencil, storage, layout, coll = ONLY[args.only]
     dims, tau, rho, u = workload(stencil, args.grid)
@@ -352,9 +354,9 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
         out[f"{key}_hbm_frac"] = round(g * BYTES_PER_LU[(st, sto)] / measured_peak_hbm()[0], 4)
         lat.close()
     out.update(adjoint_ratio(stream))
-    for tc in (False, True):
-        r = learned_throughput(stream, n=2048, steps=100, tc=tc)
-        key = "learned_tc" if tc else "learned_f32"
+    for key, tc, net in (("learned_f32", False, "learned"), ("learned_tc", True, "learned"),
+                         ("learned3_f32", False, "learned3")):
+        r = learned_throughput(stream, n=2048, steps=100, tc=tc, net=net)
         out[f"{key}_forward_glups"] = r["forward_glups"]
         out[f"{key}_backward_ms_per_step"] = r["backward_ms_per_step"]
     return out
@@ -398,21 +400,25 @@ def adjoint_ratio(stream, n=1024, steps=500, k=50):
     return res
 
 
-LEARNED_FLOP_PER_LU = 2 * (6 * 24 + 24 * 24 + 24) + 200  # network MACs x 2 + moments / invariants / collision
+# network MACs x 2 + moments / invariants / collision, per lattice update
+LEARNED_FLOP_PER_LU = {"learned": 2 * (6 * 24 + 24 * 24 + 24) + 200, "learned3": 2 * (6 * 53 + 53 * 3) + 200}
+N_THETA = {"learned": 793, "learned3": 533}
 
 
-def learned_throughput(stream, n=2048, steps=200, tc=False):
+def learned_throughput(stream, n=2048, steps=200, tc=False, net="learned"):
     """Learned collision (Eq. 5, D2Q9, FP32) on n^2 decaying turbulence: GLUPS of the forward
-    step and of the adjoint step with the parameter gradient."""
+    step and of the adjoint step with the parameter gradient. net: "learned" (6-24-24-1,
+    one shared higher-moment rate) or "learned3" (6-53-3, one rate per higher moment)."""
     import torch
     from paper_2106_12929_gb300 import Lattice
     dims = (n, n, 1)
     rho, u = lbinputs.random_spectrum_velocity(dims, 12.0, 0.05, 30000)
     tau = 0.5 + 3.0 * 0.05 * (n / (2.0 * math.pi)) / 30000.0
-    th = lbinputs.random_mlp_params(7, out_bias=math.log(tau - 0.5), out_scale=0.5)
-    net = np.concatenate([th, np.zeros(6), np.array([400.0, 100.0, 1e3, 1e6, 1e6, 1e6])])
-    lat = Lattice("D2Q9", dims, tau, "learned", storage="f32", record_every=10, learned_tc=tc)
-    lat.set_mlp(net)
+    gen = lbinputs.random_mlp3_params if net == "learned3" else lbinputs.random_mlp_params
+    th = gen(7, out_bias=math.log(tau - 0.5), out_scale=0.5)
+    values = np.concatenate([th, np.zeros(6), np.array([400.0, 100.0, 1e3, 1e6, 1e6, 1e6])])
+    lat = Lattice("D2Q9", dims, tau, net, storage="f32", record_every=10, learned_tc=tc)
+    lat.set_mlp(values)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     lat.step(5)
     t = time_steps(lat, steps, stream)
@@ -423,7 +429,7 @@ def learned_throughput(stream, n=2048, steps=200, tc=False):
     lat.step(k)
     lam = torch.zeros((9, n * n), dtype=torch.float32, device="cuda")
     lam[0] = 1.0
-    gth = torch.zeros(793, dtype=torch.float32, device="cuda")
+    gth = torch.zeros(N_THETA[net], dtype=torch.float32, device="cuda")
     lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)  # allocates the buffers
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -434,7 +440,7 @@ def learned_throughput(stream, n=2048, steps=200, tc=False):
     bwd = e0.elapsed_time(e1) / 1e3
     lat.close()
     return {"grid": [n, n], "forward_glups": round(fwd, 3),
-            "forward_tflops": round(fwd * LEARNED_FLOP_PER_LU / 1e3, 2),
+            "forward_tflops": round(fwd * LEARNED_FLOP_PER_LU[net] / 1e3, 2),
             "backward_ms_per_step": round(bwd / k * 1e3, 4),
             "forward_ms_per_step": round(n * n / fwd / 1e9 * 1e3, 4)}
 
@@ -492,7 +498,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned", "learned_tc"]), default=None,
+    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned", "learned_tc", "learned3"]), default=None,
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     ap.add_argument("--no-graphs", action="store_true", help="--only: one launch per kernel instead of graph replay")

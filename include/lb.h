@@ -68,7 +68,14 @@ typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_stencil;
  *                   1e-6 <Ds|Ds>), <X|Y> = sum X_i Y_i / f^eq_i. D2Q9 and D3Q27; no force.
  *   LB_MRT          Eq. 5 with fixed rates on D2Q9: stress moments relax with 1/tau, the
  *                   three higher Hermite moments with 1/tau_6, 1/tau_7, 1/tau_8 (1 unless
- *                   set by lb_set_relaxation). No force. */
+ *                   set by lb_set_relaxation). No force.
+ *   LB_LEARNED_MRT3 Eq. 5 on D2Q9 with the network shape Sec. 3.1 describes: one hidden
+ *                   layer of 53 tanh units and three outputs z_0, z_1, z_2, each giving one
+ *                   higher moment its own relaxation time exp(z) + 1/2, in the order the
+ *                   paper lists those moments: the fourth-order moment
+ *                   (cx^2 - 1/3)(cy^2 - 1/3), then the third-order (cx^2 - 1/3) cy and
+ *                   cx (cy^2 - 1/3). Same inputs as LB_LEARNED_MRT; 533 trained
+ *                   parameters. With adjoint and parameter gradient. No force. */
 typedef enum {
     LB_BGK = 0,
     LB_REGULARIZED = 1,
@@ -76,7 +83,8 @@ typedef enum {
     LB_NONE = 3,
     LB_TRT = 4,
     LB_KBC = 5,
-    LB_MRT = 6
+    LB_MRT = 6,
+    LB_LEARNED_MRT3 = 7
 } lb_collision;
 
 /* Storage of the populations in device memory. Arithmetic is FP64 for LB_F64 and
@@ -112,7 +120,7 @@ typedef struct {
                              and returns LB_ERR_UNSTABLE if a node went bad; 0 (default) = never */
     int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
                              lb_step_adjoint can run backwards (AB layout only); 0 = off */
-    int learned_tc;       /* learned collision, FP32/FP16/BF16 storage: 1 = evaluate the network's two
+    int learned_tc;       /* LB_LEARNED_MRT, FP32/FP16/BF16 storage: 1 = evaluate the network's two
                              hidden layers on the tensor cores with BF16 operands and FP32
                              accumulation (an inference option: lb_step_adjoint and training use
                              the FP32 network); 0 (default) = FP32 arithmetic throughout */
@@ -153,10 +161,14 @@ LB_API lb_status lb_init_from_moments(lb_ctx* ctx, const void* rho, const void* 
  * the collision (Guo, Zheng & Shi 2002; the paper only mentions forcing, Sec. 2.2). */
 LB_API lb_status lb_set_force(lb_ctx* ctx, const void* F, lb_mem mem);
 
-/* Network of the learned collision (Sec. 3.1), n_params = 805 values:
- * W1[24][6], b1[24], W2[24][24], b2[24], W3[24], b3 (793 trained parameters), then
- * the fixed input shift[6] and scale[6] (input k is (I_k - shift_k) scale_k).
- * Only valid for LB_LEARNED_MRT contexts. */
+/* Network of the learned collision (Sec. 3.1).
+ * LB_LEARNED_MRT, n_params = 805 values: W1[24][6], b1[24], W2[24][24], b2[24], W3[24],
+ * b3 (793 trained parameters), then the fixed input shift[6] and scale[6] (input k is
+ * (I_k - shift_k) scale_k).
+ * LB_LEARNED_MRT3, n_params = 545 values: W1[53][6], b1[53], W2[3][53], b2[3] (533 trained
+ * parameters; output 0 sets the fourth-order moment's time, outputs 1 and 2 the
+ * third-order ones, see lb_collision), then shift[6] and scale[6] as above.
+ * LB_ERR_STATE for other collisions, LB_ERR_ARG for another count or a non-finite value. */
 LB_API lb_status lb_set_mlp(lb_ctx* ctx, const void* params, int64_t n_params, lb_mem mem);
 
 /* Further relaxation parameters (host memory, copied): LB_TRT n = 1, params[0] =
@@ -206,6 +218,36 @@ LB_API lb_status lb_check(lb_ctx* ctx);
 /* Steps taken since the last initialisation. */
 LB_API int64_t lb_steps_taken(const lb_ctx* ctx);
 
+/* ----------------------------------------------------- spectral flow control ---- */
+/* Sec. 3.2 keeps a flow's energy spectrum near a target sigma_0 by a velocity-shift
+ * forcing: every step collides with BGK (Eq. 2) at the equilibrium f^eq(rho, u + du),
+ * du = -kappa grad_u R, where
+ *   R(u) = sum_s (ln max(sigma_s(u), c) - ln max(sigma0_s, c))^2
+ * and sigma_s(u) = sum over the Fourier modes k with round(|k|) = s of
+ * (|u_hat_x(k)|^2 + |u_hat_y(k)|^2) / 2, u_hat = (1/N) sum_x u(x) exp(-2 pi i k.x / n), for
+ * the shells s = 0 .. n/2 - 1 (the paper does not define the spectrum's normalisation or
+ * shells; this is its reading). The paper's constants are c = 2e-5 and kappa = 5e-5.
+ * grad_u R is the exact gradient of R (a spectral filter of u), computed each step on the
+ * GPU by FFTs of the grid lines. D2Q9 only, on a square grid of n = 2^k nodes per side,
+ * 4 <= n <= 4096, any storage and layout. */
+
+/* Turn the control on (sigma0[K] in host memory, K = n/2 shells, copied; cutoff c > 0,
+ * kappa >= 0) or off (sigma0 NULL). From the next lb_step every step computes du from the
+ * current state and collides at u + du (six kernel launches per step instead of one).
+ * Needs the BGK collision, no force, no walls and record_every = 0 (LB_ERR_UNSUPPORTED
+ * otherwise); LB_ERR_ARG for another K or non-finite values. */
+LB_API lb_status lb_set_spectral_control(lb_ctx* ctx, const double* sigma0, int64_t K, double cutoff,
+                                         double kappa);
+
+/* Spectrum sigma[n/2] of the current state (host memory, FP64; may be NULL) and, when the
+ * control is on, its cost R (*cost, host; may be NULL; LB_ERR_STATE without a target).
+ * Square 2^k D2Q9 grids only (LB_ERR_UNSUPPORTED). Synchronises the stream. */
+LB_API lb_status lb_spectrum(lb_ctx* ctx, double* sigma, double* cost);
+
+/* The velocity shift du[2][N] = -kappa grad_u R of the current state, as the next step
+ * would apply it (control on, else LB_ERR_STATE). */
+LB_API lb_status lb_spectral_shift(lb_ctx* ctx, void* du, lb_mem mem);
+
 /* ------------------------------------------------------------------ adjoint ---- */
 /* The discrete adjoint of f^{n+1} = S C(f^n; F), S the periodic shift along c_i
  * (Sec. 3.2 takes such gradients by automatic differentiation; here they are
@@ -233,8 +275,9 @@ LB_API lb_status lb_loss_eq6(lb_ctx* ctx, const void* u_ref, const void* w_ref, 
 /* Run the adjoint back over the n steps recorded since the last initialisation
  * (n must equal lb_steps_taken and the context must have record_every > 0).
  * lambda_T[Q][N] = dL/df^n of the current state. Outputs (each may be NULL):
- * lambda_0[Q][N] = dL/df^0; grad_F[d][N] += dL/dF; grad_theta[793] += dL/dtheta
- * (learned collision only). Recomputes each checkpoint segment forward once.
+ * lambda_0[Q][N] = dL/df^0; grad_F[d][N] += dL/dF; grad_theta += dL/dtheta over the
+ * trained parameters in lb_set_mlp's order (learned collisions only: 793 values for
+ * LB_LEARNED_MRT, 533 for LB_LEARNED_MRT3). Recomputes each checkpoint segment forward once.
  * The state is left at f^n. */
 LB_API lb_status lb_step_adjoint(lb_ctx* ctx, const void* lambda_T, int64_t n, void* lambda_0, void* grad_F,
                           void* grad_theta, lb_mem mem);

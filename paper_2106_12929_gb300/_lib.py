@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblb.so")
 
 # enums of include/lb.h
 STENCIL = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISION = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6}
+COLLISION = {"bgk": 0, "regularized": 1, "learned": 2, "none": 3, "trt": 4, "kbc": 5, "mrt": 6, "learned3": 7}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 LAYOUT = {"ab": 0, "aa": 1}
 MEM = {"host_f64": 0, "device_f64": 1, "host_f32": 2, "device_f32": 3}
@@ -25,6 +25,14 @@ Q_OF = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 D_OF = {"D2Q9": 2, "D3Q19": 3, "D3Q27": 3}
 N_NET = 805
 N_THETA = 793
+# the one-hidden-layer, three-output network (collision "learned3")
+N_NET3 = 545
+N_THETA3 = 533
+
+
+def n_theta(collision: str) -> int:
+    """Trained parameters of a learned collision's network (the length of its gradient)."""
+    return {"learned": N_THETA, "learned3": N_THETA3}[collision]
 
 
 class LBError(RuntimeError):
@@ -74,6 +82,9 @@ _SIGNATURES = {
     "lb_learned_inputs": (_INT, [_P, _P, _INT]),
     "lb_vorticity": (_INT, [_P, _P, _INT]),
     "lb_adam_update": (_INT, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I64, _P]),
+    "lb_set_spectral_control": (_INT, [_P, ctypes.POINTER(_D), _I64, _D, _D]),
+    "lb_spectrum": (_INT, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "lb_spectral_shift": (_INT, [_P, _P, _INT]),
     "lb_reduce_noalloc": (_INT, [_INT, ctypes.POINTER(_I64), _P, _P, _INT, ctypes.POINTER(_D), _P]),
     "lb_num_nodes": (_I64, [_P]),
     "lb_q": (_INT, [_P]),

@@ -6,16 +6,15 @@ from (rho0, u0), advances ``nsteps`` steps and returns the moments (rho, u) of t
 final state. Its backward pass seeds the adjoint from the moment cotangents
 (``lb_adjoint_seed_moments``) and runs ``lb_step_adjoint`` over the recorded run
 (checkpoints every ``record_every`` steps, recomputation in between), returning
-dL/dF for the body force and dL/dtheta for the learned collision's 793 network
-parameters. rho0 and u0 are treated as constants.
+dL/dF for the body force and dL/dtheta for a learned collision's network parameters
+(793 for "learned", 533 for "learned3"). rho0 and u0 are treated as constants.
 """
 from __future__ import annotations
 
 import torch
 
+from . import _lib
 from .lattice import Lattice
-
-N_THETA = 793
 
 
 class _LBRun(torch.autograd.Function):
@@ -46,7 +45,7 @@ class _LBRun(torch.autograd.Function):
         g_u = torch.zeros((lat.D, lat.N), dtype=rdt, device=dev) if g_u is None else g_u.to(device=dev, dtype=rdt)
         g_rho = None if g_rho is None else g_rho.to(device=dev, dtype=rdt).contiguous()
         gF = torch.zeros((lat.D, lat.N), dtype=rdt, device=dev) if ctx.has_F else None
-        gth = torch.zeros(N_THETA, dtype=rdt, device=dev) if ctx.has_theta else None
+        gth = torch.zeros(_lib.n_theta(lat.collision), dtype=rdt, device=dev) if ctx.has_theta else None
         lam = lat.adjoint_seed_moments(g_rho, g_u.contiguous(), grad_F=gF)
         lat.step_adjoint(lam, ctx.nsteps, grad_F=gF, grad_theta=gth, want_lambda0=False)
         return (None if gF is None else gF.to(ctx.F_dtype), None if gth is None else gth.to(ctx.theta_dtype),
@@ -57,8 +56,8 @@ def lb_run(lattice: Lattice, rho0, u0, nsteps: int, F: torch.Tensor | None = Non
            theta: torch.Tensor | None = None, net_extra: torch.Tensor | None = None):
     """Differentiable run: returns (rho, u) after ``nsteps`` steps from f^eq(rho0, u0).
 
-    F: body force [d, N] (CUDA tensor) or None. theta: the 793 trained network
-    parameters of a learned-collision lattice, with ``net_extra`` its fixed 12 input
+    F: body force [d, N] (CUDA tensor) or None. theta: the trained network parameters of a
+    learned-collision lattice (793 or 533), with ``net_extra`` its fixed 12 input
     shift/scale values. The lattice must have been created with record_every > 0.
     """
     if theta is not None and net_extra is None:

@@ -11,7 +11,7 @@
 
 namespace lb {
 
-enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3, TRT = 4, KBC = 5, MRT = 6 };
+enum Coll { BGK = 0, REG = 1, LEARNED = 2, NONE = 3, TRT = 4, KBC = 5, MRT = 6, LEARNED3 = 7 };
 
 // Relaxation rates of one collision. omega = 1/tau sets the shear viscosity for every
 // model; p holds the model's other constants: TRT p[0] = 1/tau_minus; KBC p[0] = 2 tau
@@ -26,7 +26,7 @@ struct Relax {
 template <class St>
 constexpr bool coll_supported(int coll)
 {
-    return coll == KBC ? (St::Q == 9 || St::Q == 27) : coll == MRT ? St::Q == 9 : coll != LEARNED;
+    return coll == KBC ? (St::Q == 9 || St::Q == 27) : coll == MRT ? St::Q == 9 : coll != LEARNED && coll != LEARNED3;
 }
 
 // 1/x rounded to nearest (FP32: the hardware reciprocal with IEEE rounding, not a division)

@@ -50,12 +50,18 @@ template <class R> LB_DEV R act_exp(R a);
 template <> LB_DEV float act_exp<float>(float a) { return expf(a); }
 template <> LB_DEV double act_exp<double>(double a) { return exp(a); }
 
-// Everything the forward pass of one node computes (kept for the adjoint).
+// The moments of one node that both networks read: density and velocity, equilibrium,
+// non-equilibrium stress Pi and higher moments g6, g7, g8.
 template <class R>
-struct LearnedNode {
+struct LearnedMoments {
     NodeMoments<D2Q9, R> m;
     R feq[9];
     R pxx, pxy, pyy, g6, g7, g8;
+};
+
+// Everything the forward pass of one node computes (kept for the adjoint).
+template <class R>
+struct LearnedNode : LearnedMoments<R> {
     R x[kNetIn];
     R h1[kNetHidden], h2[kNetHidden];
     R z, ez, omg;
@@ -63,7 +69,7 @@ struct LearnedNode {
 
 // Moments, equilibrium, stress and higher moments, and the six network inputs of one node.
 template <class R>
-LB_DEV void learned_inputs(const R* f, LearnedNode<R>& s, R* I)
+LB_DEV void learned_inputs(const R* f, LearnedMoments<R>& s, R* I)
 {
     R Fz[3] = {R(0), R(0), R(0)};
     s.m = node_moments<D2Q9, false>(f, Fz);
@@ -525,6 +531,100 @@ LB_DEV void block_theta_grad(AdjShared<R>& sh, int t, R* out)
     }
 }
 
+// Cotangents of the per-node quantities of the learned collision, built up by the adjoint:
+// density, velocity, non-equilibrium stress and higher moments; q_g are the adjoint's
+// projections sum_i mu_i w_i H_g(c_i) / |H_g|^2_w onto the higher rows.
+template <class R>
+struct LearnedCot {
+    R grho, gux, guy, gPxx, gPxy, gPyy, gg6, gg7, gg8;
+    R q6, q7, q8;
+};
+
+// The paths through the equilibrium and the stress rows of f*; the higher rows' terms
+// (which depend on the network) are added by the caller.
+template <class R>
+LB_DEV LearnedCot<R> learned_adj_head(const LearnedMoments<R>& s, const R* mu, R omega)
+{
+    const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
+    // sums of mu w over the basis
+    R smw = R(0), smwcx = R(0), smwcy = R(0), smwcucx = R(0), smwcucy = R(0), grho = R(0);
+    R sxx = R(0), syy = R(0), sxy = R(0), s6 = R(0), s7 = R(0), s8 = R(0);
+    const R base = R(1) - R(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R mw = mu[i] * R(D2Q9::w(i));
+        const int cx = c2(i, 0), cy = c2(i, 1);
+        const R cu = cdotu<D2Q9>(i, ux, uy, R(0));
+        grho += mw * (base + cu * (R(3) + R(4.5) * cu));
+        smw += mw;
+        smwcx += cx * mw;
+        smwcy += cy * mw;
+        smwcucx += cx * mw * cu;
+        smwcucy += cy * mw * cu;
+        if (cx) sxx += mw;
+        if (cy) syy += mw;
+        if (cx && cy) sxy += (cx == cy) ? mw : -mw;
+        s6 += R(h6(i)) * mw;
+        s7 += R(h7(i)) * mw;
+        s8 += R(h8(i)) * mw;
+    }
+    LearnedCot<R> c;
+    c.grho = grho;
+    // equilibrium path: d f^eq / d rho, d f^eq / d u
+    c.gux = rho * (R(3) * smwcx + R(9) * smwcucx - R(3) * ux * smw);
+    c.guy = rho * (R(3) * smwcy + R(9) * smwcucy - R(3) * uy * smw);
+    // stress path: cotangent of (Pxx, Pxy, Pyy) from 4.5 (1 - w_s) w_i Q_i : Pi
+    const R ks = R(4.5) * (R(1) - omega);
+    c.gPxx = ks * (sxx - smw * R(1.0 / 3.0));
+    c.gPyy = ks * (syy - smw * R(1.0 / 3.0));
+    c.gPxy = R(2) * ks * sxy;
+    c.q6 = s6 * R(1.0 / kN6);
+    c.q7 = s7 * R(1.0 / kN7);
+    c.q8 = s8 * R(1.0 / kN8);
+    return c;
+}
+
+// Back through the six network inputs (cotangent gI of the unstandardised invariants) and
+// the moments to lambda_i = d(mu . f*)/d f_i, written to lam_out[i][n].
+template <class R>
+LB_DEV void learned_adj_tail(const LearnedMoments<R>& s, LearnedCot<R> c, const R* gI, R* lam_out, int64_t plane,
+                             int n)
+{
+    const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
+    R grho = c.grho, gux = c.gux, guy = c.guy, gPxx = c.gPxx, gPyy = c.gPyy, gPxy = c.gPxy;
+    R gg6 = c.gg6, gg7 = c.gg7, gg8 = c.gg8;
+    grho += gI[0];
+    gux += R(6) * ux * gI[1];
+    guy += R(6) * uy * gI[1];
+    gPxx += R(3) * gI[2] + R(18) * s.pxx * gI[3] + R(9) * ux * ux * gI[4];
+    gPyy += R(3) * gI[2] + R(18) * s.pyy * gI[3] + R(9) * uy * uy * gI[4];
+    gPxy += R(36) * s.pxy * gI[3] + R(18) * ux * uy * gI[4];
+    gux += R(18) * (ux * s.pxx + uy * s.pxy) * gI[4];
+    guy += R(18) * (ux * s.pxy + uy * s.pyy) * gI[4];
+    gg6 += R(2) * s.g6 * R(1.0 / kN6) * gI[5];
+    gg7 += R(2) * s.g7 * R(1.0 / kN7) * gI[5];
+    gg8 += R(2) * s.g8 * R(1.0 / kN8) * gI[5];
+    // Pi = sum c c f - rho u u - rho I/3
+    grho -= gPxx * (ux * ux + R(1.0 / 3.0)) + gPxy * ux * uy + gPyy * (uy * uy + R(1.0 / 3.0));
+    gux -= rho * (R(2) * ux * gPxx + uy * gPxy);
+    guy -= rho * (ux * gPxy + R(2) * uy * gPyy);
+    const R inv = R(1) / rho;
+    const R gdotu = gux * ux + guy * uy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = c2(i, 0), cy = c2(i, 1);
+        // direct paths: Pi (c c) and the higher moments (H_g); the equilibrium
+        // term of f* has no direct dependence on f
+        R v = R(0);
+        if (cx) v += gPxx;
+        if (cy) v += gPyy;
+        if (cx && cy) v += (cx == cy) ? gPxy : -gPxy;
+        v += R(h6(i)) * gg6 + R(h7(i)) * gg7 + R(h8(i)) * gg8;
+        v += grho + (cdotu<D2Q9>(i, gux, guy, R(0)) - gdotu) * inv;
+        lam_out[(int64_t)i * plane + n] = v;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state, const typename Store<T>::Real* lam_in,
                                                                typename Store<T>::Real* lam_out, Geom g,
@@ -554,42 +654,13 @@ __global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state
 #pragma unroll
         for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nb.node(g, c2(i, 0), c2(i, 1), 0)];
         learned_forward(f, net, s);
-        const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
-        // sums of mu w over the basis
-        R smw = R(0), smwcx = R(0), smwcy = R(0), smwcucx = R(0), smwcucy = R(0), grho = R(0);
-        R sxx = R(0), syy = R(0), sxy = R(0), s6 = R(0), s7 = R(0), s8 = R(0);
-        const R base = R(1) - R(1.5) * (ux * ux + uy * uy);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const R mw = mu[i] * R(D2Q9::w(i));
-            const int cx = c2(i, 0), cy = c2(i, 1);
-            const R cu = cdotu<D2Q9>(i, ux, uy, R(0));
-            grho += mw * (base + cu * (R(3) + R(4.5) * cu));
-            smw += mw;
-            smwcx += cx * mw;
-            smwcy += cy * mw;
-            smwcucx += cx * mw * cu;
-            smwcucy += cy * mw * cu;
-            if (cx) sxx += mw;
-            if (cy) syy += mw;
-            if (cx && cy) sxy += (cx == cy) ? mw : -mw;
-            s6 += R(h6(i)) * mw;
-            s7 += R(h7(i)) * mw;
-            s8 += R(h8(i)) * mw;
-        }
-        // equilibrium path: d f^eq / d rho, d f^eq / d u
-        R gux = rho * (R(3) * smwcx + R(9) * smwcucx - R(3) * ux * smw);
-        R guy = rho * (R(3) * smwcy + R(9) * smwcucy - R(3) * uy * smw);
-        // stress path: cotangent of (Pxx, Pxy, Pyy) from 4.5 (1 - w_s) w_i Q_i : Pi
-        const R ks = R(4.5) * (R(1) - omega);
-        R gPxx = ks * (sxx - smw * R(1.0 / 3.0));
-        R gPyy = ks * (syy - smw * R(1.0 / 3.0));
-        R gPxy = R(2) * ks * sxy;
+        LearnedCot<R> c = learned_adj_head(s, mu, omega);
         // higher moments: cotangent of g_g and of w_g
         const R kg = R(1) - s.omg;
-        const R q6 = s6 * R(1.0 / kN6), q7 = s7 * R(1.0 / kN7), q8 = s8 * R(1.0 / kN8);
-        R gg6 = kg * q6, gg7 = kg * q7, gg8 = kg * q8;
-        const R gomg = -(q6 * s.g6 + q7 * s.g7 + q8 * s.g8);
+        c.gg6 = kg * c.q6;
+        c.gg7 = kg * c.q7;
+        c.gg8 = kg * c.q8;
+        const R gomg = -(c.q6 * s.g6 + c.q7 * s.g7 + c.q8 * s.g8);
         // w_g = 1/(e^z + 1/2): d w_g / dz = -e^z w_g^2
         gz = gomg * (-s.ez * s.omg * s.omg);
         // back through the network
@@ -610,37 +681,7 @@ __global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state
             for (int j = 0; j < kNetHidden; ++j) a += W1[j * kNetIn + m] * ga1[j];
             gI[m] = a * scale[m];
         }
-        // back through the invariants
-        grho += gI[0];
-        gux += R(6) * ux * gI[1];
-        guy += R(6) * uy * gI[1];
-        gPxx += R(3) * gI[2] + R(18) * s.pxx * gI[3] + R(9) * ux * ux * gI[4];
-        gPyy += R(3) * gI[2] + R(18) * s.pyy * gI[3] + R(9) * uy * uy * gI[4];
-        gPxy += R(36) * s.pxy * gI[3] + R(18) * ux * uy * gI[4];
-        gux += R(18) * (ux * s.pxx + uy * s.pxy) * gI[4];
-        guy += R(18) * (ux * s.pxy + uy * s.pyy) * gI[4];
-        gg6 += R(2) * s.g6 * R(1.0 / kN6) * gI[5];
-        gg7 += R(2) * s.g7 * R(1.0 / kN7) * gI[5];
-        gg8 += R(2) * s.g8 * R(1.0 / kN8) * gI[5];
-        // Pi = sum c c f - rho u u - rho I/3
-        grho -= gPxx * (ux * ux + R(1.0 / 3.0)) + gPxy * ux * uy + gPyy * (uy * uy + R(1.0 / 3.0));
-        gux -= rho * (R(2) * ux * gPxx + uy * gPxy);
-        guy -= rho * (ux * gPxy + R(2) * uy * gPyy);
-        const R inv = R(1) / rho;
-        const R gdotu = gux * ux + guy * uy;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int cx = c2(i, 0), cy = c2(i, 1);
-            // direct paths: Pi (c c) and the higher moments (H_g); the equilibrium
-            // term of f* has no direct dependence on f
-            R v = R(0);
-            if (cx) v += gPxx;
-            if (cy) v += gPyy;
-            if (cx && cy) v += (cx == cy) ? gPxy : -gPxy;
-            v += R(h6(i)) * gg6 + R(h7(i)) * gg7 + R(h8(i)) * gg8;
-            v += grho + (cdotu<D2Q9>(i, gux, guy, R(0)) - gdotu) * inv;
-            lam_out[(int64_t)i * g.plane + n] = v;
-        }
+        learned_adj_tail(s, c, gI, lam_out, g.plane, n);
     } else {
 #pragma unroll
         for (int k = 0; k < kNetHidden; ++k) {
@@ -666,6 +707,254 @@ __global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state
     __syncthreads();
     // partials accumulate over the adjoint steps of one run
     block_theta_grad(sh, t, gth_partials + (int64_t)(blockIdx.x + (int64_t)gridDim.x * blockIdx.y) * kNetTheta);
+}
+
+// ---------------------------------------------------------------- one hidden layer, three outputs
+// The network shape Sec. 3.1 describes: the same six standardised inputs, kNet3Hidden tanh
+// units and three outputs z_o, each setting one higher moment's relaxation time
+// exp(z_o) + 1/2, in the order the paper lists those moments: N (fourth order, Hermite row
+// (cx^2 - 1/3)(cy^2 - 1/3)), then J0 and J1 (third order, rows (cx^2 - 1/3) cy and
+// cx (cy^2 - 1/3)). Values: W1[53][6], b1[53], W2[3][53], b2[3], shift[6], scale[6].
+template <class R>
+struct Net3 {
+    R v[kNet3Values];
+};
+
+// higher row set by output o (0: row (cx^2 - 1/3) cy, 1: cx (cy^2 - 1/3), 2: the fourth-order row)
+LB_HD constexpr int net3_row(int o) { return o == 0 ? 2 : o - 1; }
+
+template <class R>
+struct Learned3Node : LearnedMoments<R> {
+    R x[kNetIn];
+    R h[kNet3Hidden];
+    R ez[3], omg[3];  // per higher row, in row order
+};
+
+template <class R>
+LB_DEV void learned3_forward(const R* f, const Net3<R>& net, Learned3Node<R>& s)
+{
+    const R* W1 = net.v;
+    const R* b1 = W1 + kNet3Hidden * kNetIn;
+    const R* W2 = b1 + kNet3Hidden;
+    const R* b2 = W2 + 3 * kNet3Hidden;
+    const R* shift = b2 + 3;
+    const R* scale = shift + kNetIn;
+    R I[kNetIn];
+    learned_inputs(f, s, I);
+#pragma unroll
+    for (int k = 0; k < kNetIn; ++k) s.x[k] = (I[k] - shift[k]) * scale[k];
+    R z[3] = {b2[0], b2[1], b2[2]};
+#pragma unroll
+    for (int j = 0; j < kNet3Hidden; ++j) {
+        R a = b1[j];
+#pragma unroll
+        for (int k = 0; k < kNetIn; ++k) a += W1[j * kNetIn + k] * s.x[k];
+        const R h = act_tanh(a);
+        s.h[j] = h;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) z[o] += W2[o * kNet3Hidden + j] * h;
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const int r = net3_row(o);
+        s.ez[r] = act_exp(z[o]);
+        s.omg[r] = R(1) / (s.ez[r] + R(0.5));
+    }
+}
+
+template <class R>
+LB_DEV void learned3_post(const Learned3Node<R>& s, R omega, R* f)
+{
+    const R ks = R(4.5) * (R(1) - omega);
+    const R tr3 = (s.pxx + s.pyy) * R(1.0 / 3.0);
+    const R q6 = (R(1) - s.omg[0]) * s.g6 * R(1.0 / kN6);
+    const R q7 = (R(1) - s.omg[1]) * s.g7 * R(1.0 / kN7);
+    const R q8 = (R(1) - s.omg[2]) * s.g8 * R(1.0 / kN8);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = c2(i, 0), cy = c2(i, 1);
+        R qp = -tr3;
+        if (cx) qp += s.pxx;
+        if (cy) qp += s.pyy;
+        if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
+        const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
+        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + ghost);
+    }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_learned3_update(const T* src, T* dst, Geom g, typename Store<T>::Real omega,
+                                                         unsigned* status, const Net3<typename Store<T>::Real> net)
+{
+    using R = typename Store<T>::Real;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y;
+    Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
+    const int n = x + g.nx * y;
+    R f[9];
+    load_node<D2Q9, MODE>(src, g, nb, n, f);
+    Learned3Node<R> s;
+    learned3_forward(f, net, s);
+    learned3_post(s, omega, f);
+    store_node<D2Q9, MODE>(dst, g, nb, n, f);
+    if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
+}
+
+// Block reduction of the parameter gradient of the three-output network. The hidden units
+// (padded to kH3Pad) form kT3Tiles register tiles of four; each tile's nodes are split into
+// kT3Parts interleaved subsets (so that the threads of a warp read distinct banks); one thread
+// per (tile, subset) accumulates W1 4x6, b1 4, W2 3x4 and b2 3 in registers, and the subsets
+// are added in a fixed order, so the result does not depend on timing.
+constexpr int kH3Pad = 56;
+constexpr int kT3Tiles = kH3Pad / 4;
+constexpr int kT3Parts = 8;
+constexpr int kT3Vals = 24 + 4 + 12 + 3;
+static_assert(kT3Tiles * kT3Parts <= kAdjBlock, "one thread per tile and subset");
+
+template <class R>
+struct Adj3Shared {
+    R ga1[kAdjBlock][kH3Pad];
+    R h[kAdjBlock][kH3Pad];
+    R x[kAdjBlock][8];
+    R gz[kAdjBlock][4];
+    R part[kT3Parts][kT3Tiles][kT3Vals + 1];
+};
+
+template <class R>
+LB_DEV void block_theta3_grad(Adj3Shared<R>& sh, int t, R* out)
+{
+    constexpr int oW1 = 0, ob1 = kNet3Hidden * kNetIn, oW2 = ob1 + kNet3Hidden, ob2 = oW2 + 3 * kNet3Hidden;
+    if (t < kT3Tiles * kT3Parts) {
+        const int tile = t % kT3Tiles, part = t / kT3Tiles, j0 = 4 * tile;
+        R acc[kT3Vals];
+#pragma unroll
+        for (int k = 0; k < kT3Vals; ++k) acc[k] = R(0);
+        for (int q = part; q < kAdjBlock; q += kT3Parts) {
+            R ga[4], hv[4], xv[8], gz[4];
+            ld4(&sh.ga1[q][j0], ga);
+            ld4(&sh.h[q][j0], hv);
+            ld4(&sh.x[q][0], xv);
+            ld4(&sh.x[q][4], xv + 4);
+            ld4(&sh.gz[q][0], gz);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                acc[24 + a] += ga[a];
+#pragma unroll
+                for (int m = 0; m < kNetIn; ++m) acc[a * kNetIn + m] += ga[a] * xv[m];
+            }
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                acc[40 + o] += gz[o];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[28 + 4 * o + b] += gz[o] * hv[b];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kT3Vals; ++k) sh.part[part][tile][k] = acc[k];
+    }
+    __syncthreads();
+    for (int v = t; v < kT3Tiles * kT3Vals; v += kAdjBlock) {
+        const int tile = v / kT3Vals, k = v % kT3Vals, j0 = 4 * tile;
+        R acc = R(0);
+#pragma unroll
+        for (int p = 0; p < kT3Parts; ++p) acc += sh.part[p][tile][k];
+        int idx = -1;
+        if (k < 24) {
+            const int j = j0 + k / kNetIn;
+            if (j < kNet3Hidden) idx = oW1 + j * kNetIn + k % kNetIn;
+        } else if (k < 28) {
+            const int j = j0 + (k - 24);
+            if (j < kNet3Hidden) idx = ob1 + j;
+        } else if (k < 40) {
+            const int o = (k - 28) / 4, j = j0 + (k - 28) % 4;
+            if (j < kNet3Hidden) idx = oW2 + o * kNet3Hidden + j;
+        } else if (tile == 0) {
+            idx = ob2 + (k - 40);
+        }
+        if (idx >= 0) out[idx] += acc;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kAdjBlock, 2) k_learned3_adjoint(const T* state, const typename Store<T>::Real* lam_in,
+                                                                typename Store<T>::Real* lam_out, Geom g,
+                                                                typename Store<T>::Real omega,
+                                                                typename Store<T>::Real* gth_partials,
+                                                                const Net3<typename Store<T>::Real> net)
+{
+    using R = typename Store<T>::Real;
+    extern __shared__ unsigned char smem_raw[];
+    Adj3Shared<R>& sh = *reinterpret_cast<Adj3Shared<R>*>(smem_raw);
+    const int t = threadIdx.x;
+    const int x = blockIdx.x * blockDim.x + t;
+    const int y = blockIdx.y;
+    if (x < g.nx) {
+        const R* W1 = net.v;
+        const R* W2 = W1 + kNet3Hidden * kNetIn + kNet3Hidden;
+        const R* scale = W2 + 3 * kNet3Hidden + 3 + kNetIn;
+        Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
+        const int n = x + g.nx * y;
+        R f[9], mu[9];
+        load_node<D2Q9, AB>(state, g, nb, n, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nb.node(g, c2(i, 0), c2(i, 1), 0)];
+        Learned3Node<R> s;
+        learned3_forward(f, net, s);
+        LearnedCot<R> c = learned_adj_head(s, mu, omega);
+        // higher moments: cotangents of g_g and, through w_g = 1/(e^z + 1/2)
+        // (d w_g / dz = -e^z w_g^2), of the network outputs
+        c.gg6 = (R(1) - s.omg[0]) * c.q6;
+        c.gg7 = (R(1) - s.omg[1]) * c.q7;
+        c.gg8 = (R(1) - s.omg[2]) * c.q8;
+        const R gomg[3] = {-(c.q6 * s.g6), -(c.q7 * s.g7), -(c.q8 * s.g8)};
+        R gz[3];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            const int r = net3_row(o);
+            gz[o] = gomg[r] * (-s.ez[r] * s.omg[r] * s.omg[r]);
+        }
+        // back through the network, staging the outer-product factors on the way
+        R gI[kNetIn];
+#pragma unroll
+        for (int m = 0; m < kNetIn; ++m) gI[m] = R(0);
+#pragma unroll
+        for (int j = 0; j < kNet3Hidden; ++j) {
+            R a = R(0);
+#pragma unroll
+            for (int o = 0; o < 3; ++o) a += W2[o * kNet3Hidden + j] * gz[o];
+            const R ga = a * (R(1) - s.h[j] * s.h[j]);
+            sh.ga1[t][j] = ga;
+            sh.h[t][j] = s.h[j];
+#pragma unroll
+            for (int m = 0; m < kNetIn; ++m) gI[m] += W1[j * kNetIn + m] * ga;
+        }
+#pragma unroll
+        for (int m = 0; m < kNetIn; ++m) gI[m] *= scale[m];
+        learned_adj_tail(s, c, gI, lam_out, g.plane, n);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sh.x[t][m] = m < kNetIn ? s.x[m] : R(0);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) sh.gz[t][o] = o < 3 ? gz[o] : R(0);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kNet3Hidden; ++j) {
+            sh.ga1[t][j] = R(0);
+            sh.h[t][j] = R(0);
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sh.x[t][m] = R(0);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) sh.gz[t][o] = R(0);
+    }
+#pragma unroll
+    for (int j = kNet3Hidden; j < kH3Pad; ++j) {
+        sh.ga1[t][j] = R(0);
+        sh.h[t][j] = R(0);
+    }
+    __syncthreads();
+    // partials accumulate over the adjoint steps of one run
+    block_theta3_grad(sh, t, gth_partials + (int64_t)(blockIdx.x + (int64_t)gridDim.x * blockIdx.y) * kNet3Theta);
 }
 
 template <class R>
@@ -731,6 +1020,53 @@ cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc)
     }
 }
 
+template <class R>
+static Net3<R> make_net3(const double* v)
+{
+    Net3<R> n;
+    for (int k = 0; k < kNet3Values; ++k) n.v[k] = (R)v[k];
+    return n;
+}
+
+template <class T>
+static cudaError_t launch_learned3(const OpArgs& a, const double* netv)
+{
+    using R = typename Store<T>::Real;
+    const Net3<R> net = make_net3<R>(netv);
+    const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
+    if (a.op == OP_UPDATE) {
+        const T* src = (const T*)a.src;
+        T* dst = (T*)a.dst;
+        if (a.mode == AB) k_learned3_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        else if (a.mode == AA_EVEN)
+            k_learned3_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        else k_learned3_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        return cudaGetLastError();
+    }
+    if (a.op == OP_ADJ_STEP) {
+        const size_t smem = sizeof(Adj3Shared<R>);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_learned3_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_learned3_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
+                                                          (R)a.omega, (R*)a.gth, net);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net)
+{
+    if (a.g.nz != 1) return cudaErrorInvalidValue;
+    switch (a.storage) {
+    case S_F64: return launch_learned3<double>(a, net);
+    case S_F32: return launch_learned3<float>(a, net);
+    case S_F16: return launch_learned3<__half>(a, net);
+    case S_BF16: return launch_learned3<__nv_bfloat16>(a, net);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 int64_t learned_adj_partial_count(const Geom& g)
 {
     return (int64_t)((g.nx + kAdjBlock - 1) / kAdjBlock) * g.ny;
@@ -741,37 +1077,39 @@ int64_t learned_adj_partial_count(const Geom& g)
 constexpr int kThetaChunks = 128;
 
 template <class P>
-__global__ void __launch_bounds__(256) k_reduce_theta_chunks(const P* partials, int64_t nblk, double* chunk)
+__global__ void __launch_bounds__(256) k_reduce_theta_chunks(const P* partials, int64_t nblk, int nth, double* chunk)
 {
     const int64_t per = (nblk + kThetaChunks - 1) / kThetaChunks;
     const int64_t b0 = blockIdx.x * per, b1 = b0 + per < nblk ? b0 + per : nblk;
-    for (int o = threadIdx.x; o < kNetTheta; o += blockDim.x) {
+    for (int o = threadIdx.x; o < nth; o += blockDim.x) {
         double acc = 0.0;
-        for (int64_t b = b0; b < b1; ++b) acc += (double)partials[b * kNetTheta + o];
-        chunk[(int64_t)blockIdx.x * kNetTheta + o] = acc;
+        for (int64_t b = b0; b < b1; ++b) acc += (double)partials[b * nth + o];
+        chunk[(int64_t)blockIdx.x * nth + o] = acc;
     }
 }
 
-__global__ void k_reduce_theta_final(const double* chunk, void* out, int out_f64)
+__global__ void k_reduce_theta_final(const double* chunk, int nth, void* out, int out_f64)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= kNetTheta) return;
+    if (o >= nth) return;
     double acc = 0.0;
-    for (int c = 0; c < kThetaChunks; ++c) acc += chunk[(int64_t)c * kNetTheta + o];
+    for (int c = 0; c < kThetaChunks; ++c) acc += chunk[(int64_t)c * nth + o];
     if (out_f64) ((double*)out)[o] += acc;
     else ((float*)out)[o] += (float)acc;
 }
 
 int64_t learned_theta_chunk_doubles() { return (int64_t)kThetaChunks * kNetTheta; }
 
-cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, double* chunk, void* out,
-                                 int out_f64, cudaStream_t s)
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int ntheta, int part_f64, double* chunk,
+                                 void* out, int out_f64, cudaStream_t s)
 {
-    if (part_f64) k_reduce_theta_chunks<double><<<kThetaChunks, 256, 0, s>>>((const double*)partials, nblk, chunk);
-    else k_reduce_theta_chunks<float><<<kThetaChunks, 256, 0, s>>>((const float*)partials, nblk, chunk);
+    if (ntheta <= 0 || ntheta > kNetTheta) return cudaErrorInvalidValue;
+    if (part_f64)
+        k_reduce_theta_chunks<double><<<kThetaChunks, 256, 0, s>>>((const double*)partials, nblk, ntheta, chunk);
+    else k_reduce_theta_chunks<float><<<kThetaChunks, 256, 0, s>>>((const float*)partials, nblk, ntheta, chunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_theta_final<<<(kNetTheta + 127) / 128, 128, 0, s>>>(chunk, out, out_f64);
+    k_reduce_theta_final<<<(ntheta + 127) / 128, 128, 0, s>>>(chunk, ntheta, out, out_f64);
     return cudaGetLastError();
 }
 

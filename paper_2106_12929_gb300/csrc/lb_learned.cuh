@@ -10,11 +10,19 @@ constexpr int kNetIn = 6, kNetHidden = 24;
 constexpr int kNetTheta = kNetHidden * kNetIn + kNetHidden + kNetHidden * kNetHidden + kNetHidden + kNetHidden + 1;
 constexpr int kNetValues = kNetTheta + 2 * kNetIn;  // + input shift and scale
 static_assert(kNetTheta == 793, "6-24-24-1 network has 793 parameters");
+// the network shape Sec. 3.1 describes: one hidden layer, three outputs (one relaxation
+// time per higher moment)
+constexpr int kNet3Hidden = 53;
+constexpr int kNet3Theta = kNet3Hidden * kNetIn + kNet3Hidden + 3 * kNet3Hidden + 3;
+constexpr int kNet3Values = kNet3Theta + 2 * kNetIn;
+static_assert(kNet3Theta == 533, "6-53-3 network has 533 parameters");
 
 // forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
 // net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint)
 // tc = 1: forward step with the network's hidden layers on the tensor cores (BF16 x BF16 -> FP32)
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc = false);
+// the same for the one-hidden-layer network with three outputs (net = kNet3Values doubles)
+cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net);
 // Network weights for the tensor-core path, packed once per lb_set_mlp into a device table:
 // bytes needed, and the host-side packing into `out` (learned_tc_table_bytes() bytes).
 size_t learned_tc_table_bytes();
@@ -23,11 +31,11 @@ void learned_tc_pack(const double* net, void* out);
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // number of blocks of the learned adjoint launch (rows of the gradient partials)
 int64_t learned_adj_partial_count(const Geom& g);
-// out[793] (+)= sum over blocks of partials[block][793] (two deterministic passes through
-// `chunk`, learned_theta_chunk_doubles() doubles of scratch)
+// out[ntheta] (+)= sum over blocks of partials[block][ntheta] (two deterministic passes
+// through `chunk`, learned_theta_chunk_doubles() doubles of scratch; ntheta <= kNetTheta)
 int64_t learned_theta_chunk_doubles();
-cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int part_f64, double* chunk, void* out,
-                                 int out_f64, cudaStream_t s);
+cudaError_t learned_reduce_theta(const void* partials, int64_t nblk, int ntheta, int part_f64, double* chunk,
+                                 void* out, int out_f64, cudaStream_t s);
 
 struct LossEq6Args {
     OpArgs a;                    // state, geometry, stream

@@ -43,7 +43,8 @@ class Lattice:
     """One periodic lattice advanced by liblb on one GPU.
 
     stencil: "D2Q9" | "D3Q19" | "D3Q27"; dims: (nx, ny, nz) with nz = 1 in 2D;
-    tau > 1/2; collision: "bgk" | "regularized" | "learned" | "none" | "trt" | "kbc" | "mrt";
+    tau > 1/2; collision: "bgk" | "regularized" | "learned" (6-24-24-1 network, one higher-moment
+    rate) | "learned3" (6-53-3 network, one rate per higher moment) | "none" | "trt" | "kbc" | "mrt";
     storage: "f64" | "f32" | "f16" | "bf16" (the half types store f_i - w_i);
     layout: "ab" (two buffers) | "aa" (in place); record_every > 0 keeps
     checkpoints for ``step_adjoint``; learned_tc runs the learned collision's network
@@ -221,6 +222,34 @@ class Lattice:
         """The six (unstandardised) network inputs of every node, [6, N]."""
         out = self._out((6, self.N), dtype, device)
         _lib.check(self._lib.lb_learned_inputs(self._h, out.data_ptr(), _mem_code(out)), "lb_learned_inputs")
+        return out
+
+    # ------------------------------------------------------------------ spectral flow control
+    def set_spectral_control(self, sigma0, cutoff: float = 2e-5, kappa: float = 5e-5):
+        """Sec. 3.2: every later step collides at u + du, du = -kappa grad_u R, R the log-spectrum
+        mismatch to sigma0 (n/2 shells) with cutoff c; sigma0 None turns it off."""
+        if sigma0 is None:
+            _lib.check(self._lib.lb_set_spectral_control(self._h, None, 0, 0.0, 0.0), "lb_set_spectral_control")
+            return self
+        s0 = np.ascontiguousarray(np.asarray(sigma0, dtype=np.float64).reshape(-1))
+        _lib.check(self._lib.lb_set_spectral_control(self._h, s0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                     s0.size, float(cutoff), float(kappa)),
+                   "lb_set_spectral_control")
+        return self
+
+    def spectrum(self, with_cost: bool = False):
+        """Energy spectrum sigma[n/2] of the current state (and the cost R if with_cost)."""
+        K = self.dims[0] // 2
+        sig = np.zeros(K)
+        cost = ctypes.c_double()
+        _lib.check(self._lib.lb_spectrum(self._h, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(cost) if with_cost else None), "lb_spectrum")
+        return (sig, cost.value) if with_cost else sig
+
+    def spectral_shift(self, dtype=torch.float64, device=None) -> torch.Tensor:
+        """The velocity shift du[2][N] the next controlled step applies."""
+        out = self._out((self.D, self.N), dtype, device)
+        _lib.check(self._lib.lb_spectral_shift(self._h, out.data_ptr(), _mem_code(out)), "lb_spectral_shift")
         return out
 
     # ------------------------------------------------------------------ adjoint

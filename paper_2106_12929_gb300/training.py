@@ -6,8 +6,11 @@ snapshots; each snapshot is mapped onto a grid of half the resolution
 a coarse run with the learned collision is started from it. After ``horizon``
 coarse steps (2 x horizon fine steps) its velocity, vorticity and energy are
 compared with the coarsened fine state by the Eq. 6 loss (``lb_loss_eq6``); the
-gradient w.r.t. the 793 network parameters comes from the checkpointed adjoint
-(``lb_step_adjoint``) and Adam (``lb_adam_update``) updates them. Every step of
+gradient w.r.t. the network parameters comes from the checkpointed adjoint
+(``lb_step_adjoint``) and Adam (``lb_adam_update``) updates them. Two networks:
+``"learned"`` (6-24-24-1, one rate shared by the higher moments, 793 parameters) and
+``"learned3"`` (the shape Sec. 3.1 describes: one hidden layer of 53 units and one rate
+per higher moment, 533 parameters). Every step of
 this runs in liblb's kernels; this module only orders the calls.
 
 The network starts as BGK exactly (output weights 0, output bias ln(tau - 1/2)),
@@ -34,9 +37,8 @@ import torch
 
 import lbinputs
 
+from . import _lib
 from .lattice import Lattice, adam_update
-
-N_THETA = 793
 
 
 def coarse_tau(tau_f: float) -> float:
@@ -59,6 +61,7 @@ class TrainConfig:
     record_every: int = 10
     seed: int = 5
     storage: str = "f32"
+    net: str = "learned"        # "learned" (6-24-24-1) or "learned3" (6-53-3)
 
 
 @dataclass
@@ -104,9 +107,10 @@ def make_shear_data(cfg: TrainConfig):
     return samples, torch.cat([shift, scale]).float()
 
 
-def init_theta(tau_c: float, seed: int) -> torch.Tensor:
+def init_theta(tau_c: float, seed: int, net: str = "learned") -> torch.Tensor:
     """Xavier hidden layers, zero output weights, output bias ln(tau_c - 1/2): exactly BGK."""
-    th = lbinputs.random_mlp_params(seed, out_bias=math.log(tau_c - 0.5), out_scale=0.0)
+    gen = lbinputs.random_mlp3_params if net == "learned3" else lbinputs.random_mlp_params
+    th = gen(seed, out_bias=math.log(tau_c - 0.5), out_scale=0.0)
     return torch.tensor(th, dtype=torch.float32, device="cuda")
 
 
@@ -134,10 +138,10 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
     train_set = samples[: n - 2 * cfg.holdout]
     val = samples[n - 2 * cfg.holdout: n - cfg.holdout]   # early stopping
     hold = samples[n - cfg.holdout:]                       # reported gain, never used for choices
-    theta = init_theta(tau_c, cfg.seed)
+    theta = init_theta(tau_c, cfg.seed, cfg.net)
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
-    lat = Lattice("D2Q9", (nc, nc, 1), tau_c, "learned", storage=cfg.storage, record_every=cfg.record_every)
+    lat = Lattice("D2Q9", (nc, nc, 1), tau_c, cfg.net, storage=cfg.storage, record_every=cfg.record_every)
     rng = np.random.default_rng(cfg.seed)
     hist = {"train_loss": [], "holdout_loss": []}
     lat.set_mlp(torch.cat([theta, extra]))
@@ -149,7 +153,7 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
     t0 = time.perf_counter()
     for it in range(1, cfg.iters + 1):
         lat.set_mlp(torch.cat([theta, extra]))
-        g = torch.zeros(N_THETA, dtype=torch.float32, device="cuda")
+        g = torch.zeros(_lib.n_theta(cfg.net), dtype=torch.float32, device="cuda")
         pick = rng.choice(len(train_set), size=min(cfg.batch, len(train_set)), replace=False)
         Ls = [rollout_loss(lat, train_set[j], cfg.horizon, grad=g) for j in pick]
         if not torch.isfinite(g).all():
@@ -194,7 +198,7 @@ def spectrum_2d(u: np.ndarray, n: int):
 
 def evaluate_turbulence(theta, extra, n_coarse: int = 2048, k0: float = 12.0, u_rms: float = 0.05,
                         seed: int = 30000, re: float = 30000.0, steps: int = 4000, every: int = 250,
-                        storage: str = "f32", reference: str = "bgk"):
+                        storage: str = "f32", reference: str = "bgk", net: str = "learned"):
     """Learned vs BGK on coarse decaying turbulence against the coarsened fine run (BGK on
     the grid of twice the resolution). If the fine reference itself goes unstable the
     result records when (the caller then lowers Re)."""
@@ -205,7 +209,7 @@ def evaluate_turbulence(theta, extra, n_coarse: int = 2048, k0: float = 12.0, u_
     fine = Lattice("D2Q9", (nf, nf, 1), tau_f, reference, storage=storage)
     fine.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     ref = Lattice("D2Q9", (n_coarse, n_coarse, 1), tau_c, "bgk", storage="f64")
-    learned = Lattice("D2Q9", (n_coarse, n_coarse, 1), tau_c, "learned", storage=storage)
+    learned = Lattice("D2Q9", (n_coarse, n_coarse, 1), tau_c, net, storage=storage)
     learned.set_mlp(torch.cat([theta.float(), extra.float()]))
     bgk = Lattice("D2Q9", (n_coarse, n_coarse, 1), tau_c, "bgk", storage=storage)
     for lat in (learned, bgk):
@@ -272,10 +276,11 @@ def main():
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--eval-n", type=int, default=2048)
     ap.add_argument("--eval-steps", type=int, default=2000)
-    ap.add_argument("--save", type=str, default=None, help="write theta + input scaling (805 floats) here")
+    ap.add_argument("--net", choices=["learned", "learned3"], default="learned")
+    ap.add_argument("--save", type=str, default=None, help="write theta + input scaling (805 / 545 floats) here")
     a = ap.parse_args()
     cfg = TrainConfig(n_fine=a.n_fine, iters=a.iters, tau_fine=a.tau_fine, horizon=a.horizon,
-                      spinup=max(1000, 4 * a.n_fine), snap_every=max(2 * a.horizon + 50, a.n_fine // 2))
+                      spinup=max(1000, 4 * a.n_fine), snap_every=max(2 * a.horizon + 50, a.n_fine // 2), net=a.net)
     t0 = time.perf_counter()
     theta, extra, hist = train(cfg, log=lambda s: print(s, flush=True))
     res = {"train": {k: v for k, v in hist.items() if k != "train_loss"}, "config": asdict(cfg)}
@@ -285,7 +290,7 @@ def main():
     if a.eval_n > 0:
         # Re 30000 first (Sec. 3.1); if the fine reference itself goes unstable there, halve Re
         for re in (30000.0, 15000.0, 7500.0, 3750.0):
-            ev = evaluate_turbulence(theta, extra, n_coarse=a.eval_n, steps=a.eval_steps, re=re)
+            ev = evaluate_turbulence(theta, extra, n_coarse=a.eval_n, steps=a.eval_steps, re=re, net=a.net)
             ev["re"] = re
             res.setdefault("eval_attempts", []).append({"re": re, "reference_unstable_at": ev.get("reference_unstable_at")})
             if "reference_unstable_at" not in ev:

@@ -20,3 +20,18 @@ def test_training_reduces_holdout_loss_below_bgk():
     # gain on rollouts never trained on (about 10 % with these settings)
     assert hist["holdout_gain"] > 0.03, hist
     assert hist["train_loss"][-1] < hist["train_loss"][0], hist
+
+
+def test_training_the_paper_shaped_network_reduces_holdout_loss_below_bgk():
+    """The same training with the network shape Sec. 3.1 describes (one hidden layer of 53
+    units, one relaxation time per higher moment)."""
+    from paper_2106_12929_gb300 import build, training
+    build.build()
+    cfg = training.TrainConfig(n_fine=256, tau_fine=0.503, spinup=1500, snap_every=100, n_snap=14, holdout=3,
+                               horizon=40, batch=4, iters=80, lr=0.05, record_every=10, net="learned3")
+    theta, extra, hist = training.train(cfg, log=print)
+    print({k: v for k, v in hist.items() if k != "train_loss"})
+    assert theta.numel() == 533 and torch.isfinite(theta).all()
+    assert hist["holdout_loss"][0][1] == pytest.approx(hist["holdout_loss_bgk"], rel=1e-2)
+    assert hist["holdout_gain"] > 0.03, hist
+    assert hist["train_loss"][-1] < hist["train_loss"][0], hist
