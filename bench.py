@@ -175,7 +175,8 @@ ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, col
     "d2q9_trt_f32": ("D2Q9", "f32", "ab", "trt"),
     "d3q19_duct_f32": ("D3Q19", "f32", "ab", "bgk"), "d3q19_duct_f16": ("D3Q19", "f16", "ab", "bgk"),
 }
-DUCT = ("d3q19_duct_f32", "d3q19_duct_f16")  # walls: duct with a sphere (radius n/8), driven by F_x
+DUCT = ("d3q19_duct_f32", "d3q19_duct_f16")
+LEARNED_ONLY = ("learned", "learned_tc", "learned3", "learned3_tc")  # network, tensor-core option  # walls: duct with a sphere (radius n/8), driven by F_x
 
 
 def workload(stencil: str, n: int | None):
@@ -199,11 +200,14 @@ def run_only(args):
         print(json.dumps({"only": "adjoint", **adjoint_ratio(torch.cuda.current_stream(), n=args.grid or 1024,
                                                              steps=args.steps)}))
         return
-    if args.only in ("learned", "learned_tc", "learned3"):
+    if args.only == "spectral":
+        print(json.dumps({"only": "spectral", **spectral_control(torch.cuda.current_stream(), n=args.grid or 128,
+                                                               steps=args.steps)}))
+        return
+    if args.only in LEARNED_ONLY:
         print(json.dumps({"only": args.only, **learned_throughput(torch.cuda.current_stream(), n=args.grid or 2048,
-                                                                  steps=args.steps, tc=args.only == "learned_tc",
-                                                                  net="learned3" if args.only == "learned3"
-                                                                  else "learned")}))
+                                                                  steps=args.steps, tc=args.only.endswith("_tc"),
+                                                                  net=args.only.split("_")[0])}))
         return
     stencil, storage, layout, coll = ONLY[args.only]
     dims, tau, rho, u = workload(stencil, args.grid)
@@ -355,10 +359,14 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
         lat.close()
     out.update(adjoint_ratio(stream))
     for key, tc, net in (("learned_f32", False, "learned"), ("learned_tc", True, "learned"),
-                         ("learned3_f32", False, "learned3")):
+                         ("learned3_f32", False, "learned3"), ("learned3_tc", True, "learned3")):
         r = learned_throughput(stream, n=2048, steps=100, tc=tc, net=net)
         out[f"{key}_forward_glups"] = r["forward_glups"]
         out[f"{key}_backward_ms_per_step"] = r["backward_ms_per_step"]
+    for n in (128, 1024):
+        r = spectral_control(stream, n=n, steps=200)
+        out[f"spectral_{n}_controlled_us_per_step"] = r["controlled_us_per_step"]
+        out[f"spectral_{n}_plain_us_per_step"] = r["plain_us_per_step"]
     return out
 
 
@@ -445,6 +453,38 @@ def learned_throughput(stream, n=2048, steps=200, tc=False, net="learned"):
             "forward_ms_per_step": round(n * n / fwd / 1e9 * 1e3, 4)}
 
 
+def spectral_control(stream, n=128, steps=200, storage="f32", kappa=5e-4):
+    """Spectral flow control (Sec. 3.2) on n^2 2D turbulence at Re 2000, Ma 0.1: time per
+    controlled step (velocity shift from the state by FFTs, then the shifted BGK step) and
+    per plain BGK step of the same lattice, both through lb_step."""
+    import torch
+    from paper_2106_12929_gb300 import Lattice
+    dims = (n, n, 1)
+    u0 = 0.1 / math.sqrt(3.0)
+    rho, u = lbinputs.random_spectrum_velocity(dims, 8.0 * n / 128.0, u0, 2000)
+    tau = 0.5 + 3.0 * u0 * (n / (2.0 * math.pi)) / 2000.0
+    lat = Lattice("D2Q9", dims, tau, "bgk", storage=storage)
+    rd, ud = torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda")
+    lat.init_from_moments(rd, ud)
+    sigma0 = lat.spectrum()
+    lat.step(5)
+    t_plain = time_steps(lat, steps, stream)
+    lat.init_from_moments(rd, ud)
+    lat.set_spectral_control(sigma0, kappa=kappa)
+    lat.step(5)
+    l0 = lat.launch_count()
+    t_ctrl = time_steps(lat, steps, stream)
+    launches = (lat.launch_count() - l0) / steps
+    _, R = lat.spectrum(with_cost=True)
+    lat.check()
+    lat.close()
+    return {"grid": [n, n], "storage": storage, "kappa": kappa,
+            "plain_us_per_step": round(t_plain / steps * 1e6, 2),
+            "controlled_us_per_step": round(t_ctrl / steps * 1e6, 2),
+            "controlled_glups": round(n * n * steps / t_ctrl / 1e9, 3),
+            "launches_per_controlled_step": launches, "cost_after": R}
+
+
 def cpu_baseline(sample_steps: int = 1):
     """The FP64 CPU oracle on this host, on a bounded sample of the same workload: the full
     256^3 D3Q19 grid for `sample_steps` step(s)."""
@@ -498,7 +538,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "learned", "learned_tc", "learned3"]), default=None,
+    ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "spectral", *LEARNED_ONLY]),
+                    default=None,
                     help="run a single workload (profiling aid); no contract line")
     ap.add_argument("--grid", type=int, default=None, help="grid size for --only (default 256, adjoint 1024)")
     ap.add_argument("--no-graphs", action="store_true", help="--only: one launch per kernel instead of graph replay")

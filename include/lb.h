@@ -120,8 +120,8 @@ typedef struct {
                              and returns LB_ERR_UNSTABLE if a node went bad; 0 (default) = never */
     int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
                              lb_step_adjoint can run backwards (AB layout only); 0 = off */
-    int learned_tc;       /* LB_LEARNED_MRT, FP32/FP16/BF16 storage: 1 = evaluate the network's two
-                             hidden layers on the tensor cores with BF16 operands and FP32
+    int learned_tc;       /* LB_LEARNED_MRT(3), FP32/FP16/BF16 storage: 1 = evaluate the network's
+                             layers on the tensor cores with BF16 operands and FP32
                              accumulation (an inference option: lb_step_adjoint and training use
                              the FP32 network); 0 (default) = FP32 arithmetic throughout */
     int graphs;           /* 1 (default): lb_step(n >= 2) without checkpoints captures two steps once
@@ -233,7 +233,7 @@ LB_API int64_t lb_steps_taken(const lb_ctx* ctx);
 
 /* Turn the control on (sigma0[K] in host memory, K = n/2 shells, copied; cutoff c > 0,
  * kappa >= 0) or off (sigma0 NULL). From the next lb_step every step computes du from the
- * current state and collides at u + du (six kernel launches per step instead of one).
+ * current state and collides at u + du (seven kernel launches per step instead of one).
  * Needs the BGK collision, no force, no walls and record_every = 0 (LB_ERR_UNSUPPORTED
  * otherwise); LB_ERR_ARG for another K or non-finite values. */
 LB_API lb_status lb_set_spectral_control(lb_ctx* ctx, const double* sigma0, int64_t K, double cutoff,

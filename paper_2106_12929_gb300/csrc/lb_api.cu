@@ -12,6 +12,7 @@
 #include "lb.h"
 #include "lb_ops.cuh"
 #include "lb_learned.cuh"
+#include "lb_spectral.cuh"
 
 namespace {
 
@@ -72,7 +73,7 @@ struct lb_ctx {
     void* F = nullptr;                 // force [D][plane], arithmetic type
     void* links = nullptr;             // bounce-back links [plane] (uint32), see lb::Geom
     void* wall_u = nullptr;            // wall velocity [D][plane], arithmetic type
-    std::vector<double> net;           // learned network (805 values), passed to kernels by value
+    std::vector<double> net;           // learned network (805 or 545 values), passed to kernels by value
     void* tc_table = nullptr;          // learned_tc: packed BF16 weight fragments on the device
     unsigned* status = nullptr;
     double* partials = nullptr;
@@ -91,14 +92,27 @@ struct lb_ctx {
     void* gtheta = nullptr;    // learned: per-block parameter gradient partials
     int64_t gtheta_cap = 0;    // bytes
 
+    // spectral flow control (Sec. 3.2): every step collides at u + du, du = -kappa grad_u R
+    bool sc_on = false;
+    int sc_logn = 0;
+    double sc_cutoff = 2e-5, sc_kappa = 5e-5;
+    void* sc_spec = nullptr;     // [2][n][n] complex values of the arithmetic type
+    double* sc_small = nullptr;  // partials [n/2][n], sigma, grad, r2 [n/2 each], cost [1], sigma0 [n/2]
+    void* sc_du = nullptr;       // [2][plane] arithmetic type
+
     // CUDA graph of a two-step cycle, replayed by lb_step when nothing is recorded
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t cycle = nullptr;
     void* cycle_state = nullptr;  // state buffer the cycle starts from (and returns to)
+    int64_t cycle_launches = 0;   // kernel launches one replay of the cycle makes
     bool graphs = true;
 };
 
 namespace {
+
+bool is_learned(int coll) { return coll == LB_LEARNED_MRT || coll == LB_LEARNED_MRT3; }
+// trained parameters of the context's network (the parameter-gradient length)
+int net_theta(int coll) { return coll == LB_LEARNED_MRT3 ? lb::kNet3Theta : lb::kNetTheta; }
 
 int64_t pop_bytes(const lb_ctx* c) { return (int64_t)c->Q * c->plane * storage_bytes(c->opt.storage); }
 int64_t real_pop_bytes(const lb_ctx* c) { return (int64_t)c->Q * c->plane * real_bytes(c->opt.storage); }
@@ -165,11 +179,43 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     return a;
 }
 
+// spectral-control scratch views of c->sc_small
+lb::SpectralArgs spectral_args(lb_ctx* c, const lb::OpArgs& a)
+{
+    lb::SpectralArgs s;
+    s.a = a;
+    s.n = (int)c->dims[0];
+    s.logn = c->sc_logn;
+    s.spec = c->sc_spec;
+    const int64_t K = s.n / 2;
+    s.partials = c->sc_small;
+    s.sigma = s.partials + (int64_t)s.n * K;
+    s.grad = s.sigma + K;
+    s.r2 = s.grad + K;
+    s.cost = s.r2 + K;
+    s.sigma0 = c->sc_on ? s.cost + 1 : nullptr;
+    s.cutoff = c->sc_cutoff;
+    s.kappa = c->sc_kappa;
+    s.du = c->sc_on ? c->sc_du : nullptr;
+    return s;
+}
+
 lb_status launch(lb_ctx* c, const lb::OpArgs& a, const char* what)
 {
     cudaError_t e;
+    if (c->sc_on && a.op == lb::OP_UPDATE) {
+        // spectral flow control: du from the state, then the step at u + du
+        int n = 0;
+        e = lb::spectral_shift(spectral_args(c, a), &n);
+        if (e == cudaSuccess) e = lb::spectral_update(a, c->sc_du);
+        c->launches += n + 1;
+        if (e != cudaSuccess) return cuda_fail(c, e, what);
+        return LB_OK;
+    }
     if (a.coll == LB_LEARNED_MRT && (a.op == lb::OP_UPDATE || a.op == lb::OP_ADJ_STEP))
         e = lb::run_learned_d2q9(a, c->net.data(), a.op == lb::OP_UPDATE && c->opt.learned_tc);
+    else if (a.coll == LB_LEARNED_MRT3 && (a.op == lb::OP_UPDATE || a.op == lb::OP_ADJ_STEP))
+        e = lb::run_learned3_d2q9(a, c->net.data(), a.op == lb::OP_UPDATE && c->opt.learned_tc);
     else
         e = lb::run_op(c->stencil, a);
     c->launches += 1;
@@ -299,7 +345,7 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     *out = nullptr;
     if (!dims) return fail(LB_ERR_ARG, "dims is null");
     if ((int)stencil < 0 || (int)stencil > 2) return fail(LB_ERR_ARG, "unknown stencil %d", (int)stencil);
-    if ((int)coll < 0 || (int)coll > 6) return fail(LB_ERR_ARG, "unknown collision %d", (int)coll);
+    if ((int)coll < 0 || (int)coll > 7) return fail(LB_ERR_ARG, "unknown collision %d", (int)coll);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_ERR_ARG, "tau must be a finite number > 1/2 (got %g)", tau);
     lb_options o;
     lb_default_options(&o);
@@ -311,22 +357,22 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
     if (o.graphs != 0 && o.graphs != 1) return fail(LB_ERR_ARG, "graphs must be 0 or 1");
     if (o.nodes_per_thread != 0 && o.nodes_per_thread != 1 && o.nodes_per_thread != 2 && o.nodes_per_thread != 4)
         return fail(LB_ERR_ARG, "nodes_per_thread must be 0, 1, 2 or 4");
-    if (o.learned_tc && (coll != LB_LEARNED_MRT || o.storage == LB_F64))
-        return fail(LB_ERR_UNSUPPORTED, "learned_tc needs the learned collision with FP32 or half storage");
+    if (o.learned_tc && (!is_learned(coll) || o.storage == LB_F64))
+        return fail(LB_ERR_UNSUPPORTED, "learned_tc needs a learned collision with FP32 or half storage");
     const int D = stencil == LB_D2Q9 ? 2 : 3;
     for (int a = 0; a < 3; ++a)
         if (dims[a] < 1 || dims[a] > 65535) return fail(LB_ERR_ARG, "dims[%d] = %lld out of [1, 65535]", a, (long long)dims[a]);
     if (D == 2 && dims[2] != 1) return fail(LB_ERR_ARG, "2D stencil needs dims[2] == 1");
     const int64_t N = dims[0] * dims[1] * dims[2];
     if (N >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "grid of %lld nodes exceeds 2^31 - 1", (long long)N);
-    if (coll == LB_LEARNED_MRT && stencil != LB_D2Q9)
+    if (is_learned(coll) && stencil != LB_D2Q9)
         return fail(LB_ERR_UNSUPPORTED, "the learned collision is defined for D2Q9 only");
     if (coll == LB_MRT && stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "MRT is provided for D2Q9 only");
     if (coll == LB_KBC && stencil == LB_D3Q19)
         return fail(LB_ERR_UNSUPPORTED, "KBC needs a tensor-product velocity set (D2Q9 or D3Q27)");
     if (o.record_every > 0 && o.layout != LB_LAYOUT_AB)
         return fail(LB_ERR_UNSUPPORTED, "recording for the adjoint needs the AB layout");
-    if (o.record_every > 0 && coll > LB_NONE)
+    if (o.record_every > 0 && (coll == LB_TRT || coll == LB_KBC || coll == LB_MRT))
         return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
 
     int dev = o.device;
@@ -387,7 +433,7 @@ void lb_destroy(lb_ctx* c)
     if (c->cycle) cudaGraphExecDestroy(c->cycle);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
-                    c->gF, c->gtheta, c->links, c->wall_u};
+                    c->gF, c->gtheta, c->links, c->wall_u, c->sc_spec, c->sc_small, c->sc_du};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->ckpt)
@@ -424,8 +470,9 @@ lb_status lb_set_force(lb_ctx* c, const void* F, lb_mem m)
     if (s != LB_OK) return s;
     drop_cycle(c);  // the force pointer (or its absence) is baked into the captured steps
     if (!mem_valid(m)) return fail(LB_ERR_ARG, "invalid lb_mem");
-    if (F && (c->coll == LB_LEARNED_MRT || c->coll == LB_KBC || c->coll == LB_MRT))
+    if (F && (is_learned(c->coll) || c->coll == LB_KBC || c->coll == LB_MRT))
         return fail(LB_ERR_UNSUPPORTED, "the learned, KBC and MRT collisions take no force");
+    if (F && c->sc_on) return fail(LB_ERR_UNSUPPORTED, "spectral flow control takes no body force");
     DeviceGuard guard(c->device);
     if (!F) {
         if (c->F) {
@@ -453,9 +500,10 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
 {
     lb_status s = check_ctx(c);
     if (s != LB_OK) return s;
-    if (c->coll != LB_LEARNED_MRT) return fail(LB_ERR_STATE, "context does not use the learned collision");
-    if (!params || n != lb::kNetValues || !mem_valid(m))
-        return fail(LB_ERR_ARG, "need %d network values (got %lld)", lb::kNetValues, (long long)n);
+    if (!is_learned(c->coll)) return fail(LB_ERR_STATE, "context does not use a learned collision");
+    const int want = c->coll == LB_LEARNED_MRT3 ? lb::kNet3Values : lb::kNetValues;
+    if (!params || n != want || !mem_valid(m))
+        return fail(LB_ERR_ARG, "need %d network values (got %lld)", want, (long long)n);
     DeviceGuard guard(c->device);
     const int f64 = mem_f64(m);
     std::vector<unsigned char> tmp((size_t)n * (f64 ? 8 : 4));
@@ -472,10 +520,12 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
     for (double x : v)
         if (!std::isfinite(x)) return fail(LB_ERR_ARG, "network values must be finite");
     if (c->opt.learned_tc) {
-        const size_t bytes = lb::learned_tc_table_bytes();
+        const bool three = c->coll == LB_LEARNED_MRT3;
+        const size_t bytes = three ? lb::learned3_tc_table_bytes() : lb::learned_tc_table_bytes();
         if (!c->tc_table && (s = alloc(c, &c->tc_table, (int64_t)bytes, "tensor-core weight table")) != LB_OK) return s;
         std::vector<unsigned char> tab(bytes);
-        lb::learned_tc_pack(v.data(), tab.data());
+        if (three) lb::learned3_tc_pack(v.data(), tab.data());
+        else lb::learned_tc_pack(v.data(), tab.data());
         // the previous table may still be read by queued steps: order the copy on the stream
         LB_CUDA(c, cudaMemcpyAsync(c->tc_table, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream), "weight table");
         LB_CUDA(c, cudaStreamSynchronize(c->stream), "weight table");
@@ -493,7 +543,8 @@ lb_status lb_set_solid(lb_ctx* c, const void* mask, const void* wall_u, lb_mem m
     if (!mask && wall_u) return fail(LB_ERR_ARG, "a wall velocity needs a mask");
     if (mask) {
         if (c->opt.layout != LB_LAYOUT_AB) return fail(LB_ERR_UNSUPPORTED, "walls need the AB layout");
-        if (c->coll == LB_LEARNED_MRT) return fail(LB_ERR_UNSUPPORTED, "the learned collision has no walls");
+        if (is_learned(c->coll)) return fail(LB_ERR_UNSUPPORTED, "the learned collisions have no walls");
+        if (c->sc_on) return fail(LB_ERR_UNSUPPORTED, "spectral flow control needs a periodic grid without walls");
         if (c->opt.record_every > 0) return fail(LB_ERR_UNSUPPORTED, "no adjoint with walls");
     }
     DeviceGuard guard(c->device);
@@ -592,6 +643,114 @@ lb_status lb_set_relaxation(lb_ctx* c, const double* params, int n)
     return LB_OK;
 }
 
+// Grid edge n and log2(n) of a context the spectral calls accept (square D2Q9, n = 2^k).
+static lb_status spectral_grid(const lb_ctx* c, int* logn)
+{
+    if (c->stencil != LB_D2Q9) return fail(LB_ERR_UNSUPPORTED, "the spectral calls are defined for D2Q9");
+    const int64_t n = c->dims[0];
+    if (c->dims[1] != n || n < 4 || n > lb::kSpecMaxN || (n & (n - 1)))
+        return fail(LB_ERR_UNSUPPORTED, "the spectral calls need a square grid of 2^k nodes per side, 4 <= n <= %d",
+                    lb::kSpecMaxN);
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    *logn = l;
+    return LB_OK;
+}
+
+static lb_status spectral_alloc(lb_ctx* c)
+{
+    const int64_t n = c->dims[0], K = n / 2;
+    lb_status s;
+    if (!c->sc_spec && (s = alloc(c, &c->sc_spec, 2 * n * n * 2 * real_bytes(c->opt.storage), "spectrum")) != LB_OK)
+        return s;
+    if (!c->sc_small && (s = alloc(c, (void**)&c->sc_small, (n * K + 4 * K + 1) * 8, "spectral sums")) != LB_OK)
+        return s;
+    return LB_OK;
+}
+
+lb_status lb_set_spectral_control(lb_ctx* c, const double* sigma0, int64_t K, double cutoff, double kappa)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!sigma0) {
+        c->sc_on = false;
+        drop_cycle(c);
+        return LB_OK;
+    }
+    int logn = 0;
+    if ((s = spectral_grid(c, &logn)) != LB_OK) return s;
+    if (c->coll != LB_BGK) return fail(LB_ERR_UNSUPPORTED, "spectral flow control is defined with the BGK collision");
+    if (c->F) return fail(LB_ERR_UNSUPPORTED, "spectral flow control takes no body force");
+    if (c->links) return fail(LB_ERR_UNSUPPORTED, "spectral flow control needs a periodic grid without walls");
+    if (c->opt.record_every > 0) return fail(LB_ERR_UNSUPPORTED, "no adjoint of the spectral flow control");
+    if (K != c->dims[0] / 2) return fail(LB_ERR_ARG, "sigma0 needs n/2 = %lld shells", (long long)(c->dims[0] / 2));
+    if (!(cutoff > 0.0) || !std::isfinite(cutoff) || !(kappa >= 0.0) || !std::isfinite(kappa))
+        return fail(LB_ERR_ARG, "cutoff must be > 0 and kappa >= 0, both finite");
+    for (int64_t k = 0; k < K; ++k)
+        if (!(sigma0[k] >= 0.0) || !std::isfinite(sigma0[k])) return fail(LB_ERR_ARG, "sigma0 must be finite and >= 0");
+    DeviceGuard guard(c->device);
+    if ((s = spectral_alloc(c)) != LB_OK) return s;
+    if (!c->sc_du && (s = alloc(c, &c->sc_du, 2 * c->plane * real_bytes(c->opt.storage), "velocity shift")) != LB_OK)
+        return s;
+    const int64_t n = c->dims[0];
+    // sigma0 sits after partials, sigma, grad, r2 and cost; ordered on the stream after queued steps
+    LB_CUDA(c, cudaMemcpyAsync(c->sc_small + n * K + 3 * K + 1, sigma0, (size_t)K * 8, cudaMemcpyHostToDevice,
+                               c->stream),
+            "sigma0 copy");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "sigma0 copy");
+    c->sc_on = true;
+    c->sc_logn = logn;
+    c->sc_cutoff = cutoff;
+    c->sc_kappa = kappa;
+    drop_cycle(c);  // the captured steps change
+    return LB_OK;
+}
+
+lb_status lb_spectrum(lb_ctx* c, double* sigma, double* cost)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!sigma && !cost) return fail(LB_ERR_ARG, "sigma or cost is required");
+    if (cost && !c->sc_on) return fail(LB_ERR_STATE, "the cost needs a target (lb_set_spectral_control)");
+    int logn = 0;
+    if ((s = spectral_grid(c, &logn)) != LB_OK) return s;
+    DeviceGuard guard(c->device);
+    if ((s = spectral_alloc(c)) != LB_OK) return s;
+    c->sc_logn = logn;
+    lb::SpectralArgs sa = spectral_args(c, base_args(c, lb::OP_MOMENTS));
+    sa.du = nullptr;
+    int n = 0;
+    cudaError_t e = lb::spectral_shift(sa, &n);
+    c->launches += n;
+    if (e != cudaSuccess) return cuda_fail(c, e, "spectrum");
+    const int64_t K = c->dims[0] / 2;
+    if (sigma) LB_CUDA(c, cudaMemcpyAsync(sigma, sa.sigma, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream), "sigma");
+    if (cost) LB_CUDA(c, cudaMemcpyAsync(cost, sa.cost, 8, cudaMemcpyDeviceToHost, c->stream), "cost");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "spectrum sync");
+    return LB_OK;
+}
+
+lb_status lb_spectral_shift(lb_ctx* c, void* du, lb_mem m)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!du || !mem_valid(m)) return fail(LB_ERR_ARG, "du and a valid lb_mem are required");
+    if (!c->sc_on) return fail(LB_ERR_STATE, "spectral flow control is not set");
+    DeviceGuard guard(c->device);
+    lb::SpectralArgs sa = spectral_args(c, base_args(c, lb::OP_MOMENTS));
+    int n = 0;
+    cudaError_t e = lb::spectral_shift(sa, &n);
+    c->launches += n;
+    if (e != cudaSuccess) return cuda_fail(c, e, "velocity shift");
+    Staged so;
+    if ((s = stage_out_alloc(c, so, du, c->N * c->D, m, false, "du")) != LB_OK) return s;
+    LB_CUDA(c, lb::convert_copy(c->sc_du, c->opt.storage == LB_F64, so.dev, mem_f64(m), c->N, c->plane, c->N, c->D, 0,
+                                c->stream),
+            "du copy");
+    c->launches += 1;
+    return stage_out_finish(c, so, du, "du");
+}
+
 static lb_status step_once(lb_ctx* c)
 {
     const int k = c->opt.record_every;
@@ -659,6 +818,7 @@ static bool build_cycle(lb_ctx* c)
     c->stream = c->cap_stream;
     bool ok = step_once(c) == LB_OK && step_once(c) == LB_OK;
     c->stream = user;
+    const int64_t captured = c->launches - launches0;
     cudaGraph_t graph = nullptr;
     const bool ended = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess;
     // the captured launches did not run: restore the bookkeeping
@@ -681,6 +841,7 @@ static bool build_cycle(lb_ctx* c)
     }
     c->cycle = exec;
     c->cycle_state = start;
+    c->cycle_launches = captured;
     return true;
 }
 
@@ -689,7 +850,7 @@ lb_status lb_step(lb_ctx* c, int64_t n)
     lb_status s = check_ctx(c);
     if (s != LB_OK) return s;
     if (n < 0) return fail(LB_ERR_ARG, "negative step count");
-    if (c->coll == LB_LEARNED_MRT && c->net.empty()) return fail(LB_ERR_STATE, "network not set");
+    if (is_learned(c->coll) && c->net.empty()) return fail(LB_ERR_STATE, "network not set");
     DeviceGuard guard(c->device);
     if (c->opt.record_every > 0 && !c->recording && n > 0)
         if ((s = record_begin(c)) != LB_OK) return s;
@@ -704,7 +865,7 @@ lb_status lb_step(lb_ctx* c, int64_t n)
             if (c->cycle) {
                 LB_CUDA(c, cudaGraphLaunch(c->cycle, c->stream), "step graph");
                 c->steps += 2;
-                c->launches += 2;
+                c->launches += c->cycle_launches;
                 t += 2;
                 if (c->opt.check_every > 0 && t % c->opt.check_every == 0)
                     if ((s = lb_check(c)) != LB_OK) return s;
@@ -906,8 +1067,9 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     if (k <= 0) return fail(LB_ERR_STATE, "context was created with record_every = 0");
     if (n != c->steps) return fail(LB_ERR_STATE, "n = %lld but %lld steps were recorded", (long long)n, (long long)c->steps);
     if (n > 0 && !c->recording) return fail(LB_ERR_STATE, "no recorded run");
-    if (gth && c->coll != LB_LEARNED_MRT) return fail(LB_ERR_ARG, "grad_theta needs the learned collision");
-    if (c->coll > LB_NONE) return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
+    if (gth && !is_learned(c->coll)) return fail(LB_ERR_ARG, "grad_theta needs a learned collision");
+    if (c->coll == LB_TRT || c->coll == LB_KBC || c->coll == LB_MRT)
+        return fail(LB_ERR_UNSUPPORTED, "no adjoint of the TRT, KBC or MRT collision");
     if (c->links) return fail(LB_ERR_UNSUPPORTED, "no adjoint with walls");
     DeviceGuard guard(c->device);
     const int f64 = c->opt.storage == LB_F64;
@@ -922,9 +1084,10 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
         c->ring.push_back(p);
     }
     int64_t nblk = 0;
-    if (c->coll == LB_LEARNED_MRT) {
+    const int ntheta = net_theta(c->coll);
+    if (is_learned(c->coll)) {
         nblk = lb::learned_adj_partial_count(c->g);
-        const int64_t need = nblk * 793;
+        const int64_t need = nblk * ntheta;
         // block partials, then the chunk sums of the deterministic reduction
         const int64_t bytes = need * real_bytes(c->opt.storage) + lb::learned_theta_chunk_doubles() * 8 + 256;
         if (c->gtheta_cap < bytes) {
@@ -988,10 +1151,11 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     }
     if (gth) {
         Staged so;
-        if ((s = stage_out_alloc(c, so, gth, 793, m, true, "grad_theta")) != LB_OK) return s;
-        const int64_t part_bytes = nblk * 793 * real_bytes(c->opt.storage);
+        if ((s = stage_out_alloc(c, so, gth, ntheta, m, true, "grad_theta")) != LB_OK) return s;
+        const int64_t part_bytes = nblk * ntheta * real_bytes(c->opt.storage);
         double* chunk = (double*)((char*)c->gtheta + (part_bytes + 255) / 256 * 256);
-        LB_CUDA(c, lb::learned_reduce_theta(c->gtheta, nblk, f64, chunk, so.dev, mem_f64(m), c->stream), "grad_theta");
+        LB_CUDA(c, lb::learned_reduce_theta(c->gtheta, nblk, ntheta, f64, chunk, so.dev, mem_f64(m), c->stream),
+                "grad_theta");
         c->launches += 2;
         if ((s = stage_out_finish(c, so, gth, "grad_theta")) != LB_OK) return s;
     }

@@ -801,6 +801,137 @@ __global__ void __launch_bounds__(128) k_learned3_update(const T* src, T* dst, G
     if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
 }
 
+// The three-output network on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation), laid out like k_learned_update_tc: a warp's 32 nodes are two 16-row tiles;
+// layer 1 multiplies [32 x 16] inputs (6 used) by W1^T [16 x 56] (53 used, seven n-tiles),
+// layer 2 the tanh activations [32 x 64] (56 from layer 1's accumulators, in place as A
+// fragments) by W2^T [64 x 8] (3 used). Outputs: lanes 4g and 4g + 1 hold columns 0, 1 and
+// 2, 3 of rows g and g + 8.
+constexpr int kNet3Tiles = (kNet3Hidden + 7) / 8;  // 7
+struct Net3Frag {
+    uint32_t w1[kNet3Tiles][32];  // layer 1, n-tile t: B register 0 per lane
+    uint32_t w2[4][2][32];        // layer 2, k-step s (k = 16s..16s+15): B registers 0, 1 per lane
+    float b1[8 * kNet3Tiles];
+    float b2[8];
+};
+
+size_t learned3_tc_table_bytes() { return sizeof(Net3Frag); }
+
+void learned3_tc_pack(const double* v, void* out)
+{
+    const double* W1 = v;
+    const double* b1 = W1 + kNet3Hidden * kNetIn;
+    const double* W2 = b1 + kNet3Hidden;
+    const double* b2 = W2 + 3 * kNet3Hidden;
+    Net3Frag fr;
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, q = lane & 3;
+        for (int t = 0; t < kNet3Tiles; ++t) {
+            const int n = 8 * t + g;
+            auto w1 = [&](int k) { return (n < kNet3Hidden && k < kNetIn) ? W1[n * kNetIn + k] : 0.0; };
+            fr.w1[t][lane] = (uint32_t)bf16_bits(w1(2 * q)) | ((uint32_t)bf16_bits(w1(2 * q + 1)) << 16);
+        }
+        for (int st = 0; st < 4; ++st)
+            for (int r = 0; r < 2; ++r) {
+                const int k0 = 16 * st + 2 * q + 8 * r;
+                auto w2 = [&](int k) { return (g < 3 && k < kNet3Hidden) ? W2[g * kNet3Hidden + k] : 0.0; };
+                fr.w2[st][r][lane] = (uint32_t)bf16_bits(w2(k0)) | ((uint32_t)bf16_bits(w2(k0 + 1)) << 16);
+            }
+    }
+    for (int k = 0; k < 8 * kNet3Tiles; ++k) fr.b1[k] = k < kNet3Hidden ? (float)b1[k] : 0.f;
+    for (int k = 0; k < 8; ++k) fr.b2[k] = k < 3 ? (float)b2[k] : 0.f;
+    std::memcpy(out, &fr, sizeof(fr));
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_learned3_update_tc(const T* src, T* dst, Geom g, float omega,
+                                                            unsigned* status, const Net3<float> net,
+                                                            const uint32_t* __restrict__ table)
+{
+    constexpr int kWords = (int)(sizeof(Net3Frag) / 4);
+    __shared__ uint32_t stab[kWords];
+    __shared__ uint32_t sx[4][32][4];  // per warp: 32 nodes x 8 BF16 inputs
+    for (int k = threadIdx.x; k < kWords; k += blockDim.x) stab[k] = table[k];
+    __syncthreads();
+    const Net3Frag& fr = *reinterpret_cast<const Net3Frag*>(stab);
+    const float* shift = net.v + kNet3Theta;
+    const float* scale = shift + kNetIn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = x < g.nx;  // every lane takes part in the warp's matrix products
+    const int y = blockIdx.y;
+    Nbr nb = make_nbr<sizeof(T)>(g, valid ? x : 0, y, 0);
+    const int n = x + g.nx * y;
+    float f[9];
+    if (valid) load_node<D2Q9, MODE>(src, g, nb, n, f);
+    else
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = 0.f;
+    Learned3Node<float> s;
+    float I[kNetIn];
+    learned_inputs(f, s, I);
+    float xin[kNetIn];
+#pragma unroll
+    for (int k = 0; k < kNetIn; ++k) xin[k] = (I[k] - shift[k]) * scale[k];
+    sx[warp][lane][0] = pack_bf16(xin[0], xin[1]);
+    sx[warp][lane][1] = pack_bf16(xin[2], xin[3]);
+    sx[warp][lane][2] = pack_bf16(xin[4], xin[5]);
+    sx[warp][lane][3] = 0u;
+    __syncwarp();
+    const int gq = lane >> 2, q = lane & 3;
+    float zc[2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const uint32_t a0 = sx[warp][16 * m + gq][q], a1 = sx[warp][16 * m + gq + 8][q];
+        uint32_t h[8][2];
+#pragma unroll
+        for (int t = 0; t < kNet3Tiles; ++t) {
+            float c[4];
+            c[0] = c[2] = fr.b1[8 * t + 2 * q];
+            c[1] = c[3] = fr.b1[8 * t + 2 * q + 1];
+            mma_bf16(c, a0, a1, 0u, 0u, fr.w1[t][lane], 0u);
+            h[t][0] = tanh_bf16x2(pack_bf16(c[0], c[1]));  // row gq
+            h[t][1] = tanh_bf16x2(pack_bf16(c[2], c[3]));  // row gq + 8
+        }
+        h[7][0] = h[7][1] = 0u;
+        float c[4];
+        c[0] = c[2] = fr.b2[2 * q];
+        c[1] = c[3] = fr.b2[2 * q + 1];
+#pragma unroll
+        for (int st = 0; st < 4; ++st)
+            mma_bf16(c, h[2 * st][0], h[2 * st][1], h[2 * st + 1][0], h[2 * st + 1][1], fr.w2[st][0][lane],
+                     fr.w2[st][1][lane]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) zc[m][k] = c[k];
+    }
+    // node r = lane: tile r / 16, row r % 16 (g = row % 8, upper half = row / 8); its outputs
+    // 0, 1 sit in lane 4g (c0, c1 or c2, c3) and output 2 in lane 4g + 1 (c0 or c2)
+    const int row = lane & 15, src0 = 4 * (row & 7), up = row >> 3, mt = lane >> 4;
+    float z[3];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const float v0 = __shfl_sync(0xffffffffu, zc[m][0], src0), v1 = __shfl_sync(0xffffffffu, zc[m][1], src0);
+        const float v2 = __shfl_sync(0xffffffffu, zc[m][2], src0), v3 = __shfl_sync(0xffffffffu, zc[m][3], src0);
+        const float w0 = __shfl_sync(0xffffffffu, zc[m][0], src0 + 1);
+        const float w2 = __shfl_sync(0xffffffffu, zc[m][2], src0 + 1);
+        if (m == mt) {
+            z[0] = up ? v2 : v0;
+            z[1] = up ? v3 : v1;
+            z[2] = up ? w2 : w0;
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const int r = net3_row(o);
+        s.ez[r] = expf(z[o]);
+        s.omg[r] = 1.f / (s.ez[r] + 0.5f);
+    }
+    if (!valid) return;
+    learned3_post(s, omega, f);
+    store_node<D2Q9, MODE>(dst, g, nb, n, f);
+    if (!(s.m.rho > 0.f && s.m.rho < 1e30f)) atomicOr(status, 1u);
+}
+
 // Block reduction of the parameter gradient of the three-output network. The hidden units
 // (padded to kH3Pad) form kT3Tiles register tiles of four; each tile's nodes are split into
 // kT3Parts interleaved subsets (so that the threads of a warp read distinct banks); one thread
@@ -1029,11 +1160,28 @@ static Net3<R> make_net3(const double* v)
 }
 
 template <class T>
-static cudaError_t launch_learned3(const OpArgs& a, const double* netv)
+static cudaError_t launch_learned3(const OpArgs& a, const double* netv, bool tc)
 {
     using R = typename Store<T>::Real;
     const Net3<R> net = make_net3<R>(netv);
     const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
+    if constexpr (sizeof(R) == 4) {
+        if (tc && a.op == OP_UPDATE) {
+            if (!a.tc_table) return cudaErrorInvalidValue;
+            const uint32_t* tab = (const uint32_t*)a.tc_table;
+            const T* src = (const T*)a.src;
+            T* dst = (T*)a.dst;
+            if (a.mode == AB)
+                k_learned3_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
+            else if (a.mode == AA_EVEN)
+                k_learned3_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
+                                                                          tab);
+            else
+                k_learned3_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
+                                                                         tab);
+            return cudaGetLastError();
+        }
+    }
     if (a.op == OP_UPDATE) {
         const T* src = (const T*)a.src;
         T* dst = (T*)a.dst;
@@ -1055,14 +1203,14 @@ static cudaError_t launch_learned3(const OpArgs& a, const double* netv)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net)
+cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc)
 {
     if (a.g.nz != 1) return cudaErrorInvalidValue;
     switch (a.storage) {
-    case S_F64: return launch_learned3<double>(a, net);
-    case S_F32: return launch_learned3<float>(a, net);
-    case S_F16: return launch_learned3<__half>(a, net);
-    case S_BF16: return launch_learned3<__nv_bfloat16>(a, net);
+    case S_F64: return launch_learned3<double>(a, net, false);
+    case S_F32: return launch_learned3<float>(a, net, tc);
+    case S_F16: return launch_learned3<__half>(a, net, tc);
+    case S_BF16: return launch_learned3<__nv_bfloat16>(a, net, tc);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -22,11 +22,14 @@ static_assert(kNet3Theta == 533, "6-53-3 network has 533 parameters");
 // tc = 1: forward step with the network's hidden layers on the tensor cores (BF16 x BF16 -> FP32)
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc = false);
 // the same for the one-hidden-layer network with three outputs (net = kNet3Values doubles)
-cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net);
+cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc = false);
 // Network weights for the tensor-core path, packed once per lb_set_mlp into a device table:
 // bytes needed, and the host-side packing into `out` (learned_tc_table_bytes() bytes).
 size_t learned_tc_table_bytes();
 void learned_tc_pack(const double* net, void* out);
+// the same for the three-output network (learned3_tc_table_bytes() bytes)
+size_t learned3_tc_table_bytes();
+void learned3_tc_pack(const double* net, void* out);
 // out[6][N] <- the six network inputs (moment invariants) of every node of the state a.src
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // number of blocks of the learned adjoint launch (rows of the gradient partials)

@@ -184,6 +184,31 @@ def test_autograd_parameter_gradient_matches_oracle():
     assert np.max(np.abs(theta.grad.cpu().numpy() - gth)) <= 1e-10 * np.max(np.abs(gth))
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_tensor_core_option(storage, layout):
+    """The network on the tensor cores (BF16 operands, FP32 accumulation) against the FP32
+    kernel: with zero output weights both give z = the output biases (they differ by FP32
+    rounding elsewhere, which can flip an FP16 rounding); with a random network the BF16
+    activations move the rates by ~1e-2 relative."""
+    dims = (130, 40, 1)  # two blocks of 128 lanes per row, the second one ragged
+    rho, u = lbinputs.random_moments(dims, seed=7, u_amp=0.05)
+    tau = 0.6
+    same_tol = 1e-6 if storage == "f32" else 2e-4
+    for net, tol in ((net3(tau, out_scale=0.0, taus=(0.9, 0.7, 1.3)), same_tol),
+                     (net3(tau, seed=12, taus=(0.9, 0.7, 1.3)), 1e-3)):
+        a = L(NAME, dims, tau, "learned3", storage=storage, layout=layout)
+        b = L(NAME, dims, tau, "learned3", storage=storage, layout=layout, learned_tc=True)
+        for lat in (a, b):
+            lat.set_mlp(net)
+            lat.init_from_moments(rho, u)
+            lat.step(10)
+        fa, fb = pops(a), pops(b)
+        assert werr(fa, fb, W) <= tol
+        if tol == 1e-3:
+            assert werr(fa, fb, W) > 0.0  # the BF16 network really ran
+
+
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_graph_replay_equals_single_steps(layout):
     dims = (48, 20, 1)
@@ -216,7 +241,7 @@ def test_argument_checks():
     with pytest.raises(LBError, match="LB_ERR_UNSUPPORTED"):
         lat.set_force(np.zeros((2, 128)))
     with pytest.raises(LBError, match="LB_ERR_UNSUPPORTED"):
-        L(NAME, dims, 0.6, "learned3", storage="f32", learned_tc=True)
+        L(NAME, dims, 0.6, "learned3", storage="f64", learned_tc=True)
     with pytest.raises(LBError, match="LB_ERR_UNSUPPORTED"):
         L("D3Q19", (8, 8, 8), 0.6, "learned3")
     lat.set_mlp(net3(0.6))

@@ -69,7 +69,7 @@ def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
     (dict(nodes_per_thread=3), 1),
     (dict(coll=8), 1),
     (dict(stencil=1, dims=(4, 4, 4), coll=7), 6),   # the three-output network is D2Q9 only too
-    (dict(coll=7, learned_tc=1), 6),                # no tensor-core option for it
+    (dict(coll=7, learned_tc=1, storage=0), 6),     # its tensor-core option needs FP32 or half storage
     (dict(stencil=1, dims=(4, 4, 4), coll=5), 6),  # KBC needs D2Q9 or D3Q27
     (dict(stencil=2, dims=(4, 4, 4), coll=6), 6),  # MRT is D2Q9 only
     (dict(coll=4, record_every=3), 6),             # no adjoint of TRT / KBC / MRT
