@@ -188,7 +188,7 @@ LB_API lb_status lb_set_relaxation(lb_ctx* ctx, const double* params, int n);
  * u_w = wall_u at the solid node x + c_i (wall density 1; wall_u [d][N] or NULL = resting
  * walls). Solid nodes do not collide; their exposed state is the rest equilibrium f_i = w_i.
  * mask NULL removes all walls. AB layout only, not with the learned collision or recording
- * (LB_ERR_UNSUPPORTED). With walls every step runs one node per thread. Copies both arrays. */
+ * (LB_ERR_UNSUPPORTED). Copies both arrays. */
 LB_API lb_status lb_set_solid(lb_ctx* ctx, const void* mask, const void* wall_u, lb_mem mem);
 
 /* Advance n >= 0 steps of Eq. 1 (one fused kernel launch per step). */

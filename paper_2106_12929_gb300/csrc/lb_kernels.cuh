@@ -51,6 +51,35 @@ LB_DEV void load_force(const R* F, const Geom& g, int n, R* Fl)
     Fl[2] = St::D == 3 ? F[2 * g.plane + n] : R(0);
 }
 
+// Halfway bounce-back writes of one fluid node with link word lk (AB layout): for every solid
+// neighbour x - c_i the next step pulls f_i(x) from slot i of that solid node, which receives
+// f*_opp(i)(x) + 2 w_i (c_i . u_wall) / c_s^2 (moving-wall term; wall density 1). Solid slots
+// are written by these reflections only (a solid node stores nothing itself), and each
+// (solid node, slot) pair has exactly one fluid source, so the writes never collide.
+template <class St, bool RAW, class T>
+LB_DEV void bounce_back(T* dst, const Geom& g, const Nbr& nb, unsigned lk, const typename Store<T>::Real* f)
+{
+    using R = typename Store<T>::Real;
+    const R* Wu = (const R*)g.wall_u;
+#pragma unroll
+    for (int i = 1; i < St::Q; ++i) {
+        if (!((lk >> i) & 1u)) continue;
+        const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
+        R v = f[opp(i)];
+        if (Wu) {
+            const int m = nb.node(g, -cx, -cy, -cz);
+            R cu = R(0);
+            if (cx) cu += cx > 0 ? Wu[m] : -Wu[m];
+            if (cy) cu += cy > 0 ? Wu[g.plane + m] : -Wu[g.plane + m];
+            if (St::D == 3 && cz) cu += cz > 0 ? Wu[2 * g.plane + m] : -Wu[2 * g.plane + m];
+            v += R(6.0 * St::w(i)) * cu;
+        }
+        T* p = at(dst, nb, i, -cx, -cy, -cz);
+        if constexpr (RAW) store_raw<St>(p, i, v);
+        else store_pop<St>(p, i, v);
+    }
+}
+
 // ------------------------------------------------------------------ step (K1/K2)
 template <class St, class T, int COLL, bool FORCE, int MODE>
 __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
@@ -71,28 +100,7 @@ __global__ void __launch_bounds__(128) k_update(const T* src, T* dst, const type
     if constexpr (FORCE) load_force<St>(F, g, id.n, Fl);
     bool ok = collide<St, COLL, FORCE>(f, Fl, rx);
     store_node<St, MODE, RAW>(dst, g, nb, id.n, f);
-    if (MODE == AB && lk) {
-        // x - c_i solid: next step pulls f_i(x) from slot i of that node, which receives
-        // f*_opp(i)(x) + 2 w_i (c_i . u_wall) / c_s^2 (moving-wall term; wall density 1)
-        const R* Wu = (const R*)g.wall_u;
-#pragma unroll
-        for (int i = 1; i < St::Q; ++i) {
-            if (!((lk >> i) & 1u)) continue;
-            const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
-            R v = f[opp(i)];
-            if (Wu) {
-                const int m = nb.node(g, -cx, -cy, -cz);
-                R cu = R(0);
-                if (cx) cu += cx > 0 ? Wu[m] : -Wu[m];
-                if (cy) cu += cy > 0 ? Wu[g.plane + m] : -Wu[g.plane + m];
-                if (St::D == 3 && cz) cu += cz > 0 ? Wu[2 * g.plane + m] : -Wu[2 * g.plane + m];
-                v += R(6.0 * St::w(i)) * cu;
-            }
-            T* p = at(dst, nb, i, -cx, -cy, -cz);
-            if constexpr (RAW) store_raw<St>(p, i, v);
-            else store_pop<St>(p, i, v);
-        }
-    }
+    if (MODE == AB && lk) bounce_back<St, RAW>(dst, g, nb, lk, f);
     if (!ok) atomicOr(status, 1u);
 }
 
@@ -115,7 +123,7 @@ __global__ void k_build_links(const unsigned char* mask, Geom g, unsigned* links
 // two scalar accesses, the inner one at a fixed byte distance from the vector
 // address. Every AB store and every non-x-moving load is a vector access, which
 // halves the memory instructions and conversions per node.
-template <class St, class T, int COLL, bool FORCE, int MODE>
+template <class St, class T, int COLL, bool FORCE, int MODE, bool WALLS = false>
 __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const typename Store<T>::Real* F, Geom g,
                                                      Relax<typename Store<T>::Real> rx, unsigned* status)
 {
@@ -124,6 +132,15 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x0 >= g.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
+    // walls (AB only): link words of both nodes (n0 is even: nx is even for this kernel)
+    unsigned lk0 = 0u, lk1 = 0u;
+    if constexpr (WALLS) {
+        const uint2 l = *(const uint2*)(g.links + (x0 + (int64_t)g.nx * (y + (int64_t)g.ny * z)));
+        lk0 = l.x;
+        lk1 = l.y;
+        if (lk0 & lk1 & kSolidBit) return;
+    }
+    const bool sol0 = WALLS && (lk0 & kSolidBit), sol1 = WALLS && (lk1 & kSolidBit);
     const int yy[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
     const int zz[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
     const int64_t xo_m = (int64_t)(x0 == 0 ? g.nx - 1 : x0 - 1) * S;       // x0 - 1
@@ -158,15 +175,20 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
         Pair2<R>::load(F + g.plane + n0, F0[1], F1[1]);
         if (St::D == 3) Pair2<R>::load(F + 2 * g.plane + n0, F0[2], F1[2]);
     }
-    const bool ok0 = collide<St, COLL, FORCE>(f0, F0, rx);
-    const bool ok1 = collide<St, COLL, FORCE>(f1, F1, rx);
+    const bool ok0 = collide<St, COLL, FORCE>(f0, F0, rx) || sol0;  // a solid node's result is dropped
+    const bool ok1 = collide<St, COLL, FORCE>(f1, F1, rx) || sol1;
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_EVEN) ? opp(i) : i;
         const int sx = ss * St::c(i, 0);
         char* base = (char*)dst + slot * pb + row(ss * St::c(i, 1), ss * St::c(i, 2));
         if (sx == 0) {
-            store_pop2<St>((T*)(base + xo_0), slot, f0[i], f1[i]);
+            if (WALLS && (sol0 || sol1)) {  // a solid node's slots belong to the reflections
+                if (!sol0) store_pop<St>((T*)(base + xo_0), slot, f0[i]);
+                if (!sol1) store_pop<St>((T*)(base + xo_0 + S), slot, f1[i]);
+            } else {
+                store_pop2<St>((T*)(base + xo_0), slot, f0[i], f1[i]);
+            }
         } else if (sx < 0) {
             store_pop<St>((T*)(base + xo_m), slot, f0[i]);
             store_pop<St>((T*)(base + xo_0), slot, f1[i]);
@@ -174,6 +196,10 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
             store_pop<St>((T*)(base + xo_0 + S), slot, f0[i]);
             store_pop<St>((T*)(base + xo_2), slot, f1[i]);
         }
+    }
+    if constexpr (WALLS) {
+        if (lk0 && !sol0) bounce_back<St, false>(dst, g, make_nbr<S>(g, x0, y, z), lk0, f0);
+        if (lk1 && !sol1) bounce_back<St, false>(dst, g, make_nbr<S>(g, x0 + 1, y, z), lk1, f1);
     }
     if (!(ok0 && ok1)) atomicOr(status, 1u);
 }
@@ -184,7 +210,7 @@ __global__ void __launch_bounds__(128) k_update_pair(const T* src, T* dst, const
 // instructions and conversions per node again. An access with x shift 0 is one vector for all
 // four nodes; a load shifted by -1 or +1 takes the vector at x0 (three of its values) plus
 // one scalar; a shifted store is four scalar stores.
-template <class St, class T, int COLL, bool FORCE, int MODE>
+template <class St, class T, int COLL, bool FORCE, int MODE, bool WALLS = false>
 __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const float* F, Geom g, Relax<float> rx,
                                                      unsigned* status)
 {
@@ -193,6 +219,17 @@ __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x0 >= g.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
+    // walls (AB only): link words of the four nodes (n0 % 4 == 0: nx % 4 == 0 here)
+    unsigned lk[4] = {0u, 0u, 0u, 0u};
+    bool sol[4] = {false, false, false, false};
+    if constexpr (WALLS) {
+        const uint4 l = *(const uint4*)(g.links + (x0 + (int64_t)g.nx * (y + (int64_t)g.ny * z)));
+        lk[0] = l.x; lk[1] = l.y; lk[2] = l.z; lk[3] = l.w;
+        if (lk[0] & lk[1] & lk[2] & lk[3] & kSolidBit) return;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sol[k] = (lk[k] & kSolidBit) != 0u;
+    }
+    const bool any_solid = WALLS && (sol[0] || sol[1] || sol[2] || sol[3]);
     const int yy[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
     const int zz[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
     const int64_t xo_m = (int64_t)(x0 == 0 ? g.nx - 1 : x0 - 1) * S;  // x0 - 1
@@ -233,15 +270,21 @@ __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const
     }
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ok = collide<St, COLL, FORCE>(f[k], Fl[k], rx) && ok;
+    for (int k = 0; k < 4; ++k) ok = (collide<St, COLL, FORCE>(f[k], Fl[k], rx) || sol[k]) && ok;
 #pragma unroll
     for (int i = 0; i < St::Q; ++i) {
         const int slot = (MODE == AA_EVEN) ? opp(i) : i;
         const int sx = ss * St::c(i, 0);
         char* base = (char*)dst + slot * pb + row(ss * St::c(i, 1), ss * St::c(i, 2));
         if (sx == 0) {
-            const float v[4] = {f[0][i], f[1][i], f[2][i], f[3][i]};
-            Quad4<T>::store((T*)(base + xo_0), v);
+            if (any_solid) {  // a solid node's slots belong to the reflections
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!sol[k]) Store<T>::store((T*)(base + xo_0 + k * S), f[k][i]);
+            } else {
+                const float v[4] = {f[0][i], f[1][i], f[2][i], f[3][i]};
+                Quad4<T>::store((T*)(base + xo_0), v);
+            }
         } else if (sx < 0) {
             Store<T>::store((T*)(base + xo_m), f[0][i]);
             Store<T>::store((T*)(base + xo_0), f[1][i]);
@@ -253,6 +296,11 @@ __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const
             Store<T>::store((T*)(base + xo_0 + 3 * S), f[2][i]);
             Store<T>::store((T*)(base + xo_4), f[3][i]);
         }
+    }
+    if constexpr (WALLS) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (lk[k] && !sol[k]) bounce_back<St, false>(dst, g, make_nbr<S>(g, x0 + k, y, z), lk[k], f[k]);
     }
     if (!ok) atomicOr(status, 1u);
 }
@@ -608,7 +656,6 @@ template <class St, class T, int COLL>
 inline int update_shape(const OpArgs& a)
 {
     if (COLL == NONE) return 1;  // streaming only: stored values move untouched, one per thread
-    if (a.g.links) return 1;     // walls: the bounce-back writes live in the one-node kernel
     int npt = a.npt;
     if (npt == 0) {
         // four per thread for half storage, except D3Q27 KBC, whose 27 entropic weights per
@@ -636,7 +683,11 @@ cudaError_t launch_update(const OpArgs& a)
             const int quads = a.g.nx / 4;
             const dim3 bl(quads >= 128 ? 128 : ((quads + 31) / 32) * 32, 1, 1);
             const dim3 gr((quads + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
-            if (a.mode == AB)
+            if (a.g.links) {  // walls: AB only
+                if constexpr (COLL != NONE)
+                    k_update_quad<St, T, COLL, FORCE, AB, true><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx,
+                                                                                         a.status);
+            } else if (a.mode == AB)
                 k_update_quad<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
             else if (a.mode == AA_EVEN)
                 k_update_quad<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx,
@@ -652,7 +703,10 @@ cudaError_t launch_update(const OpArgs& a)
         const int pairs = a.g.nx / 2;
         const dim3 bl(pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32, 1, 1);
         const dim3 gr((pairs + bl.x - 1) / bl.x, a.g.ny, a.g.nz);
-        if (a.mode == AB)
+        if (a.g.links) {  // walls: AB only
+            if constexpr (COLL != NONE)
+                k_update_pair<St, T, COLL, FORCE, AB, true><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
+        } else if (a.mode == AB)
             k_update_pair<St, T, COLL, FORCE, AB><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);
         else if (a.mode == AA_EVEN)
             k_update_pair<St, T, COLL, FORCE, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, F, a.g, rx, a.status);

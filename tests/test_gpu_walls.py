@@ -194,3 +194,70 @@ def test_walls_argument_checks():
         L("D2Q9", (8, 8, 1), 0.7, "learned", storage="f32").set_solid(mask)
     with pytest.raises(LBError):
         L("D2Q9", (8, 8, 1), 0.7, "bgk", storage="f32", record_every=2).set_solid(mask)
+
+
+# ------------------------------------------------------------------ walls in the vector kernels
+SHAPE_CASES = [("D2Q9", (16, 6, 1)), ("D3Q19", (8, 5, 4)), ("D3Q27", (12, 4, 3))]
+
+
+def _wall_colls(name):
+    colls = [("bgk", True), ("regularized", False), ("trt", True)]
+    if name != "D3Q19":
+        colls.append(("kbc", False))
+    if name == "D2Q9":
+        colls.append(("mrt", False))
+    return colls
+
+
+@pytest.mark.parametrize("name,dims", SHAPE_CASES)
+def test_two_nodes_per_thread_with_walls_fp64(name, dims):
+    """Two nodes per thread with walls (a solid node inside a vector access keeps its slots for
+    the reflections; the fluid one is stored alone), 30 % solid, moving walls: the oracle."""
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    mask = lbinputs.random_solid_mask(dims, seed=31, fraction=0.3)
+    f0 = near_eq(name, dims, seed=32)
+    F = lbinputs.random_field((d, N), seed=33, amp=1e-3)
+    wall_u = lbinputs.random_field((d, N), seed=34, amp=0.02) * mask
+    for coll, forced in _wall_colls(name):
+        lat = L(name, dims, 0.64, coll, storage="f64", nodes_per_thread=2)
+        if forced:
+            lat.set_force(F)
+        lat.set_populations(f0)
+        lat.set_solid(mask, wall_u)
+        lat.step(5)
+        ref = oracle.step_walls(name, dims, 0.64, coll, f0, mask, nsteps=5, F=F if forced else None, wall_u=wall_u)
+        assert werr(gpu_pops(lat), ref, w) <= 1e-12, coll
+
+
+@pytest.mark.parametrize("name,dims", SHAPE_CASES)
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_wall_launch_shapes_agree(name, dims, storage):
+    """One, two and four nodes per thread with walls run the same per-node arithmetic: the
+    states agree to the last bits of the arithmetic type (FP32 1e-6) or one quantisation step
+    of the stored deviation (half, 1e-4), relative to w_i; half storage also tracks the oracle."""
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    mask = lbinputs.random_solid_mask(dims, seed=35, fraction=0.3)
+    f0 = near_eq(name, dims, seed=36)
+    F = lbinputs.random_field((d, N), seed=37, amp=1e-3)
+    wall_u = lbinputs.random_field((d, N), seed=38, amp=0.02) * mask
+    for coll, forced in _wall_colls(name):
+        out = []
+        for npt in (1, 2, 4):
+            lat = L(name, dims, 0.64, coll, storage=storage, nodes_per_thread=npt)
+            if forced:
+                lat.set_force(F)
+            lat.set_populations(f0)
+            lat.set_solid(mask, wall_u)
+            lat.step(4)
+            out.append(gpu_pops(lat))
+            lat.close()
+        tol = 1e-6 if storage == "f32" else 1e-4
+        for o in out[1:]:
+            assert werr(o, out[0], w) <= tol, coll
+        if storage != "f32":
+            ref = oracle.step_walls(name, dims, 0.64, coll, f0, mask, nsteps=4, F=F if forced else None,
+                                    wall_u=wall_u)
+            dev = np.max(np.abs(ref - w[:, None]) / w[:, None])
+            assert werr(out[2], ref, w) <= {"f16": 2e-3, "bf16": 2e-2}[storage] * dev, coll
