@@ -174,9 +174,11 @@ ONLY = {  # single-workload runs (for profiling): (stencil, storage, layout, col
     "d2q9_kbc_f32": ("D2Q9", "f32", "ab", "kbc"), "d2q9_mrt_f32": ("D2Q9", "f32", "ab", "mrt"),
     "d2q9_trt_f32": ("D2Q9", "f32", "ab", "trt"),
     "d3q19_duct_f32": ("D3Q19", "f32", "ab", "bgk"), "d3q19_duct_f16": ("D3Q19", "f16", "ab", "bgk"),
+    "d3q19_force_f32": ("D3Q19", "f32", "ab", "bgk"), "d3q19_force_f16": ("D3Q19", "f16", "ab", "bgk"),
 }
-DUCT = ("d3q19_duct_f32", "d3q19_duct_f16")
-LEARNED_ONLY = ("learned", "learned_tc", "learned3", "learned3_tc")  # network, tensor-core option  # walls: duct with a sphere (radius n/8), driven by F_x
+DUCT = ("d3q19_duct_f32", "d3q19_duct_f16")  # walls: duct with a sphere (radius n/8), driven by F_x
+FORCED = DUCT + ("d3q19_force_f32", "d3q19_force_f16")  # constant body force F_x (Guo source)
+LEARNED_ONLY = ("learned", "learned_tc", "learned3", "learned3_tc")  # network, tensor-core option
 
 
 def workload(stencil: str, n: int | None):
@@ -215,18 +217,21 @@ def run_only(args):
     lat = Lattice(stencil, dims, tau, coll, storage=storage, layout=layout, graphs=not args.no_graphs,
                   nodes_per_thread=args.nodes_per_thread)
     lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
-    if args.only in DUCT:
+    if args.only in FORCED:
         F = np.zeros((3, N))
         F[0] = 1e-6
-        lat.set_force(torch.tensor(F, dtype=torch.float32, device="cuda"))
+        lat.set_force(torch.tensor(F, dtype=torch.float64 if storage == "f64" else torch.float32, device="cuda"))
+    if args.only in DUCT:
         lat.set_solid(lbinputs.duct_with_obstacle(dims, radius=dims[0] / 8.0))
     lat.step(args.warmup)
     t = time_steps(lat, args.steps, torch.cuda.current_stream())
     lat.check()
     g = N * args.steps / t / 1e9
     bpl = BYTES_PER_LU[(stencil, storage)]
-    if args.only in DUCT:  # + force read (arithmetic type) + the 4-byte link word of every node
-        bpl += 3 * (8 if storage == "f64" else 4) + 4
+    if args.only in FORCED:  # + force read (arithmetic type)
+        bpl += 3 * (8 if storage == "f64" else 4)
+    if args.only in DUCT:  # + the 4-byte link word of every node
+        bpl += 4
     print(json.dumps({"only": args.only, "grid": list(dims), "steps": args.steps, "graphs": not args.no_graphs,
                       "nodes_per_thread": args.nodes_per_thread,
                       "glups": round(g, 3),

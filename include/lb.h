@@ -129,7 +129,8 @@ typedef struct {
                              of one per kernel; same kernels, same results); 0 = direct launches */
     int nodes_per_thread; /* shape of the stream-collide launch: 0 (default) = chosen from the grid
                              (one node per thread in 32-thread blocks when the grid has fewer rows
-                             than SMs, else four per thread for half storage, two otherwise);
+                             than SMs, else four per thread for half storage without a force,
+                             two otherwise);
                              1, 2 or 4 = forced, falling back to the next smaller shape the grid
                              allows (2 needs an even nx; 4 needs half storage and nx % 4 == 0).
                              Every shape gives bit-identical results */

@@ -261,29 +261,46 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
                 f[i] = v;
             }
         } else {
-            equilibrium<St>(m, feq);  // REG: keep only the Hermite order <= 2 projection of f - f^eq
+            // REG: keep only the Hermite order <= 2 projection of f - f^eq. Opposite velocities
+            // i, i + 1 share the even parts, which halves the work per pair: f^eq = w (a +- b)
+            // with a = (rho - 1) + rho (4.5 (c.u)^2 - 1.5 u.u) and b = 3 rho c.u; the second
+            // moments of f - f^eq take the pair sums; the correction (c c - I/3):Pi is even in c.
+            const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+            const R a0 = m.rho1 - m.rho * uu15, rho45 = R(4.5) * m.rho, rho3 = R(3) * m.rho;
+            feq[0] = R(St::w(0)) * a0;
             R pxx = R(0), pyy = R(0), pzz = R(0), pxy = R(0), pxz = R(0), pyz = R(0);
             R ax = R(0), ay = R(0), az = R(0);
 #pragma unroll
-            for (int i = 0; i < St::Q; ++i) {
-                const R d = f[i] - feq[i];
+            for (int i = 1; i < St::Q; i += 2) {  // opp(i) = i + 1
+                const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
+                const R a = a0 + rho45 * cu * cu, b = rho3 * cu;
+                feq[i] = R(St::w(i)) * (a + b);
+                feq[i + 1] = R(St::w(i)) * (a - b);
+                const R di = f[i] - feq[i], dj = f[i + 1] - feq[i + 1];
+                const R sp = di + dj;
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
-                if (cx) pxx += d;
-                if (cy) pyy += d;
-                if (St::D == 3 && cz) pzz += d;
-                if (cx && cy) pxy += (cx == cy) ? d : -d;
-                if (St::D == 3 && cx && cz) pxz += (cx == cz) ? d : -d;
-                if (St::D == 3 && cy && cz) pyz += (cy == cz) ? d : -d;
+                if (cx) pxx += sp;
+                if (cy) pyy += sp;
+                if (St::D == 3 && cz) pzz += sp;
+                if (cx && cy) pxy += (cx == cy) ? sp : -sp;
+                if (St::D == 3 && cx && cz) pxz += (cx == cz) ? sp : -sp;
+                if (St::D == 3 && cy && cz) pyz += (cy == cz) ? sp : -sp;
                 if constexpr (FORCE) {
-                    if (cx) ax += cx > 0 ? d : -d;
-                    if (cy) ay += cy > 0 ? d : -d;
-                    if (St::D == 3 && cz) az += cz > 0 ? d : -d;
+                    const R sm = di - dj;
+                    if (cx) ax += cx > 0 ? sm : -sm;
+                    if (cy) ay += cy > 0 ? sm : -sm;
+                    if (St::D == 3 && cz) az += cz > 0 ? sm : -sm;
                 }
             }
             const R tr = pxx + pyy + pzz;
             const R relax = R(1) - omega;
+            {
+                R v = feq[0] + relax * R(St::w(0)) * (R(4.5) * (-tr * R(1.0 / 3.0)));
+                if constexpr (FORCE) v += guo_source<St>(0, m, F, pre);
+                f[0] = v;
+            }
 #pragma unroll
-            for (int i = 0; i < St::Q; ++i) {
+            for (int i = 1; i < St::Q; i += 2) {
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
                 // (c c - cs2 I) : Pi
                 R qp = -tr * R(1.0 / 3.0);
@@ -293,11 +310,17 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
                 if (cx && cy) qp += (cx == cy) ? R(2) * pxy : R(-2) * pxy;
                 if (St::D == 3 && cx && cz) qp += (cx == cz) ? R(2) * pxz : R(-2) * pxz;
                 if (St::D == 3 && cy && cz) qp += (cy == cz) ? R(2) * pyz : R(-2) * pyz;
-                R neq = R(4.5) * qp;
-                if constexpr (FORCE) neq += R(3) * cdotu<St>(i, ax, ay, az);
-                R v = feq[i] + relax * R(St::w(i)) * neq;
-                if constexpr (FORCE) v += guo_source<St>(i, m, F, pre);
-                f[i] = v;
+                const R e = R(4.5) * qp;
+                R o = R(0);
+                if constexpr (FORCE) o = R(3) * cdotu<St>(i, ax, ay, az);
+                const R rw = relax * R(St::w(i));
+                R vi = feq[i] + rw * (e + o), vj = feq[i + 1] + rw * (e - o);
+                if constexpr (FORCE) {
+                    vi += guo_source<St>(i, m, F, pre);
+                    vj += guo_source<St>(i + 1, m, F, pre);
+                }
+                f[i] = vi;
+                f[i + 1] = vj;
             }
         }
         return m.rho > R(0) && m.rho < R(1e30);

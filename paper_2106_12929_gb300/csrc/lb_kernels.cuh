@@ -659,8 +659,10 @@ inline int update_shape(const OpArgs& a)
     int npt = a.npt;
     if (npt == 0) {
         // four per thread for half storage, except D3Q27 KBC, whose 27 entropic weights per
-        // node make four nodes too many live registers
-        const bool quad_ok = Store<T>::shifted && !(St::Q == 27 && COLL == KBC);
+        // node make four nodes too many live registers, and with a body force (the Guo source
+        // takes the four-node kernel to 168 registers: D3Q19 FP16 at 256^3 runs 64.0 GLUPS
+        // with two nodes per thread, 60.5 with four)
+        const bool quad_ok = Store<T>::shifted && !(St::Q == 27 && COLL == KBC) && !a.force;
         npt = small_grid(a) ? 1 : (quad_ok ? 4 : 2);
     }
     if (npt == 4 && !(Store<T>::shifted && a.g.nx % 4 == 0)) npt = 2;
