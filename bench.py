@@ -46,7 +46,7 @@ BYTES_PER_LU = {  # algorithmic bytes per lattice update: read Q + write Q popul
 # DRAM traffic per launch of the D3Q19 FP32 AB stream-collide kernel at 256^3 from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources
 # with the listed hash; the hash is recomputed at run time and the figure dropped if it differs.
-NCU_TRAFFIC = {"kernel_hash": "74d8b353d95c8066", "bytes_per_launch": 2493143296}  # ncu of --only ab_f32, 256^3
+NCU_TRAFFIC = {"kernel_hash": "f18ecd039cb3dfdc", "bytes_per_launch": 2493409792}  # ncu of --only ab_f32, 256^3
 KERNEL_SOURCES = ["lb_device.cuh", "lb_collide.cuh", "lb_kernels.cuh"]
 
 
@@ -505,6 +505,50 @@ def cpu_baseline(sample_steps: int = 1):
             "sample": f"D3Q19 BGK FP64, 256^3 TGV, {sample_steps} step(s) ({dt:.1f} s wall)"}
 
 
+def cpu_baseline_table():
+    """The FP64 CPU oracle on this host's cores (as many as OMP_NUM_THREADS allows) on bounded
+    samples of each workload: the 2D TGV at 64^2 (all 1000 steps), the 3D TGV at 64^3 and
+    256^3, D3Q27 regularized turbulence at 384^3, and the forced D2Q9 shear layer at 1024^2
+    forward plus adjoint. One JSON object per sample, in MLUPS."""
+    import oracle
+    rows = []
+
+    def timed(label, nodes, steps, fn):
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        rows.append({"sample": label, "mlups": round(nodes * steps / dt / 1e6, 3), "seconds": round(dt, 2)})
+
+    dims, rho, u = lbinputs.taylor_green_2d(64, u0=0.05)
+    f = oracle.init_eq("D2Q9", dims, rho, u)
+    timed("D2Q9 BGK FP64 TGV 64^2 x 1000 steps", 64 * 64, 1000, lambda: oracle.step("D2Q9", dims, 0.8, "bgk", f, 1000))
+    for n, steps in ((64, 100), (256, 10)):
+        dims, tau, rho, u = tgv_workload(n)
+        f = oracle.init_eq("D3Q19", dims, rho, u)
+        timed(f"D3Q19 BGK FP64 TGV {n}^3 x {steps} steps", n ** 3, steps,
+              lambda: oracle.step("D3Q19", dims, tau, "bgk", f, steps))
+    # 384^3 holds three 12 GB FP64 population arrays on the host; smaller hosts take 256^3
+    avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    n = 384 if avail > 200e9 else 256
+    dims = (n, n, n)
+    rho, u = lbinputs.random_spectrum_velocity(dims, 8.0, 0.04, 2106)
+    f = oracle.init_eq("D3Q27", dims, rho, u)
+    tau = 0.5 + 3.0 * 0.04 * (n / (2.0 * math.pi)) / 3000.0
+    timed(f"D3Q27 regularized FP64 turbulence {n}^3 x 3 steps", n ** 3, 3,
+          lambda: oracle.step("D3Q27", dims, tau, "regularized", f, 3))
+    del f, rho, u
+    dims, rho, u = lbinputs.shear_layer(1024, u0=0.05)
+    N = 1024 * 1024
+    F = lbinputs.smooth_force(dims, 1e-5, seed=12929)
+    f0 = oracle.init_eq("D2Q9", dims, rho, u)
+    lam = lbinputs.random_field((9, N), seed=1)
+    timed("D2Q9 BGK+Guo FP64 shear layer 1024^2 x 20 steps, forward", N, 20,
+          lambda: oracle.step("D2Q9", dims, 0.51, "bgk", f0, 20, F=F))
+    timed("D2Q9 BGK+Guo FP64 shear layer 1024^2 x 20 steps, adjoint (with its forward sweep)", N, 20,
+          lambda: oracle.adjoint("D2Q9", dims, 0.51, "bgk", f0, 20, lam, F=F))
+    return {"cores": oracle.num_threads(), "samples": rows}
+
+
 def run_reference(args):
     """The oracle timed on the host cores as the reference arm: each step is one lattice
     update of a 64^3 periodic TGV at the same Re and Ma (a bounded sample of the workload)."""
@@ -543,6 +587,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the CPU oracle on bounded samples of every workload (no GPU work)")
     ap.add_argument("--only", choices=sorted(list(ONLY) + ["adjoint", "spectral", *LEARNED_ONLY]),
                     default=None,
                     help="run a single workload (profiling aid); no contract line")
@@ -553,7 +599,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.cpu_table:
+        print(json.dumps(cpu_baseline_table()))
+    elif args.impl == "reference":
         run_reference(args)
     elif args.only:
         run_only(args)
