@@ -945,22 +945,27 @@ static_assert(kT3Tiles * kT3Parts <= kAdjBlock, "one thread per tile and subset"
 
 template <class R>
 struct Adj3Shared {
-    R ga1[kAdjBlock][kH3Pad];
+    union {
+        R ga1[kAdjBlock][kH3Pad];
+        R part[kT3Parts][kT3Tiles][kT3Vals + 1];  // reuses ga1 once every thread has read it
+    };
     R h[kAdjBlock][kH3Pad];
     R x[kAdjBlock][8];
     R gz[kAdjBlock][4];
-    R part[kT3Parts][kT3Tiles][kT3Vals + 1];
 };
+static_assert(kT3Parts * kT3Tiles * (kT3Vals + 1) <= kAdjBlock * kH3Pad, "partials fit in the ga1 rows");
 
 template <class R>
 LB_DEV void block_theta3_grad(Adj3Shared<R>& sh, int t, R* out)
 {
     constexpr int oW1 = 0, ob1 = kNet3Hidden * kNetIn, oW2 = ob1 + kNet3Hidden, ob2 = oW2 + 3 * kNet3Hidden;
-    if (t < kT3Tiles * kT3Parts) {
-        const int tile = t % kT3Tiles, part = t / kT3Tiles, j0 = 4 * tile;
-        R acc[kT3Vals];
+    const bool worker = t < kT3Tiles * kT3Parts;
+    const int tile = t % kT3Tiles, part = t / kT3Tiles;
+    R acc[kT3Vals];
 #pragma unroll
-        for (int k = 0; k < kT3Vals; ++k) acc[k] = R(0);
+    for (int k = 0; k < kT3Vals; ++k) acc[k] = R(0);
+    if (worker) {
+        const int j0 = 4 * tile;
         for (int q = part; q < kAdjBlock; q += kT3Parts) {
             R ga[4], hv[4], xv[8], gz[4];
             ld4(&sh.ga1[q][j0], ga);
@@ -981,6 +986,9 @@ LB_DEV void block_theta3_grad(Adj3Shared<R>& sh, int t, R* out)
                 for (int b = 0; b < 4; ++b) acc[28 + 4 * o + b] += gz[o] * hv[b];
             }
         }
+    }
+    __syncthreads();  // ga1 is read by every tile: only now may the partials overwrite it
+    if (worker) {
 #pragma unroll
         for (int k = 0; k < kT3Vals; ++k) sh.part[part][tile][k] = acc[k];
     }
