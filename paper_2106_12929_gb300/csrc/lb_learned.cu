@@ -402,16 +402,21 @@ constexpr int kAdjBlock = 128;
 
 // shared-memory staging of the per-node backprop vectors of one block (rows 16-byte
 // aligned so that four consecutive hidden units load as one vector)
-constexpr int kRow = 28;  // row stride: 16-byte aligned, and 8 consecutive rows hit distinct banks
+// Row stride 24 (16-byte aligned rows) keeps the block at 53.8 KB of FP32 shared memory, so four
+// blocks fit on an SM; the reduction's threads read one row at a time (no bank conflicts), the
+// staging stores of consecutive rows conflict two ways.
+constexpr int kRow = 24;
 template <class R>
 struct AdjShared {
-    R ga1[kAdjBlock][kRow];
+    union {
+        R ga1[kAdjBlock][kRow];
+        R part[48][28];  // upper half of each reduction tile (24 products + 4 bias sums), after ga1 is read
+    };
     R ga2[kAdjBlock][kRow];
     R h1[kAdjBlock][kRow];
     R h2[kAdjBlock][kRow];
     R x[kAdjBlock][8];
     R gz[kAdjBlock];
-    R part[48][kRow];  // upper half of each reduction tile (24 products + 4 bias sums)
 };
 
 template <class R>
@@ -494,6 +499,7 @@ LB_DEV void block_theta_grad(AdjShared<R>& sh, int t, R* out)
             }
         }
     }
+    __syncthreads();  // every tile has read ga1: the partials may overwrite it
     if (half == 1) {
 #pragma unroll
         for (int k = 0; k < 24; ++k) sh.part[tile][k] = acc[k];
