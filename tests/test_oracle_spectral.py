@@ -134,3 +134,18 @@ def test_control_keeps_the_spectrum_closer_than_the_free_flow():
     Rf = spectral.cost(oracle.moments("D2Q9", dims, free)[1], n, s0)
     Rc = spectral.cost(oracle.moments("D2Q9", dims, ctrl)[1], n, s0)
     assert Rc < 0.5 * Rf, (Rc, Rf)
+
+
+def test_constants_are_the_papers():
+    import os
+    const = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                const[k] = float(v)
+    assert spectral.CUTOFF == const["spectrum_cutoff"]
+    assert spectral.KAPPA == const["force_constant"]
+    # the paper-shaped network: one hidden layer, parameter count within 1 % of the paper's
+    assert const["net_hidden_layers"] == 1
+    assert abs(oracle.N_THETA3 - const["net_parameters"]) <= 0.01 * const["net_parameters"]
