@@ -130,7 +130,7 @@ LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
     for (int k = 0; k < kNetHidden; ++k) z += W3[k] * s.h2[k];
     s.z = z;
     s.ez = act_exp(z);
-    s.omg = R(1) / (s.ez + R(0.5));
+    s.omg = recip(s.ez + R(0.5));  // correctly rounded, as 1 / x
 }
 
 template <class R>
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(128) k_learned_update_tc(const T* src, T* dst,
     const float z = (sel == 0 ? v0 : sel == 1 ? v1 : sel == 2 ? v2 : v3) + net.v[kNetTheta - 1];
     s.z = z;
     s.ez = expf(z);
-    s.omg = 1.f / (s.ez + 0.5f);
+    s.omg = recip(s.ez + 0.5f);
     if (!valid) return;
     learned_post(s, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
@@ -614,7 +614,7 @@ LB_DEV void learned_adj_tail(const LearnedMoments<R>& s, LearnedCot<R> c, const 
     grho -= gPxx * (ux * ux + R(1.0 / 3.0)) + gPxy * ux * uy + gPyy * (uy * uy + R(1.0 / 3.0));
     gux -= rho * (R(2) * ux * gPxx + uy * gPxy);
     guy -= rho * (ux * gPxy + R(2) * uy * gPyy);
-    const R inv = R(1) / rho;
+    const R inv = recip(rho);
     const R gdotu = gux * ux + guy * uy;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -764,7 +764,7 @@ LB_DEV void learned3_forward(const R* f, const Net3<R>& net, Learned3Node<R>& s)
     for (int o = 0; o < 3; ++o) {
         const int r = net3_row(o);
         s.ez[r] = act_exp(z[o]);
-        s.omg[r] = R(1) / (s.ez[r] + R(0.5));
+        s.omg[r] = recip(s.ez[r] + R(0.5));
     }
 }
 
@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(128) k_learned3_update_tc(const T* src, T* dst
     for (int o = 0; o < 3; ++o) {
         const int r = net3_row(o);
         s.ez[r] = expf(z[o]);
-        s.omg[r] = 1.f / (s.ez[r] + 0.5f);
+        s.omg[r] = recip(s.ez[r] + 0.5f);
     }
     if (!valid) return;
     learned3_post(s, omega, f);
