@@ -13,8 +13,9 @@
 // (forward DFT along y, modal energies and per-column shell sums), shells (sigma and
 // dR/dsigma, one warp per shell), cost (R), columns (filter by G, inverse DFT along y), rows
 // (inverse DFT along x, du). Each DFT is an in-place radix-2 FFT of one grid line in shared
-// memory, one block per line, with a per-block twiddle table; both velocity components go
-// through the same butterfly stages. Every sum runs in a fixed order (deterministic).
+// memory, one block per line, in passes of three radix-2 stages held in registers (a padded
+// layout keeps the passes free of bank conflicts), with a per-block twiddle table; both velocity
+// components go through the same passes. Every sum runs in a fixed order (deterministic).
 #include "lb_collide.cuh"
 #include "lb_spectral.cuh"
 
@@ -41,28 +42,57 @@ LB_DEV void twiddles(Cx<R>* tw, int n, R sign)
     }
 }
 
-// In-place radix-2 decimation-in-time FFT of the two n-point lines z[0..n) and z[n..2n)
-// (loaded in bit-reversed order) with the twiddles tw of twiddles(); unnormalised.
+// Shared-memory position of element i of a line: one spare slot after every eight elements, so
+// that the threads of a half-warp reading the sets of the first passes hit distinct banks.
+LB_HD int pz(int i) { return i + (i >> 3); }
+LB_HD int line_stride(int n) { return n + (n >> 3); }
+
+// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 of the two
+// n-point lines z[0 ..) and z[line_stride(n) ..) (bit-reversed input order): those stages
+// only combine elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads
+// whole sets, runs the RB stages in registers and stores them back (one shared-memory round
+// trip and one barrier for RB stages). tw from twiddles(); unnormalised.
+template <class R, int RB>
+LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s)
+{
+    constexpr int RR = 1 << RB;
+    const int h = 1 << s, sets = n >> RB, ls = line_stride(n);
+    for (int t = threadIdx.x; t < 2 * sets; t += blockDim.x) {
+        Cx<R>* line = z + (t >= sets ? ls : 0);
+        const int q = t >= sets ? t - sets : t;
+        const int j = q & (h - 1);
+        const int base = (q - j) * RR + j;  // (q / h) RR h + j
+        Cx<R> v[RR];
+#pragma unroll
+        for (int k = 0; k < RR; ++k) v[k] = line[pz(base + k * h)];
+#pragma unroll
+        for (int l = 0; l < RB; ++l) {  // stage s + l: half H = h 2^l, pairs (k, k + 2^l)
+#pragma unroll
+            for (int k = 0; k < RR; ++k) {
+                if (k & (1 << l)) continue;
+                const int m = j + (k & ((1 << l) - 1)) * h;  // position of the pair within its half
+                const Cx<R> w = tw[m << (logn - 1 - s - l)];   // exp(sign i pi m / H)
+                const Cx<R> p = v[k], qv = v[k | (1 << l)];
+                const R tr = w.re * qv.re - w.im * qv.im, ti = w.re * qv.im + w.im * qv.re;
+                v[k] = {p.re + tr, p.im + ti};
+                v[k | (1 << l)] = {p.re - tr, p.im - ti};
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RR; ++k) line[pz(base + k * h)] = v[k];
+    }
+    __syncthreads();
+}
+
+// FFT of the two lines (bit-reversed input order, loaded and synchronised by the caller):
+// passes of three stages, the last one of one or two.
 template <class R>
 LB_DEV void fft2_lines(Cx<R>* z, const Cx<R>* tw, int n, int logn)
 {
-    const int nb = n >> 1;  // butterflies per line and stage
-    for (int lh = 0; lh < logn; ++lh) {
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < 2 * nb; b += blockDim.x) {
-            Cx<R>* line = z + (b >= nb ? n : 0);
-            const int bb = b >= nb ? b - nb : b;
-            const int j = bb & (half - 1);
-            const int i0 = ((bb - j) << 1) + j, i1 = i0 + half;
-            const Cx<R> w = tw[j << (logn - 1 - lh)];  // exp(sign i pi j / half)
-            const R c = w.re, s = w.im;
-            const Cx<R> p = line[i0], q = line[i1];
-            const R tr = c * q.re - s * q.im, ti = c * q.im + s * q.re;
-            line[i0] = {p.re + tr, p.im + ti};
-            line[i1] = {p.re - tr, p.im - ti};
-        }
-        __syncthreads();
-    }
+    int s = 0;
+    for (; s + 3 <= logn; s += 3) fft_pass<R, 3>(z, tw, n, logn, s);
+    if (logn - s == 2) fft_pass<R, 2>(z, tw, n, logn, s);
+    else if (logn - s == 1) fft_pass<R, 1>(z, tw, n, logn, s);
 }
 
 // round(|k|) of the mode (kx, ky) (signed wavenumbers), in exact integer arithmetic: an FP32
@@ -81,14 +111,15 @@ LB_DEV int signed_k(int k, int n) { return k < n / 2 ? k : k - n; }
 
 // rows, forward: moments of every node of row y, DFT along x -> spec[a][y][kx]
 template <class T, int MODE>
-__global__ void __launch_bounds__(512) k_sc_rows_fwd(const T* buf, Geom g, int logn,
+__global__ void __launch_bounds__(256) k_sc_rows_fwd(const T* buf, Geom g, int logn,
                                                      Cx<typename Store<T>::Real>* spec)
 {
     using R = typename Store<T>::Real;
     extern __shared__ __align__(16) unsigned char sc_smem[];
     const int n = g.nx, y = blockIdx.x;
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tw = z + 2 * n;
+    const int ls = line_stride(n);
+    Cx<R>* tw = z + 2 * ls;
     twiddles(tw, n, R(-1));
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
         Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
@@ -96,14 +127,14 @@ __global__ void __launch_bounds__(512) k_sc_rows_fwd(const T* buf, Geom g, int l
         load_node<D2Q9, MODE>(buf, g, nb, x + n * y, f);
         const NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
         const int r = bitrev(x, logn);
-        z[r] = {m.ux, R(0)};
-        z[n + r] = {m.uy, R(0)};
+        z[pz(r)] = {m.ux, R(0)};
+        z[ls + pz(r)] = {m.uy, R(0)};
     }
     __syncthreads();
     fft2_lines(z, tw, n, logn);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        spec[(int64_t)y * n + k] = z[k];
-        spec[((int64_t)n + y) * n + k] = z[n + k];
+        spec[(int64_t)y * n + k] = z[pz(k)];
+        spec[((int64_t)n + y) * n + k] = z[ls + pz(k)];
     }
 }
 
@@ -123,24 +154,25 @@ LB_DEV int first_m(int kxs, int s, int n)
 // partials[s][kx] (the modes of shell s in this column are one run of |ky|; summed in order
 // of |ky|, +ky before -ky)
 template <class R>
-__global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, double* partials)
+__global__ void __launch_bounds__(256) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, double* partials)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tw = z + 2 * n;
+    const int ls = line_stride(n);
+    Cx<R>* tw = z + 2 * ls;
     double* e = reinterpret_cast<double*>(tw + n / 2);
     const int kx = blockIdx.x, K = n / 2;
     twiddles(tw, n, R(-1));
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
         const int r = bitrev(y, logn);
-        z[r] = spec[(int64_t)y * n + kx];
-        z[n + r] = spec[((int64_t)n + y) * n + kx];
+        z[pz(r)] = spec[(int64_t)y * n + kx];
+        z[ls + pz(r)] = spec[((int64_t)n + y) * n + kx];
     }
     __syncthreads();
     fft2_lines(z, tw, n, logn);
     const double inv_n4 = 1.0 / ((double)n * n * (double)n * n);
     for (int ky = threadIdx.x; ky < n; ky += blockDim.x) {
-        const Cx<R> a = z[ky], b = z[n + ky];
+        const Cx<R> a = z[pz(ky)], b = z[ls + pz(ky)];
         spec[(int64_t)ky * n + kx] = a;
         spec[((int64_t)n + ky) * n + kx] = b;
         e[ky] = 0.5 * ((double)a.re * a.re + (double)a.im * a.im + (double)b.re * b.re + (double)b.im * b.im) * inv_n4;
@@ -159,15 +191,26 @@ __global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int log
 }
 
 // shells: sigma_s = sum over the columns (one warp per shell: lane l takes kx = l, l + 32, ...
-// in order, then a fixed shuffle tree), dR/dsigma_s and the shell's term of R
+// into four running sums in a fixed order, then a fixed shuffle tree), dR/dsigma_s and the
+// shell's term of R
 __global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, const double* sigma0, double c,
                                                    double* sigma, double* grad, double* r2)
 {
     const int K = n / 2, lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= K) return;
-    double acc = 0.0;
-    for (int kx = lane; kx < n; kx += 32) acc += partials[(int64_t)s * n + kx];
+    // four independent running sums per lane keep four loads in flight
+    const double* p = partials + (int64_t)s * n;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int kx = lane;
+    for (; kx + 96 < n; kx += 128) {
+        a0 += p[kx];
+        a1 += p[kx + 32];
+        a2 += p[kx + 64];
+        a3 += p[kx + 96];
+    }
+    for (; kx < n; kx += 32) a0 += p[kx];
+    double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane != 0) return;
@@ -192,11 +235,12 @@ __global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double*
 
 // columns, inverse: multiply by G(k), inverse DFT along y
 template <class R>
-__global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const double* grad)
+__global__ void __launch_bounds__(256) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const double* grad)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tw = z + 2 * n;
+    const int ls = line_stride(n);
+    Cx<R>* tw = z + 2 * ls;
     const int kx = blockIdx.x, K = n / 2, kxs = signed_k(kx, n);
     twiddles(tw, n, R(1));
     for (int ky = threadIdx.x; ky < n; ky += blockDim.x) {
@@ -204,37 +248,38 @@ __global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int log
         const R G = sh < K ? (R)grad[sh] : R(0);
         const int r = bitrev(ky, logn);
         const Cx<R> a = spec[(int64_t)ky * n + kx], b = spec[((int64_t)n + ky) * n + kx];
-        z[r] = {G * a.re, G * a.im};
-        z[n + r] = {G * b.re, G * b.im};
+        z[pz(r)] = {G * a.re, G * a.im};
+        z[ls + pz(r)] = {G * b.re, G * b.im};
     }
     __syncthreads();
     fft2_lines(z, tw, n, logn);
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
-        spec[(int64_t)y * n + kx] = z[y];
-        spec[((int64_t)n + y) * n + kx] = z[n + y];
+        spec[(int64_t)y * n + kx] = z[pz(y)];
+        spec[((int64_t)n + y) * n + kx] = z[ls + pz(y)];
     }
 }
 
 // rows, inverse: inverse DFT along x, du_a = scale Re(.), scale = -kappa / N^2
 template <class R>
-__global__ void __launch_bounds__(512) k_sc_rows_inv(const Cx<R>* spec, int n, int logn, R scale, R* du,
+__global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, int logn, R scale, R* du,
                                                      int64_t plane)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tw = z + 2 * n;
+    const int ls = line_stride(n);
+    Cx<R>* tw = z + 2 * ls;
     const int y = blockIdx.x;
     twiddles(tw, n, R(1));
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int r = bitrev(k, logn);
-        z[r] = spec[(int64_t)y * n + k];
-        z[n + r] = spec[((int64_t)n + y) * n + k];
+        z[pz(r)] = spec[(int64_t)y * n + k];
+        z[ls + pz(r)] = spec[((int64_t)n + y) * n + k];
     }
     __syncthreads();
     fft2_lines(z, tw, n, logn);
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        du[(int64_t)y * n + x] = scale * z[x].re;
-        du[plane + (int64_t)y * n + x] = scale * z[n + x].re;
+        du[(int64_t)y * n + x] = scale * z[pz(x)].re;
+        du[plane + (int64_t)y * n + x] = scale * z[ls + pz(x)].re;
     }
 }
 
@@ -278,7 +323,7 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches)
     const OpArgs& a = s.a;
     const int n = s.n, logn = s.logn, th = line_threads(n), K = n / 2;
     Cx<R>* spec = (Cx<R>*)s.spec;
-    const size_t lines = (2 * (size_t)n + (size_t)K) * sizeof(Cx<R>);  // two lines + twiddles
+    const size_t lines = (2 * (size_t)line_stride(n) + (size_t)K) * sizeof(Cx<R>);  // two lines + twiddles
     cudaError_t e;
     const T* buf = (const T*)a.src;
     if (a.mode == AB) {
