@@ -234,7 +234,7 @@ LB_API int64_t lb_steps_taken(const lb_ctx* ctx);
 
 /* Turn the control on (sigma0[K] in host memory, K = n/2 shells, copied; cutoff c > 0,
  * kappa >= 0) or off (sigma0 NULL). From the next lb_step every step computes du from the
- * current state and collides at u + du (seven kernel launches per step instead of one).
+ * current state and collides at u + du (five kernel launches per step instead of one).
  * Needs the BGK collision, no force, no walls and record_every = 0 (LB_ERR_UNSUPPORTED
  * otherwise); LB_ERR_ARG for another K or non-finite values. */
 LB_API lb_status lb_set_spectral_control(lb_ctx* ctx, const double* sigma0, int64_t K, double cutoff,

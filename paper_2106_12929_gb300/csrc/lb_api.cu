@@ -204,11 +204,10 @@ lb_status launch(lb_ctx* c, const lb::OpArgs& a, const char* what)
 {
     cudaError_t e;
     if (c->sc_on && a.op == lb::OP_UPDATE) {
-        // spectral flow control: du from the state, then the step at u + du
+        // spectral flow control: du from the state and the step at u + du
         int n = 0;
-        e = lb::spectral_shift(spectral_args(c, a), &n);
-        if (e == cudaSuccess) e = lb::spectral_update(a, c->sc_du);
-        c->launches += n + 1;
+        e = lb::spectral_step(spectral_args(c, a), &n);
+        c->launches += n;
         if (e != cudaSuccess) return cuda_fail(c, e, what);
         return LB_OK;
     }

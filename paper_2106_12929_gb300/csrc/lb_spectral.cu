@@ -9,10 +9,11 @@
 //   grad_u_a R(x) = Re sum_k G(k) U_a(k) exp(+2 pi i k.x / n) / N^2,
 //   G(k) = dR/dsigma_s of k's shell s (0 outside the kept shells),
 //   dR/dsigma_s = 2 (ln sigma_s - ln max(sigma0_s, c)) / sigma_s if sigma_s > c, else 0.
-// Six launches compute du from the state: rows (moments + forward DFT along x), columns
-// (forward DFT along y, modal energies and per-column shell sums), shells (sigma and
-// dR/dsigma, one warp per shell), cost (R), columns (filter by G, inverse DFT along y), rows
-// (inverse DFT along x, du). Each DFT is an in-place radix-2 FFT of one grid line in shared
+// A controlled step is five launches: rows (moments + forward DFT along x), columns (forward
+// DFT along y, modal energies and per-column shell sums), shells (sigma and dR/dsigma, one
+// warp per shell), columns (filter by G, inverse DFT along y; the cost R), rows (inverse DFT
+// along x: du, then the shifted BGK step of the row's nodes). lb_spectral_shift writes du
+// instead of stepping. Each DFT is an in-place radix-2 FFT of one grid line in shared
 // memory, one block per line, in passes of three radix-2 stages held in registers (a padded
 // layout keeps the passes free of bank conflicts), with a per-block twiddle table; both velocity
 // components go through the same passes. Every sum runs in a fixed order (deterministic).
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n
     }
 }
 
-// cost R = sum_s r2[s] (one warp, fixed order)
-__global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost)
+// R = sum_s r2[s] by one warp in a fixed order
+LB_DEV void sum_cost(const double* r2, int K, double* cost)
 {
     double acc = 0.0;
     for (int s = threadIdx.x; s < K; s += 32) acc += r2[s];
@@ -233,10 +234,16 @@ __global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double*
     if (threadIdx.x == 0) cost[0] = acc;
 }
 
-// columns, inverse: multiply by G(k), inverse DFT along y
+// cost R = sum_s r2[s] (one warp, fixed order)
+__global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost) { sum_cost(r2, K, cost); }
+
+// columns, inverse: multiply by G(k), inverse DFT along y; block 0's first warp also totals
+// the cost R (cost non-null)
 template <class R>
-__global__ void __launch_bounds__(256) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const double* grad)
+__global__ void __launch_bounds__(256) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const double* grad,
+                                                     const double* r2, double* cost)
 {
+    if (cost && blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
     const int ls = line_stride(n);
@@ -283,28 +290,54 @@ __global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, i
     }
 }
 
-// one BGK step with the equilibrium at u + du
+// one BGK step of node (x, y) with the equilibrium at u + du
 template <class T, int MODE>
-__global__ void __launch_bounds__(128) k_update_ushift(const T* src, T* dst, Geom g, typename Store<T>::Real omega,
-                                                       const typename Store<T>::Real* du, unsigned* status)
+LB_DEV void shifted_bgk_node(const T* src, T* dst, const Geom& g, typename Store<T>::Real omega, int x, int y,
+                             typename Store<T>::Real dux, typename Store<T>::Real duy, unsigned* status)
 {
     using R = typename Store<T>::Real;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= g.nx) return;
-    const int y = blockIdx.y;
     Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
     const int n = x + g.nx * y;
     R f[9], feq[9], Fz[3] = {R(0), R(0), R(0)};
     load_node<D2Q9, MODE>(src, g, nb, n, f);
     NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
     const R rho = m.rho;
-    m.ux += du[n];
-    m.uy += du[g.plane + n];
+    m.ux += dux;
+    m.uy += duy;
     equilibrium<D2Q9>(m, feq);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(rho > R(0) && rho < R(1e30))) atomicOr(status, 1u);
+}
+
+// rows, inverse, fused with the step: the inverse DFT of row y gives du of the row in shared
+// memory, and the block then steps the row's nodes (the step reads only the pre-step state,
+// which no kernel of this step writes; every node is stepped by exactly one thread, as in the
+// one-kernel AA update)
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) k_sc_rows_inv_step(const Cx<typename Store<T>::Real>* spec, int logn,
+                                                          typename Store<T>::Real scale, const T* src, T* dst,
+                                                          Geom g, typename Store<T>::Real omega, unsigned* status)
+{
+    using R = typename Store<T>::Real;
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
+    const int n = g.nx, ls = line_stride(n);
+    Cx<R>* tw = z + 2 * ls;
+    const int y = blockIdx.x;
+    twiddles(tw, n, R(1));
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int r = bitrev(k, logn);
+        z[pz(r)] = spec[(int64_t)y * n + k];
+        z[ls + pz(r)] = spec[((int64_t)n + y) * n + k];
+    }
+    __syncthreads();
+    fft2_lines(z, tw, n, logn);
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const R dux = scale * z[pz(x)].re, duy = scale * z[ls + pz(x)].re;
+        shifted_bgk_node<T, MODE>(src, dst, g, omega, x, y, dux, duy, status);
+    }
 }
 
 static int line_threads(int n) { return n < 256 ? n : 256; }
@@ -316,8 +349,9 @@ static cudaError_t smem_attr(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// step = true: the controlled step itself (a.dst, a.status, a.omega of s.a), du stays on chip
 template <class T>
-static cudaError_t shift_typed(const SpectralArgs& s, int* launches)
+static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
 {
     using R = typename Store<T>::Real;
     const OpArgs& a = s.a;
@@ -342,56 +376,55 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches)
     k_sc_shells<<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, s.sigma0, s.cutoff, s.sigma, s.grad, s.r2);
     *launches += 3;
     if (!s.sigma0) return cudaGetLastError();
-    k_sc_cost<<<1, 32, 0, a.stream>>>(s.r2, K, s.cost);
-    *launches += 1;
-    if (!s.du) return cudaGetLastError();
+    if (!s.du && !step) {
+        k_sc_cost<<<1, 32, 0, a.stream>>>(s.r2, K, s.cost);
+        *launches += 1;
+        return cudaGetLastError();
+    }
     if ((e = smem_attr(k_sc_cols_inv<R>, lines)) != cudaSuccess) return e;
-    k_sc_cols_inv<R><<<n, th, lines, a.stream>>>(spec, n, logn, s.grad);
-    if ((e = smem_attr(k_sc_rows_inv<R>, lines)) != cudaSuccess) return e;
+    k_sc_cols_inv<R><<<n, th, lines, a.stream>>>(spec, n, logn, s.grad, s.r2, s.cost);
     const R scale = (R)(-s.kappa / ((double)n * n * (double)n * n));
+    if (step) {  // inverse rows fused with the step
+        const T* src = (const T*)a.src;
+        T* dst = (T*)a.dst;
+        const R om = (R)a.omega;
+        if (a.mode == AB) {
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AB>, lines)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AB><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om, a.status);
+        } else if (a.mode == AA_EVEN) {
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_EVEN>, lines)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AA_EVEN><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om,
+                                                                       a.status);
+        } else {
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_ODD>, lines)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AA_ODD><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om,
+                                                                      a.status);
+        }
+        *launches += 2;
+        return cudaGetLastError();
+    }
+    if ((e = smem_attr(k_sc_rows_inv<R>, lines)) != cudaSuccess) return e;
     k_sc_rows_inv<R><<<n, th, lines, a.stream>>>(spec, n, logn, scale, (R*)s.du, a.g.plane);
     *launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t spectral_shift(const SpectralArgs& s, int* launches)
+static cudaError_t shift_or_step(const SpectralArgs& s, int* launches, bool step)
 {
     if (s.a.g.nx != s.n || s.a.g.ny != s.n || s.a.g.nz != 1 || s.n < 4 || s.n > kSpecMaxN || (1 << s.logn) != s.n)
         return cudaErrorInvalidValue;
+    if (step && !s.sigma0) return cudaErrorInvalidValue;
     switch (s.a.storage) {
-    case S_F64: return shift_typed<double>(s, launches);
-    case S_F32: return shift_typed<float>(s, launches);
-    case S_F16: return shift_typed<__half>(s, launches);
-    case S_BF16: return shift_typed<__nv_bfloat16>(s, launches);
+    case S_F64: return shift_typed<double>(s, launches, step);
+    case S_F32: return shift_typed<float>(s, launches, step);
+    case S_F16: return shift_typed<__half>(s, launches, step);
+    case S_BF16: return shift_typed<__nv_bfloat16>(s, launches, step);
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <class T>
-static cudaError_t update_typed(const OpArgs& a, const void* du)
-{
-    using R = typename Store<T>::Real;
-    const dim3 bl(128, 1, 1), gr((a.g.nx + 127) / 128, a.g.ny, 1);
-    const T* src = (const T*)a.src;
-    T* dst = (T*)a.dst;
-    const R* d = (const R*)du;
-    if (a.mode == AB) k_update_ushift<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, d, a.status);
-    else if (a.mode == AA_EVEN)
-        k_update_ushift<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, d, a.status);
-    else k_update_ushift<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, d, a.status);
-    return cudaGetLastError();
-}
+cudaError_t spectral_shift(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, false); }
 
-cudaError_t spectral_update(const OpArgs& a, const void* du)
-{
-    if (a.g.nz != 1 || !du) return cudaErrorInvalidValue;
-    switch (a.storage) {
-    case S_F64: return update_typed<double>(a, du);
-    case S_F32: return update_typed<float>(a, du);
-    case S_F16: return update_typed<__half>(a, du);
-    case S_BF16: return update_typed<__nv_bfloat16>(a, du);
-    default: return cudaErrorInvalidValue;
-    }
-}
+cudaError_t spectral_step(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, true); }
 
 }  // namespace lb

@@ -26,7 +26,8 @@ constexpr int kSpecMaxN = 4096;
 // Spectrum sigma of the state a.src; with sigma0 also the cost R and dR/dsigma; with du
 // also the velocity shift du = -kappa grad_u R. Adds the number of launches to *launches.
 cudaError_t spectral_shift(const SpectralArgs& s, int* launches);
-// One BGK step whose equilibrium is taken at u + du (du [2][plane], arithmetic type).
-cudaError_t spectral_update(const OpArgs& a, const void* du);
+// One controlled step from the state s.a.src into s.a.dst (s.a's mode, omega and status):
+// spectrum, cost and dR/dsigma as above, then BGK at u + du with du kept on chip (s.du unused).
+cudaError_t spectral_step(const SpectralArgs& s, int* launches);
 
 }  // namespace lb
