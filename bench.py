@@ -368,6 +368,14 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
         r = learned_throughput(stream, n=2048, steps=100, tc=tc, net=net)
         out[f"{key}_forward_glups"] = r["forward_glups"]
         out[f"{key}_backward_ms_per_step"] = r["backward_ms_per_step"]
+    # FP32 FMA peak of this GPU for the ALU-bound learned forward kernels: cuBLAS SGEMM with
+    # TF32 off (plain FP32 FMAs), 8192^3, best of 5
+    peak = fp32_fma_peak(stream)
+    out["fp32_sgemm_tflops"] = round(peak, 2)
+    for key in ("learned_f32", "learned3_f32"):
+        net = key.split("_")[0]
+        out[f"{key}_forward_frac_of_fp32_peak"] = round(
+            out[f"{key}_forward_glups"] * LEARNED_FLOP_PER_LU[net] / 1e3 / peak, 3)
     for n in (128, 1024):
         r = spectral_control(stream, n=n, steps=200)
         out[f"spectral_{n}_controlled_us_per_step"] = r["controlled_us_per_step"]
@@ -456,6 +464,28 @@ def learned_throughput(stream, n=2048, steps=200, tc=False, net="learned"):
             "forward_tflops": round(fwd * LEARNED_FLOP_PER_LU[net] / 1e3, 2),
             "backward_ms_per_step": round(bwd / k * 1e3, 4),
             "forward_ms_per_step": round(n * n / fwd / 1e9 * 1e3, 4)}
+
+
+def fp32_fma_peak(stream, n=8192, reps=5):
+    """Measured FP32 FMA throughput (TFLOP/s): cuBLAS SGEMM with TF32 disabled, best of reps."""
+    import torch
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        torch.mm(a, b)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.mm(a, b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
 
 
 def spectral_control(stream, n=128, steps=200, storage="f32", kappa=5e-4):
