@@ -143,21 +143,32 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
             // (axis velocities: Mdev_aa / 2, edge velocities: c_a c_b M_ab / 4, rest and
             // corners: 0), Dh the rest. f* = f - beta (2 Ds + gamma Dh), beta = omega/2,
             // gamma = 1/beta - (2 - 1/beta) <Ds|Dh> / (<Dh|Dh> + 1e-6 <Ds|Ds>) with
-            // <X|Y> = sum X_i Y_i / f^eq_i.
+            // <X|Y> = sum X_i Y_i / f^eq_i. Opposite velocities i, i + 1 share the even parts
+            // (f^eq = w (a +- b), the second moments take pair sums, Ds is even in c), so the
+            // work runs once per pair.
             static_assert(St::Q == 9 || St::Q == 27, "KBC needs D2Q9 or D3Q27");
-            equilibrium<St>(m, feq);
+            const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+            const R a0 = m.rho1 - m.rho * uu15, rho45 = R(4.5) * m.rho, rho3 = R(3) * m.rho;
             R D[St::Q];
+            feq[0] = R(St::w(0)) * a0;
+            D[0] = f[0] - feq[0];
             R mxx = R(0), myy = R(0), mzz = R(0), mxy = R(0), mxz = R(0), myz = R(0);
 #pragma unroll
-            for (int i = 0; i < St::Q; ++i) {
+            for (int i = 1; i < St::Q; i += 2) {  // opp(i) = i + 1
+                const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
+                const R a = a0 + rho45 * cu * cu, b = rho3 * cu;
+                feq[i] = R(St::w(i)) * (a + b);
+                feq[i + 1] = R(St::w(i)) * (a - b);
                 D[i] = f[i] - feq[i];
+                D[i + 1] = f[i + 1] - feq[i + 1];
+                const R sp = D[i] + D[i + 1];
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
-                if (cx) mxx += D[i];
-                if (cy) myy += D[i];
-                if (St::D == 3 && cz) mzz += D[i];
-                if (cx && cy) mxy += (cx == cy) ? D[i] : -D[i];
-                if (St::D == 3 && cx && cz) mxz += (cx == cz) ? D[i] : -D[i];
-                if (St::D == 3 && cy && cz) myz += (cy == cz) ? D[i] : -D[i];
+                if (cx) mxx += sp;
+                if (cy) myy += sp;
+                if (St::D == 3 && cz) mzz += sp;
+                if (cx && cy) mxy += (cx == cy) ? sp : -sp;
+                if (St::D == 3 && cx && cz) mxz += (cx == cz) ? sp : -sp;
+                if (St::D == 3 && cy && cz) myz += (cy == cz) ? sp : -sp;
             }
             const R third = R(1) / R(St::D);
             const R tr = (mxx + myy + mzz) * third;
@@ -165,39 +176,34 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
             // entropic weights 1/f^eq_i = 1/(w_i rho P_i), P_i = 1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u.
             // An opposite pair has P = A +- B (A = 1 + 4.5 (c.u)^2 - 1.5 u.u, B = 3 c.u), so one
             // reciprocal 1/(A^2 - B^2) serves both: 1/P_i = (A - B)/(A^2 - B^2), 1/P_opp = (A + B)/(...).
-            const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
             const R irho = recip_fast(m.rho);
-            R ie[St::Q];
-            ie[0] = irho * R(1.0 / St::w(0)) * recip_fast(R(1) - uu15);
+            const R ie0 = irho * R(1.0 / St::w(0)) * recip_fast(R(1) - uu15);
+            R sh = R(0), hh = ie0 * D[0] * D[0], ss = R(0);
+            R Ds[St::Q];
+            Ds[0] = R(0);
 #pragma unroll
             for (int i = 1; i < St::Q; i += 2) {
                 const R cu = cdotu<St>(i, m.ux, m.uy, m.uz);
                 const R A = R(1) - uu15 + R(4.5) * cu * cu, B = R(3) * cu;
                 const R r = irho * R(1.0 / St::w(i)) * recip_fast(A * A - B * B);  // w_i = w_opp(i)
-                ie[i] = (A - B) * r;
-                ie[i + 1] = (A + B) * r;
-            }
-            R Ds[St::Q];
-            R sh = R(0), hh = R(0), ss = R(0);
-#pragma unroll
-            for (int i = 0; i < St::Q; ++i) {
+                const R iei = (A - B) * r, iej = (A + B) * r;
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
                 const int nz = (cx != 0) + (cy != 0) + (cz != 0);
                 if (nz == 1 || nz == 2) {
-                    R s;
-                    if (nz == 1) s = cx ? dxx : (cy ? dyy : dzz);
-                    else if (cx && cy) s = (cx == cy) ? R(0.25) * mxy : R(-0.25) * mxy;
-                    else if (cx && cz) s = (cx == cz) ? R(0.25) * mxz : R(-0.25) * mxz;
-                    else s = (cy == cz) ? R(0.25) * myz : R(-0.25) * myz;
-                    Ds[i] = s;
-                    const R h = D[i] - s;
-                    const R si = s * ie[i];
-                    sh += si * h;
-                    ss += si * s;
-                    hh += h * h * ie[i];
+                    R sv;
+                    if (nz == 1) sv = cx ? dxx : (cy ? dyy : dzz);
+                    else if (cx && cy) sv = (cx == cy) ? R(0.25) * mxy : R(-0.25) * mxy;
+                    else if (cx && cz) sv = (cx == cz) ? R(0.25) * mxz : R(-0.25) * mxz;
+                    else sv = (cy == cz) ? R(0.25) * myz : R(-0.25) * myz;
+                    Ds[i] = Ds[i + 1] = sv;
+                    const R hi = D[i] - sv, hj = D[i + 1] - sv;
+                    const R wi = iei * hi, wj = iej * hj;
+                    sh += sv * (wi + wj);
+                    ss += sv * sv * (iei + iej);
+                    hh += wi * hi + wj * hj;
                 } else {
-                    Ds[i] = R(0);
-                    hh += D[i] * D[i] * ie[i];
+                    Ds[i] = Ds[i + 1] = R(0);
+                    hh += iei * D[i] * D[i] + iej * D[i + 1] * D[i + 1];
                 }
             }
             const R beta = R(0.5) * omega, ib = rx.p[0];  // p[0] = 1/beta = 2 tau
@@ -205,11 +211,7 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
             const R gamma = den > R(0) ? ib - (R(2) - ib) * sh * recip(den) : R(2);
             const R bg = beta * gamma, b2 = R(2) * beta;
 #pragma unroll
-            for (int i = 0; i < St::Q; ++i) {
-                const int nz = (St::c(i, 0) != 0) + (St::c(i, 1) != 0) + (St::c(i, 2) != 0);
-                if (nz == 1 || nz == 2) f[i] = f[i] - (b2 * Ds[i] + bg * (D[i] - Ds[i]));
-                else f[i] = f[i] - bg * D[i];
-            }
+            for (int i = 0; i < St::Q; ++i) f[i] = f[i] - (b2 * Ds[i] + bg * (D[i] - Ds[i]));
         } else if constexpr (COLL == MRT) {
             // D2Q9 Hermite moments of D = f - f^eq: stress (order 2) relaxed by omega, the
             // three higher moments (cx^2 - 1/3) cy, cx (cy^2 - 1/3), (cx^2 - 1/3)(cy^2 - 1/3)
