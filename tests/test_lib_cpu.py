@@ -89,6 +89,11 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lb_step(None, 1) == 1
     assert lib.lb_check(None) == 1
     assert lib.lb_num_nodes(None) == -1
+    sig = (ctypes.c_double * 4)()
+    assert lib.lb_set_spectral_control(None, sig, 4, 2e-5, 5e-5) == 1
+    assert lib.lb_spectrum(None, sig, None) == 1
+    assert lib.lb_spectral_shift(None, None, 0) == 1
+    assert lib.lb_set_mlp(None, None, 545, 0) == 1
     lib.lb_destroy(None)
 
 
