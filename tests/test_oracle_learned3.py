@@ -55,3 +55,30 @@ def test_conserves_mass_and_momentum():
     out = oracle.collide_node("D2Q9", 0.55, "learned3", f, mlp=_net(0.0, out_scale=0.7, seed=4))
     assert abs(out.sum() - f.sum()) < 1e-15
     np.testing.assert_allclose(c.T @ out, c.T @ f, atol=1e-16)
+
+
+def _rotation_perm():
+    d, c, w, _ = oracle.stencil("D2Q9")
+    # rotation by 90 degrees: (cx, cy) -> (-cy, cx); perm[i] = index of R c_i
+    rc = np.stack([-c[:, 1], c[:, 0], c[:, 2]], 1)
+    return np.array([np.where((c == v).all(1))[0][0] for v in rc])
+
+
+def test_rotation_equivariance_needs_equal_third_order_times():
+    """A 90-degree rotation maps the third-order moments J0, J1 onto each other (and keeps the
+    network inputs, which are invariants), so the collision commutes with it exactly when
+    the J0 and J1 outputs agree; with different times it does not. The shared-rate network
+    is always equivariant (test_oracle_pins.py)."""
+    perm = _rotation_perm()
+    tau = 0.6
+    f = _node(14, eps=0.3)
+    fr = np.empty_like(f)
+    fr[perm] = f  # population of direction i moves to direction R c_i
+    same = _net(np.log(np.array([1.3, 0.8, 0.8]) - 0.5))
+    a = oracle.collide_node("D2Q9", tau, "learned3", f, mlp=same)
+    b = oracle.collide_node("D2Q9", tau, "learned3", fr, mlp=same)
+    np.testing.assert_allclose(b[perm], a, atol=2e-16)
+    differ = _net(np.log(np.array([1.3, 0.8, 2.1]) - 0.5))
+    a = oracle.collide_node("D2Q9", tau, "learned3", f, mlp=differ)
+    b = oracle.collide_node("D2Q9", tau, "learned3", fr, mlp=differ)
+    assert np.max(np.abs(b[perm] - a)) > 1e-6
