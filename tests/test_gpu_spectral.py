@@ -49,7 +49,7 @@ def flow(n, seed=2000, k0=None, u0=0.1 / math.sqrt(3.0), re=2000.0):
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-6)])
-@pytest.mark.parametrize("n", [4, 16, 128])
+@pytest.mark.parametrize("n", [4, 16, 128, 2048, 4096])
 def test_spectrum_and_cost_match_oracle(storage, tol, n):
     dims, tau, rho, u = flow(n, k0=max(1.0, n / 16.0))
     f0 = oracle.init_eq(NAME, dims, rho, u)
