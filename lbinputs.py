@@ -110,7 +110,8 @@ def random_spectrum_velocity(dims, k0: float, u_rms: float, seed: int):
     Each integer wavevector kappa gets amplitude sqrt(E(|kappa|) / shell count)
     and a uniform random phase (numpy PCG64 from ``seed``); the field is projected
     onto its divergence-free part, transformed back to real space and scaled so
-    that the per-component rms equals u_rms. rho = 1.
+    that the rms of a component, averaged over the components (sqrt(mean |u|^2 / d)),
+    equals u_rms. rho = 1.
     """
     nx, ny, nz = (int(d) for d in dims)
     d = 2 if nz == 1 else 3

@@ -1,0 +1,80 @@
+"""Host-side logic that needs no GPU: the training driver's scale conventions and spectrum
+diagnostic, the workload generators' closed forms, and the benchmark's bookkeeping."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import lbinputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_coarse_relaxation_time_keeps_the_viscosity_in_acoustic_scaling():
+    from paper_2106_12929_gb300 import training
+    # nu_c dt_c / dx_c^2 = nu_f dt_f / dx_f^2 with dx_c = 2 dx_f, dt_c = 2 dt_f: nu_lu halves
+    for tau_f in (0.503, 0.51, 0.8):
+        tau_c = training.coarse_tau(tau_f)
+        assert (tau_c - 0.5) == pytest.approx((tau_f - 0.5) / 2.0, rel=1e-15)
+
+
+def test_training_spectrum_of_single_modes():
+    from paper_2106_12929_gb300 import training
+    n = 32
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    A, B = 0.02, 0.03
+    u = np.zeros((2, n * n))
+    u[0] = (A * np.cos(2 * np.pi * (3 * x + 4 * y) / n)).ravel()  # |k| = 5
+    u[1] = (B * np.sin(2 * np.pi * 7 * y / n)).ravel()            # |k| = 7
+    e = training.spectrum_2d(u, n)
+    expect = np.zeros(n // 2)
+    expect[5] = A * A / 4
+    expect[7] = B * B / 4
+    np.testing.assert_allclose(e, expect, rtol=0, atol=1e-18)
+
+
+def test_init_theta_is_exactly_bgk_for_both_networks():
+    pytest.importorskip("torch")
+    from paper_2106_12929_gb300 import _lib
+    for net, gen in (("learned", lbinputs.random_mlp_params), ("learned3", lbinputs.random_mlp3_params)):
+        th = gen(5, out_bias=math.log(0.01), out_scale=0.0)
+        assert th.size == _lib.n_theta(net)
+        # output weights are zero, so the output is the bias ln(tau_c - 1/2) for every input
+        n_out = 1 if net == "learned" else 3
+        n_w = 24 if net == "learned" else 3 * 53
+        w_out = th[-(n_w + n_out):-n_out]
+        assert np.all(w_out == 0.0)
+        assert np.all(th[-n_out:] == math.log(0.01))
+
+
+def test_relaxation_time_from_reynolds_number():
+    # nu = u0 (n / 2 pi) / Re, tau = 3 nu + 1/2 (c_s^2 = 1/3)
+    u0, n, re = 0.1 / math.sqrt(3.0), 256, 1600.0
+    tau = lbinputs.tau_from_reynolds(re, u0, n)
+    assert tau == pytest.approx(0.5 + 3.0 * u0 * n / (2 * math.pi) / re, rel=1e-14)
+    assert tau == pytest.approx(0.504411, abs=1e-6)  # the 256^3 benchmark's value
+
+
+def test_random_spectrum_velocity_is_solenoidal_with_the_requested_rms():
+    dims = (32, 32, 1)
+    rho, u = lbinputs.random_spectrum_velocity(dims, 4.0, 0.05, 7)
+    assert np.all(rho == 1.0)
+    ux, uy = (c.reshape(32, 32) for c in u)
+    k = np.fft.fftfreq(32, 1.0 / 32)
+    div = 1j * k[None, :] * np.fft.fft2(ux) + 1j * k[:, None] * np.fft.fft2(uy)
+    inner = (np.abs(k) < 16)[:, None] & (np.abs(k) < 16)[None, :]  # the Nyquist lines have no sign
+    assert np.max(np.abs(div[inner])) <= 1e-12 * np.max(np.abs(np.fft.fft2(ux)))
+    # the rms per component, averaged over the components, is u_rms
+    assert np.sqrt(0.5 * (np.mean(ux ** 2) + np.mean(uy ** 2))) == pytest.approx(0.05, rel=1e-12)
+
+
+def test_job_throughput_of_a_single_replica():
+    sys.path.insert(0, ROOT)
+    import bench
+    lups, t = bench.job_throughput(1000, 10, 2.0, world=1)
+    assert t == 2.0 and lups == pytest.approx(5000.0)
+    assert bench.BYTES_PER_LU[("D3Q19", "f32")] == 152
+    assert bench.BYTES_PER_LU[("D3Q27", "f16")] == 108
+    assert bench.LEARNED_FLOP_PER_LU["learned3"] == 2 * (6 * 53 + 53 * 3) + 200
