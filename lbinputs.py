@@ -12,7 +12,7 @@ Workloads (the paper runs analytic or seeded flows only; Sec. 2.2, 3.1, 3.3):
   * 3D Taylor-Green vortex in Brachet's form (Sec. 2.2 code example, Fig. 2);
   * doubly periodic shear layer (Sec. 3.1 training flow);
   * random-phase decaying isotropic turbulence with E(k) ~ k^4 exp(-2 (k/k0)^2)
-    (Sec. 3.1 transfer flow);
+    (Sec. 3.1 transfer flow, Sec. 3.2 flow-control flow);
   * a smooth seeded body-force field and near-equilibrium random populations;
   * solid masks for walls: a seeded random obstacle field and a duct with a cylinder or
     sphere.
