@@ -81,6 +81,30 @@ def test_trt_even_moments_relax_with_tau_odd_with_tau_minus(name):
     assert abs(odd @ (f - feq)) > 1e-6  # the check is not vacuous
 
 
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q27"])
+def test_trt_forced_source_splits_by_parity(name):
+    # With a body force the source's second moment (1 - 1/(2 tau))(u F + F u) is even and its
+    # third moment sum c_x^2 c_y S = (1 - 1/(2 tau_minus)) c_s^4 3 F_y is odd (the Guo source's
+    # moments, split into the halves of each opposite pair); u is the half-force velocity
+    d, c, w, _ = oracle.stencil(name)
+    f = _node(name, 25)
+    F = np.array([1.5e-3, -2.5e-3, 1e-3])[:d]
+    tau, lam = 0.62, 0.1
+    tau_m = 0.5 + lam / (tau - 0.5)
+    out = oracle.collide_node(name, tau, "trt", f, F=F, params=[lam])
+    feq = _feq_of(name, f, F)
+    cf = c[:, :d].astype(float)
+    u = (cf.T @ f + 0.5 * F) / f.sum()
+    for a, b in [(0, 0), (0, 1), (1, 1)]:
+        even = cf[:, a] * cf[:, b]
+        src = (1 - 0.5 / tau) * (u[a] * F[b] + u[b] * F[a])
+        assert abs(even @ (out - feq) - (1 - 1 / tau) * (even @ (f - feq)) - src) < 1e-15
+    odd = cf[:, 0] ** 2 * cf[:, 1]
+    src = (1 - 0.5 / tau_m) * 3.0 * CS2 * CS2 * F[1]
+    assert abs(odd @ (out - feq) - (1 - 1 / tau_m) * (odd @ (f - feq)) - src) < 1e-15
+    assert abs(1 / tau_m - 1 / tau) > 0.1  # the two halves use different rates
+
+
 def test_trt_unit_rates_give_equilibrium():
     f = _node("D3Q19", 24)
     out = oracle.collide_node("D3Q19", 1.0, "trt", f, params=[0.25])
