@@ -97,6 +97,38 @@ def test_streaming_adjoint_dot_product_exact(name, dims):
     assert abs(float((Sa * b).sum()) - float((a * STb).sum())) < 1e-12
 
 
+@pytest.mark.parametrize("name,dims", [("D2Q9", (5, 4, 1)), ("D3Q19", (3, 2, 2))])
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("with_rho", [False, True])
+def test_moment_seed_is_the_derivative_of_the_moments(name, dims, forced, with_rho):
+    # L = sum_x grho rho + gu . u with (rho, u) of Eq. 4 (u = (j + F/2)/rho): lambda = dL/df and
+    # the direct dL/dF, both against central differences of the oracle's moments
+    d, c, w, _ = oracle.stencil(name)
+    N = oracle.n_nodes(dims)
+    rho, u = lbinputs.random_moments(dims, seed=40, u_amp=0.08)
+    f = oracle.init_eq(name, dims, rho, u) + 2e-3 * lbinputs.random_populations(w, N, 41)
+    F = lbinputs.random_field((d, N), 42, amp=1e-3) if forced else None
+    grho = lbinputs.random_field(N, 43) if with_rho else None
+    gu = lbinputs.random_field((d, N), 44)
+    lam, gF = oracle.seed_moments(name, dims, f, grho, gu, F=F)
+
+    def L(f_, F_=F):
+        r, uu = oracle.moments(name, dims, f_, F=F_)
+        return float((gu * uu).sum()) + (float((grho * r).sum()) if with_rho else 0.0)
+
+    df = lbinputs.random_field(f.shape, 45) * w[:, None]
+    h = 1e-6
+    fd = (L(f + h * df) - L(f - h * df)) / (2 * h)
+    assert abs(fd - float((lam * df).sum())) <= 1e-8 * abs(fd)
+    if forced:
+        dF = lbinputs.random_field(F.shape, 46)
+        hF = 1e-6
+        fd = (L(f, F + hF * dF) - L(f, F - hF * dF)) / (2 * hF)
+        assert abs(fd - float((gF * dF).sum())) <= 1e-8 * abs(fd)
+    else:
+        assert gF is None
+
+
 def test_energy_loss_seed_matches_finite_differences():
     dims = (6, 5, 1)
     N = 30
