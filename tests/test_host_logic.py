@@ -78,3 +78,14 @@ def test_job_throughput_of_a_single_replica():
     assert bench.BYTES_PER_LU[("D3Q19", "f32")] == 152
     assert bench.BYTES_PER_LU[("D3Q27", "f16")] == 108
     assert bench.LEARNED_FLOP_PER_LU["learned3"] == 2 * (6 * 53 + 53 * 3) + 200
+
+
+def test_both_benchmark_arms_name_the_same_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+    cfg = bench.workload_config(2)
+    n = bench.N_GRID
+    assert cfg["grid"] == [n, n, n] and cfg["nodes"] == n ** 3 and cfg["parallelism"] == "replicas x2"
+    tau = lbinputs.tau_from_reynolds(bench.RE, bench.U0, n)
+    assert f"tau = {tau:.6f}" in cfg["workload"] and f"{n}^3" in cfg["workload"]
+    assert bench.workload_config(1) == {**cfg, "parallelism": "replicas x1"}
