@@ -6,14 +6,20 @@
  * (Bedrunka et al., arXiv 2106.12929, Sec. 2.1, Eq. 1) with
  *   - the D2Q9, D3Q19 and D3Q27 velocity sets (Sec. 2.2, 3.1, 3.3),
  *   - the second-order equilibrium (Eq. 3) and the moments rho, rho u (Eq. 4),
- *   - BGK (Eq. 2), regularized (Sec. 2.1) or moment-space collision with a learned
- *     higher-moment relaxation rate (Eq. 5, Sec. 3.1), and a Guo body force,
+ *   - BGK (Eq. 2), regularized (Sec. 2.1) or moment-space collision with learned
+ *     higher-moment relaxation rates (Eq. 5, Sec. 3.1: a shared rate from a 6-24-24-1
+ *     network, or three rates from the paper's one-hidden-layer network), the further
+ *     models Sec. 2.1 cites (TRT, entropic KBC, MRT with fixed rates), and a Guo body force,
+ *   - halfway bounce-back walls on solid nodes (Sec. 2.2 lists boundary conditions),
  * plus the discrete adjoint of the time stepping (gradients through the solver,
- * Sec. 3.2) and the Eq. 6 training loss.
+ * Sec. 3.2), the Eq. 6 training loss and its training helpers, and the spectral flow
+ * control of Sec. 3.2 (every step a velocity shift down the gradient of a log-spectrum
+ * mismatch).
  *
  * Conventions for every call
  *   - Grid: dims = {nx, ny, nz}; 2D stencils need nz == 1. Node n = x + nx (y + ny z).
- *     N = nx ny nz nodes, N < 2^31. Every direction is periodic.
+ *     N = nx ny nz nodes, N < 2^31. Every direction is periodic (walls are solid
+ *     nodes set by lb_set_solid).
  *   - Arrays crossing the boundary are dense, component-major, x fastest:
  *     populations f[Q][N], velocity u[d][N], force F[d][N], density rho[N].
  *     Their element type and location are given by an lb_mem value; device pointers
@@ -128,11 +134,12 @@ typedef struct {
                              into a CUDA graph and replays it (one launch per pair of steps instead
                              of one per kernel; same kernels, same results); 0 = direct launches */
     int nodes_per_thread; /* shape of the stream-collide launch: 0 (default) = chosen from the grid
-                             (one node per thread in 32-thread blocks when the grid has fewer rows
-                             than SMs, else four per thread for half storage without a force,
-                             two otherwise);
+                             (one node per thread in 32-thread blocks when the grid has fewer
+                             256-node x-rows than SMs, else four per thread for half storage
+                             without a force (except D3Q27 KBC), two otherwise);
                              1, 2 or 4 = forced, falling back to the next smaller shape the grid
                              allows (2 needs an even nx; 4 needs half storage and nx % 4 == 0).
+                             LB_NONE and the learned collisions always run one node per thread.
                              Every shape gives bit-identical results */
 } lb_options;
 
@@ -143,8 +150,10 @@ LB_API void lb_default_options(lb_options* opt);
  * zero them. tau > 1/2 is the BGK relaxation time of Eq. 2 (viscosity
  * nu = c_s^2 (tau - 1/2)); for LB_LEARNED_MRT it is the stress relaxation time
  * tau_n of Sec. 3.1. opt may be NULL (defaults). On success *out owns the memory
- * until lb_destroy. Errors: LB_ERR_ARG (dims, tau, enum values), LB_ERR_UNSUPPORTED
- * (learned collision on a stencil other than D2Q9), LB_ERR_OOM, LB_ERR_CUDA. */
+ * until lb_destroy. Errors: LB_ERR_ARG (dims, tau, enum values, option values),
+ * LB_ERR_UNSUPPORTED (the learned collisions or MRT on a stencil other than D2Q9, KBC on
+ * D3Q19, learned_tc without a learned collision or with FP64 storage, record_every with the
+ * AA layout or with TRT, KBC or MRT), LB_ERR_OOM, LB_ERR_CUDA. */
 LB_API lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau,
                     lb_collision collision, const lb_options* opt);
 
@@ -159,7 +168,9 @@ LB_API lb_status lb_init_from_moments(lb_ctx* ctx, const void* rho, const void* 
 /* Set the body force F[d][N] (constant in time); NULL clears it. The velocity of a
  * forced state is u = (sum_i c_i f_i + F/2)/rho and the Guo source
  * S_i = (1 - omega/2) w_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F is added in
- * the collision (Guo, Zheng & Shi 2002; the paper only mentions forcing, Sec. 2.2). */
+ * the collision (Guo, Zheng & Shi 2002; the paper only mentions forcing, Sec. 2.2).
+ * LB_ERR_UNSUPPORTED with the learned, KBC or MRT collisions or with the spectral
+ * control on. */
 LB_API lb_status lb_set_force(lb_ctx* ctx, const void* F, lb_mem mem);
 
 /* Network of the learned collision (Sec. 3.1).
@@ -188,11 +199,13 @@ LB_API lb_status lb_set_relaxation(lb_ctx* ctx, const double* params, int n);
  *   f_opp(i)(x, t + 1) = f*_i(x, t) - 2 w_i (c_i . u_w) / c_s^2,
  * u_w = wall_u at the solid node x + c_i (wall density 1; wall_u [d][N] or NULL = resting
  * walls). Solid nodes do not collide; their exposed state is the rest equilibrium f_i = w_i.
- * mask NULL removes all walls. AB layout only, not with the learned collision or recording
- * (LB_ERR_UNSUPPORTED). Copies both arrays. */
+ * mask NULL removes all walls. AB layout only, not with the learned collisions, recording
+ * or the spectral control (LB_ERR_UNSUPPORTED). Copies both arrays. */
 LB_API lb_status lb_set_solid(lb_ctx* ctx, const void* mask, const void* wall_u, lb_mem mem);
 
-/* Advance n >= 0 steps of Eq. 1 (one fused kernel launch per step). */
+/* Advance n >= 0 steps of Eq. 1: one fused kernel launch per step (five with the spectral
+ * control on); with graphs on and no recording, pairs of steps replay one captured CUDA
+ * graph. With check_every > 0 returns LB_ERR_UNSTABLE as described in lb_options. */
 LB_API lb_status lb_step(lb_ctx* ctx, int64_t n);
 
 /* rho[N] and u[d][N] of the current pre-collision state (Eq. 4, with the force
