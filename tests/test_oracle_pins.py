@@ -237,6 +237,28 @@ def test_learned_invariants_and_collision_are_rotation_equivariant():
         assert abs(a.sum() - f.sum()) < 1e-15
 
 
+def test_learned_invariants_of_constructed_states():
+    # f = f^eq(rho, u) plus weighted Hermite perturbations w_i H(c_i) with known content: a
+    # shear part w cx cy p / c_s^4 has Pi_xy = p, a normal part w (cx^2 - c_s^2) q / (2 c_s^4)
+    # has Pi_xx = q, Pi_yy = 0, and the ghost parts w H_6 a, w H_8 b have ghost moments
+    # a |H_6|^2, b |H_8|^2 (|H|^2 = sum w H^2); none changes rho or rho u, and the
+    # second-order equilibrium has no ghost content, so Pi^neq and the ghost moments are these
+    d, c, w, _ = oracle.stencil("D2Q9")
+    cx, cy = c[:, 0].astype(float), c[:, 1].astype(float)
+    rho, u = 1.03, np.array([0.05, -0.08])
+    p, q, a, b = 2e-3, -3e-3, 4e-3, 5e-3
+    h6, h8 = (cx * cx - CS2) * cy, (cx * cx - CS2) * (cy * cy - CS2)
+    f = (oracle.init_eq("D2Q9", (1, 1, 1), [rho], u.reshape(2, 1))[:, 0]
+         + w * (cx * cy * p / CS2 ** 2 + (cx * cx - CS2) * q / (2 * CS2 ** 2) + h6 * a + h8 * b))
+    n6, n8 = float((w * h6 * h6).sum()), float((w * h8 * h8).sum())
+    expect = [rho - 1.0, (u @ u) / CS2, q / CS2, (q * q + 2 * p * p) / CS2 ** 2,
+              (u[0] ** 2 * q + 2 * u[0] * u[1] * p) / CS2 ** 2, a * a * n6 + b * b * n8]
+    np.testing.assert_allclose(oracle.invariants(f), expect, rtol=1e-12, atol=1e-17)
+    # at equilibrium only the first two are nonzero
+    feq = oracle.init_eq("D2Q9", (1, 1, 1), [rho], u.reshape(2, 1))[:, 0]
+    np.testing.assert_allclose(oracle.invariants(feq), expect[:2] + [0, 0, 0, 0], rtol=1e-12, atol=1e-16)
+
+
 def test_learned_rate_in_open_interval_and_paper_offset():
     const = {}
     with open(os.path.join(GOLDEN, "paper_constants.txt")) as fh:
