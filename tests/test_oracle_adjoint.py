@@ -177,3 +177,19 @@ def test_eq6_loss_seed_matches_finite_differences():
     assert abs(L0 - expect) < 1e-15
     w2, E2 = oracle.vorticity(dims, f)
     np.testing.assert_allclose(w2, vort, atol=1e-17)
+
+
+def test_vorticity_of_single_modes():
+    # second-order central differences of sin(2 pi k x / n) give sin(2 pi k / n) cos(2 pi k x / n),
+    # and w = dv/dx - du/dy; E = (1/2N) sum |u|^2 = (A^2 + B^2)/4 over whole periods
+    nx, ny = 12, 10
+    dims = (nx, ny, 1)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    A, B, k, m = 0.03, 0.02, 2, 3
+    u = np.stack([(B * np.sin(2 * np.pi * m * y / ny)).ravel(), (A * np.sin(2 * np.pi * k * x / nx)).ravel()])
+    f = oracle.init_eq("D2Q9", dims, np.ones(nx * ny), u)
+    w, E = oracle.vorticity(dims, f)
+    expect = (A * math.sin(2 * math.pi * k / nx) * np.cos(2 * np.pi * k * x / nx)
+              - B * math.sin(2 * math.pi * m / ny) * np.cos(2 * np.pi * m * y / ny)).ravel()
+    np.testing.assert_allclose(w, expect, rtol=0, atol=1e-15)
+    assert E == pytest.approx((A * A + B * B) / 4, rel=1e-13)
