@@ -26,7 +26,11 @@
  *          A second network follows the shape Sec. 3.1 describes: one hidden layer
  *          and three outputs, one relaxation time exp(z_n) + 1/2 per higher moment.
  *   Eq. 6  training loss from velocity, vorticity and energy mismatch.
- *   Sec. 3.2 gradients through the solver (here: the discrete adjoint, by hand).
+ *   Sec. 3.2 gradients through the solver (here: the discrete adjoint, by hand), and
+ *          the velocity-shift forcing of the spectral control: BGK toward
+ *          f^eq(rho, u + du) -> ora_step_ushift (du itself is computed in spectral.py).
+ *   Sec. 2.2 boundary conditions (listed without formulas): halfway bounce-back on
+ *          solid nodes with the moving-wall term -> ora_step_walls.
  * Readings where the paper is silent (stencil order, Guo forcing, Hermite moment
  * basis, the six network inputs, loss normalisation) are stated at each function.
  *
