@@ -139,6 +139,32 @@ def test_regularized_second_moment(name):
 
 
 @pytest.mark.parametrize("name", STENCILS)
+def test_regularized_with_force_moments(name):
+    # with a Guo force (u = (j + F/2)/rho): the second moment of f* - f^eq is
+    # (1 - omega) Pi^neq + (1 - omega/2)(u F + F u), and the third moment sum cx^2 cy (f* - f^eq)
+    # carries the relaxed first-order part (1 - omega) c_s^2 a1_y with a1 = sum c (f - f^eq) = -F/2,
+    # plus the source's own third moment
+    d, c, w, _ = oracle.stencil(name)
+    cf = c[:, :d].astype(float)
+    f = _random_node(name, 61)
+    F = np.array([2e-3, -1.5e-3, 1e-3])[:d]
+    tau = 0.7
+    om = 1 / tau
+    out = oracle.collide_node(name, tau, "regularized", f, F=F)
+    rho = f.sum()
+    u = (cf.T @ f + 0.5 * F) / rho
+    feq = oracle.init_eq(name, (1, 1, 1), [rho], u.reshape(d, 1))[:, 0]
+    pneq = np.einsum("ia,ib,i->ab", cf, cf, f - feq)
+    src = (1 - 0.5 * om) * (np.outer(u, F) + np.outer(F, u))
+    np.testing.assert_allclose(np.einsum("ia,ib,i->ab", cf, cf, out - feq), (1 - om) * pneq + src, atol=1e-16)
+    S = oracle.guo_source(name, tau, u, F)
+    h3 = cf[:, 0] ** 2 * cf[:, 1]
+    expect = (1 - om) * CS2 * (-0.5 * F[1]) + h3 @ S
+    assert abs(h3 @ (out - feq) - expect) < 1e-17
+    assert abs((1 - om) * CS2 * 0.5 * F[1]) > 1e-5  # the relaxed first-order part is not negligible
+
+
+@pytest.mark.parametrize("name", STENCILS)
 def test_regularized_discards_non_hydrodynamic_part(name):
     # adding a vector with zero 0th, 1st and 2nd moments leaves the regularized f* unchanged
     d, c, w, _ = oracle.stencil(name)
