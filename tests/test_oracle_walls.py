@@ -124,3 +124,31 @@ def test_couette_profile_with_moving_wall(name, coll, tau):
     u, _ = _row_velocity(name, dims, f, None)
     y = np.arange(1, H + 1, dtype=float)
     np.testing.assert_allclose(u, U * (y - 0.5) / H, rtol=0, atol=1e-9 * U)
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27"])
+@pytest.mark.parametrize("wall_axis,flow_axis", [(2, 1), (0, 2), (1, 0)])
+def test_couette_in_every_orientation(name, wall_axis, flow_axis):
+    # walls normal to wall_axis (solid planes at index 0 and H + 1), the upper one moving with U
+    # along flow_axis: the steady profile is U (s - 1/2) / H across the channel, zero elsewhere
+    H, U, tau = 5, 0.01, 0.8
+    d, c, w, _ = oracle.stencil(name)
+    dims = [3, 3, 3]
+    dims[wall_axis] = H + 2
+    dims = tuple(dims)
+    N = oracle.n_nodes(dims)
+    idx = np.indices((dims[2], dims[1], dims[0])).reshape(3, -1)[::-1]  # x, y, z of each node
+    s = idx[wall_axis]
+    mask = ((s == 0) | (s == H + 1)).astype(np.uint8)
+    wall_u = np.zeros((d, N))
+    wall_u[flow_axis, s == H + 1] = U
+    f = oracle.init_eq(name, dims, np.ones(N), np.zeros((d, N)))
+    nu = CS2 * (tau - 0.5)
+    f = oracle.step_walls(name, dims, tau, "bgk", f, mask, nsteps=int(40.0 * H * H / (nu * math.pi ** 2)),
+                          wall_u=wall_u)
+    _, u = oracle.moments(name, dims, f)
+    fluid = mask == 0
+    np.testing.assert_allclose(u[flow_axis, fluid], U * (s[fluid] - 0.5) / H, rtol=0, atol=1e-9 * U)
+    for a in range(d):
+        if a != flow_axis:
+            np.testing.assert_allclose(u[a, fluid], 0.0, rtol=0, atol=1e-12 * U)
