@@ -89,3 +89,11 @@ def test_both_benchmark_arms_name_the_same_workload():
     tau = lbinputs.tau_from_reynolds(bench.RE, bench.U0, n)
     assert f"tau = {tau:.6f}" in cfg["workload"] and f"{n}^3" in cfg["workload"]
     assert bench.workload_config(1) == {**cfg, "parallelism": "replicas x1"}
+
+
+def test_every_experiment_is_reachable_from_the_command_line():
+    import inspect
+    from paper_2106_12929_gb300 import experiments
+    src = inspect.getsource(experiments.main)
+    for name in ("tgv2d_decay", "tgv3d_precision", "turbulence_precision", "adjoint_fd", "spectral_control"):
+        assert callable(getattr(experiments, name)) and f'"{name}"' in src and name in experiments.__doc__
