@@ -18,7 +18,8 @@
  *
  * Conventions for every call
  *   - Grid: dims = {nx, ny, nz}; 2D stencils need nz == 1. Node n = x + nx (y + ny z).
- *     N = nx ny nz nodes, N < 2^31. Every direction is periodic (walls are solid
+ *     N = nx ny nz nodes, 1 <= nx, ny, nz <= 65535 and N < 2^31 (LB_ERR_ARG otherwise).
+ *     Every direction is periodic (walls are solid
  *     nodes set by lb_set_solid).
  *   - Arrays crossing the boundary are dense, component-major, x fastest:
  *     populations f[Q][N], velocity u[d][N], force F[d][N], density rho[N].

@@ -74,6 +74,12 @@ def _create(lib, stencil=0, dims=(8, 8, 1), tau=0.8, coll=0, **opt_kw):
     (dict(stencil=2, dims=(4, 4, 4), coll=6), 6),  # MRT is D2Q9 only
     (dict(coll=4, record_every=3), 6),             # no adjoint of TRT / KBC / MRT
     (dict(learned_tc=1), 6),                # tensor-core network needs the learned collision
+    (dict(dims=(-4, 8, 1)), 1),
+    (dict(dims=(65536, 1, 1)), 1),          # every edge at most 65535 (launch-grid limit)
+    (dict(dims=(50000, 50000, 1)), 1),      # N = 2.5e9 nodes: beyond N < 2^31
+    (dict(stencil=1, dims=(2048, 2048, 600)), 1),
+    (dict(check_every=-1), 1),
+    (dict(record_every=-2), 1),
 ])
 def test_create_rejects_bad_arguments_without_gpu(lib, kw, expect):
     opt_keys = {"storage", "layout", "record_every", "check_every", "graphs", "learned_tc", "nodes_per_thread"}
