@@ -116,3 +116,22 @@ def test_product_path_has_no_cpu_fallback():
             with open(os.path.join(pkg_dir, fn)) as fh:
                 src = fh.read()
             assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+@pytest.mark.parametrize("stencil,dims,mem,null_f", [
+    (0, (8, 8, 1), 1, True),              # f is required
+    (5, (8, 8, 1), 1, False),             # unknown stencil
+    (0, (8, 8, 1), 0, False),             # host arrays are not accepted
+    (0, (65536, 1, 1), 1, False),         # edge beyond 65535
+    (0, (8, 8, 2), 1, False),             # 2D stencil needs nz = 1
+    (1, (8192, 4097, 1), 1, False),       # more nodes than its fixed scratch array serves
+])
+def test_noalloc_sums_reject_bad_arguments_before_any_device_work(lib, stencil, dims, mem, null_f):
+    # every case fails argument validation, which runs before any CUDA call, so the host buffer
+    # passed as f is never dereferenced
+    buf = (ctypes.c_double * 8)()
+    out = (ctypes.c_double * 6)()
+    d = (ctypes.c_int64 * 3)(*dims)
+    f = None if null_f else ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.lb_reduce_noalloc(stencil, d, f, None, mem, out, None) == 1
+    assert lib.lb_last_error()
