@@ -4,8 +4,8 @@ lb_reduce_noalloc serves callers that cannot allocate device memory where they
 need the sums (for instance when another framework's caching allocator owns the
 device memory, or in a loop where a cudaMalloc/cudaFree would stall the device):
 it takes a caller-owned population array and keeps its partial sums in a fixed
-static device array of the library. This file is collected last so that a run
-stopping at the first failure has already run every other test.
+static device array of the library. This file is collected after the parity tests of the
+hot path so that a run stopping at the first failure has already run them.
 """
 import ctypes
 
