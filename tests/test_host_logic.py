@@ -97,3 +97,23 @@ def test_every_experiment_is_reachable_from_the_command_line():
     src = inspect.getsource(experiments.main)
     for name in ("tgv2d_decay", "tgv3d_precision", "turbulence_precision", "adjoint_fd", "spectral_control"):
         assert callable(getattr(experiments, name)) and f'"{name}"' in src and name in experiments.__doc__
+
+
+def test_clock_sampler_reads_median_clock_and_active_reasons():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return ("1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "2070, 2070, 1100.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "2070, 2070, 1180.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n", "")
+
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.proc, s.out = _Proc(), []
+    got = s.stop()
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
