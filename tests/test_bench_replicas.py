@@ -47,3 +47,46 @@ def test_two_replicas_take_the_slowest_rank():
         lups, t = out[r]
         assert t == pytest.approx(3.0)
         assert lups == pytest.approx(2 * 1000 * 10 / 3.0)
+
+
+def _rank_retry(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # only rank 0's first clock record is rejected; both ranks must take the region again
+    records = [{"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown"] if rank == 0 else []},
+               {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}]
+
+    class _Sampler:
+        def __init__(self, gpu_index):
+            self.rec = records.pop(0)
+
+        def stop(self):
+            return self.rec
+
+    class _Lat:
+        def launch_count(self):
+            return 0
+
+    bench.ClockSampler = _Sampler
+    bench.time_steps = lambda lat, k, stream: 1.0
+    t, clocks, _ = bench.timed_region(_Lat(), 5, None, 0, world, device="cpu")
+    out[rank] = (clocks["remeasured"], len(records))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_a_rejected_clock_record_on_one_rank_retakes_the_region_on_all():
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_retry, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    assert out[0] == (True, 0) and out[1] == (True, 0)

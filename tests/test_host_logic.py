@@ -117,3 +117,50 @@ def test_clock_sampler_reads_median_clock_and_active_reasons():
     s.proc, s.out = _Proc(), []
     got = s.stop()
     assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_record_rejection_rule():
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected({**ok, "sm_mhz": 1500.0, "reasons": ["sw_power_cap"]})  # kept, noted
+    assert bench.clocks_rejected({**ok, "reasons": ["hw_slowdown"]})
+    assert bench.clocks_rejected({**ok, "reasons": ["sw_power_cap", "sw_thermal_slowdown"]})
+    assert bench.clocks_rejected({**ok, "sm_mhz": 1200.0})  # well below max with no reason: a clock lock
+
+
+@pytest.mark.parametrize("first_bad", [False, True])
+def test_timed_region_is_taken_once_more_after_a_rejected_clock_record(monkeypatch, first_bad):
+    sys.path.insert(0, ROOT)
+    import bench
+    records = [{"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"] if first_bad else []},
+               {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}]
+    times = [2.0, 1.0]
+
+    class _Sampler:
+        def __init__(self, gpu_index):
+            self.rec = records.pop(0)
+
+        def stop(self):
+            return self.rec
+
+    class _Lat:
+        launches = 0
+
+        def launch_count(self):
+            return self.launches
+
+    lat = _Lat()
+
+    def _time_steps(lat_, k, stream):
+        lat_.launches += k
+        return times.pop(0)
+
+    monkeypatch.setattr(bench, "ClockSampler", _Sampler)
+    monkeypatch.setattr(bench, "time_steps", _time_steps)
+    t, clocks, launches = bench.timed_region(lat, 10, None, 0, world=1)
+    assert launches == 10 and clocks["remeasured"] is first_bad
+    assert t == (1.0 if first_bad else 2.0) and clocks["reasons"] == []
+    assert len(records) == (0 if first_bad else 1)
