@@ -164,3 +164,17 @@ def test_timed_region_is_taken_once_more_after_a_rejected_clock_record(monkeypat
     assert launches == 10 and clocks["remeasured"] is first_bad
     assert t == (1.0 if first_bad else 2.0) and clocks["reasons"] == []
     assert len(records) == (0 if first_bad else 1)
+
+
+def test_build_rebuilds_an_object_only_when_a_dependency_is_newer(tmp_path):
+    from paper_2106_12929_gb300 import build
+    src, hdr, obj = (tmp_path / n for n in ("a.cu", "a.cuh", "a.o"))
+    for p in (src, hdr, obj):
+        p.write_text("x")
+    os.utime(src, (100, 100))
+    os.utime(hdr, (100, 100))
+    os.utime(obj, (200, 200))
+    assert not build._stale(str(obj), [str(src), str(hdr)])
+    os.utime(hdr, (300, 300))  # a header edited after the object was built
+    assert build._stale(str(obj), [str(src), str(hdr)])
+    assert build._stale(str(tmp_path / "missing.o"), [str(src)])
