@@ -555,7 +555,7 @@ def spectral_control(stream, n=128, steps=200, storage="f32", kappa=5e-4):
             "launches_per_controlled_step": launches, "cost_after": R}
 
 
-def cpu_baseline(sample_steps: int = 1):
+def cpu_baseline(sample_steps: int = 20):  # 10-20 s of oracle work on 16 Arm cores
     """The FP64 CPU oracle on this host, on a bounded sample of the same workload: the full
     256^3 D3Q19 grid for `sample_steps` step(s)."""
     import oracle
