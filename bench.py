@@ -67,33 +67,59 @@ def measured_peak_hbm():
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons. A reader thread stamps
+    each line with the host time it arrived, so that stop() can keep the samples taken inside
+    the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        import threading
         self.proc = None
-        self.out = []
+        self.lines = []  # (host time, line)
+        self.thread = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
 
-    def stop(self):
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line))
+
+    def wait_first_sample(self, timeout: float = 3.0):
+        """Block until nvidia-smi has printed its first sample (or the timeout passed)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
+    def stop(self, window=None):
+        """Summary of the samples: those stamped inside window = (t0, t1) when there are any,
+        else all of them."""
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            text, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            text, _ = self.proc.communicate()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        stamped = list(self.lines)
+        inside = [ln for t, ln in stamped if window and window[0] <= t <= window[1]]
+        return self.summarise(inside if inside else [ln for _, ln in stamped], in_window=bool(inside))
+
+    @staticmethod
+    def summarise(lines, in_window=True):
         sm, smax, reasons = [], [], set()
-        for line in text.strip().splitlines():
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -109,7 +135,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "in_timed_region": in_window}
 
 
 def dist_info():
@@ -157,24 +183,42 @@ def clocks_rejected(clocks) -> bool:
     return not clocks["reasons"] and clocks["sm_mhz"] < 0.9 * clocks["sm_max_mhz"]
 
 
+MIN_TIMED_SECONDS = 0.8  # clock samples come every 200 ms: repeat the K-step region this long
+
+
 def timed_region(lat, k: int, stream, gpu_index: int, world: int, device: str = "cuda"):
-    """K steps timed on the device with the clocks sampled meanwhile; taken once more when the
-    clock record rejects the first attempt (the decision is the same on every rank). Returns
-    (seconds, clocks, launches); clocks["remeasured"] says whether the second attempt was used."""
+    """K steps timed on the device with the clocks sampled meanwhile. The K-step region is
+    timed `reps` times back to back (at least three, and for at least MIN_TIMED_SECONDS so that
+    nvidia-smi's 200 ms samples fall inside it; every rank runs the same count) and the median
+    is returned. The whole measurement is taken once more when the clock record rejects the
+    first attempt (the decision is the same on every rank). Returns (seconds, clocks,
+    launches per region); clocks["remeasured"] says whether the second attempt was used and
+    clocks["repeats"] how many regions were timed."""
     for attempt in range(2):
         sampler = ClockSampler(gpu_index)
+        sampler.wait_first_sample()
         launches0 = lat.launch_count()
+        t0 = time.time()
         barrier(world)
-        t = time_steps(lat, k, stream)
+        first = time_steps(lat, k, stream)
         barrier(world)
-        clocks = sampler.stop()
-        launches = lat.launch_count() - launches0
+        per = max_over_ranks(first, world, device)
+        reps = int(min(max(3, math.ceil(MIN_TIMED_SECONDS / max(per, 1e-6))), 1000))
+        times = [first]
+        for _ in range(reps - 1):
+            barrier(world)
+            times.append(time_steps(lat, k, stream))
+            barrier(world)
+        t1 = time.time()
+        clocks = sampler.stop(window=(t0, t1))
+        launches = (lat.launch_count() - launches0) // reps
         retry = max_over_ranks(1.0 if clocks_rejected(clocks) else 0.0, world, device) > 0.0
         if attempt == 0 and retry:
             continue
         if clocks is not None:
             clocks["remeasured"] = attempt == 1
-        return t, clocks, launches
+            clocks["repeats"] = reps
+        return statistics.median(times), clocks, launches
 
 
 def time_steps(lat, k: int, stream):
@@ -190,14 +234,14 @@ def time_steps(lat, k: int, stream):
     return start.elapsed_time(end) / 1e3
 
 
-def workload_config(world):
-    """The `config` object of the benchmark line (both arms): the 256^3 TGV workload."""
-    n = N_GRID
+def workload_config(world, n=N_GRID):
+    """The `config` object of the benchmark line (both arms): the n^3 TGV workload (256^3
+    unless the reference arm had to time a smaller grid)."""
     tau = lbinputs.tau_from_reynolds(RE, U0, n)
     return {"workload": f"D3Q19 BGK FP32 two-buffer pull stream-collide, {n}^3 periodic 3D Taylor-Green "
                         f"vortex, Re {RE:g}, Ma 0.1 (u0 = {U0:.6f}), tau = {tau:.6f}",
             "grid": [n, n, n], "nodes": n ** 3, "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (two 1.27 GB population buffers per replica)"}
+            "l2": f"inputs larger than L2 (two {19 * 4 * n ** 3 / 1e9:.2f} GB population buffers per replica)"}
 
 
 def tgv_workload(n=N_GRID):
@@ -614,14 +658,28 @@ def cpu_baseline_table():
     return {"cores": oracle.num_threads(), "samples": rows}
 
 
+REFERENCE_LU_BUDGET = 6e9  # lattice updates the reference arm may spend (~200 s at 30 MLUPS)
+
+
+def reference_grid(steps: int, warmup: int) -> int:
+    """Edge of the grid the reference arm times: the 256^3 workload itself when its K + W
+    steps fit the budget (the driver's short runs), else the largest of 128^3, 64^3 that does."""
+    for n in (N_GRID, 128, 64):
+        if (steps + warmup) * n ** 3 <= REFERENCE_LU_BUDGET:
+            return n
+    return 32
+
+
 def run_reference(args):
     """The oracle timed on the host cores as the reference arm: each step is one lattice
-    update of a 64^3 periodic TGV at the same Re and Ma (a bounded sample of the workload)."""
+    update of the periodic TGV at the same Re and Ma on the grid reference_grid() picks
+    (256^3, the benchmark's own grid, unless K + W steps of it would take minutes); the
+    line's `config` names the grid that was timed."""
     world, rank, _ = dist_info()
     if rank != 0:
         return
     import oracle
-    n = 64
+    n = reference_grid(args.steps, args.warmup)
     dims, tau, rho, u = tgv_workload(n)
     N = n ** 3
     f = oracle.init_eq("D3Q19", dims, rho, u)
@@ -634,10 +692,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(world),
+        "config": workload_config(world, n),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"FP64 oracle (plain C, OpenMP over nodes), each step one update of a 64^3 grid "
-                                   f"of the same flow (Re {RE:g}, Ma 0.1, tau = {tau:.6f} at 64^3), "
+                         "sample": f"FP64 oracle (plain C, OpenMP over nodes), each step one update of the {n}^3 "
+                                   f"grid of the same flow (Re {RE:g}, Ma 0.1, tau = {tau:.6f}), "
                                    f"{args.steps} steps after {args.warmup}"},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

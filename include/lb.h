@@ -339,9 +339,12 @@ LB_API lb_status lb_adam_update(float* theta, float* m, float* v, const float* g
  * It needs no context and performs no device allocation: its per-block partial sums
  * live in a fixed file-scope device array of the library (about 385 KB, held on every
  * GPU that loads the library until the process exits), which limits the grid to
- * N <= 33,554,432 nodes; larger grids are rejected with LB_ERR_ARG. The first call on
- * a device looks up that array's device address (with that device current); make
- * that first call before any stream capture. All calls share the array: calls that
+ * N <= 33,554,432 nodes; larger grids are rejected with LB_ERR_ARG. f and F must be
+ * device (or managed) memory of the current device (checked with
+ * cudaPointerGetAttributes; anything else is LB_ERR_ARG, before any launch). The first
+ * call on a device looks up that array's device address (with that device current)
+ * and keeps it for the life of the process; make that first call before any stream
+ * capture, and do not call this entry point on a device after a cudaDeviceReset. All calls share the array: calls that
  * overlap on the GPU (other streams or threads on the same device) race, so order
  * them. Errors: LB_ERR_ARG (arguments, size), LB_ERR_CUDA. */
 LB_API lb_status lb_reduce_noalloc(lb_stencil stencil, const int64_t dims[3], const void* f, const void* F,

@@ -7,7 +7,10 @@ final state. Its backward pass seeds the adjoint from the moment cotangents
 (``lb_adjoint_seed_moments``) and runs ``lb_step_adjoint`` over the recorded run
 (checkpoints every ``record_every`` steps, recomputation in between), returning
 dL/dF for the body force and dL/dtheta for a learned collision's network parameters
-(793 for "learned", 533 for "learned3"). rho0 and u0 are treated as constants.
+(793 for "learned", 533 for "learned3"). rho0 and u0 are treated as constants. The
+lattice keeps only its last recorded run: a backward pass after the lattice was
+stepped, re-initialised or given a new force or network raises instead of returning
+another run's gradient.
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ class _LBRun(torch.autograd.Function):
         rho, u = lattice.moments(dtype=torch.float64 if lattice.storage == "f64" else torch.float32,
                                  device=lattice.device)
         ctx.lattice = lattice
+        ctx.version = lattice.version
         ctx.nsteps = nsteps
         ctx.has_F = F is not None
         ctx.has_theta = theta is not None
@@ -40,6 +44,11 @@ class _LBRun(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_rho, g_u):
         lat: Lattice = ctx.lattice
+        if lat.version != ctx.version:
+            # lb_step_adjoint differentiates whatever run the lattice recorded last; after another
+            # run, a new initial state, force or network it would return that run's gradient
+            raise RuntimeError("lb_run backward: the lattice was re-initialised, stepped or given a new force or "
+                               "network since this run's forward pass; its recorded run is gone")
         rdt = torch.float64 if lat.storage == "f64" else torch.float32
         dev = lat.device
         g_u = torch.zeros((lat.D, lat.N), dtype=rdt, device=dev) if g_u is None else g_u.to(device=dev, dtype=rdt)

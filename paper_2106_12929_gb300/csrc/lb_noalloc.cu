@@ -13,7 +13,9 @@
 // the library holds it (kScratchDoubles doubles, about 385 KB) until the process
 // exits. Its address is looked up once per device (cudaGetSymbolAddress) by the
 // first call on that device, with that device current; make that first call before
-// any stream capture. All calls share the array and it keeps the last call's
+// any stream capture. The looked-up address is kept for the life of the process, so
+// it does not survive a cudaDeviceReset of that device: do not call this entry point
+// on a device after resetting it. All calls share the array and it keeps the last call's
 // contents; every word a call reads was written earlier in the same call (each
 // block overwrites its partial slot, the final pass overwrites the result slot), so
 // nothing has to be cleared. Calls whose work overlaps on the GPU (different
@@ -165,6 +167,23 @@ extern "C" lb_status lb_reduce_noalloc(lb_stencil stencil, const int64_t dims[3]
     if (N > kMaxNodes)  // the scratch array holds the partials of at most 8192 blocks of 4096 nodes
         return reject(LB_ERR_ARG, "lb_reduce_noalloc: more than 33,554,432 nodes (its fixed scratch array holds the "
                                   "partial sums of at most 8192 blocks of 4096 nodes)");
+    // f and F must be memory the current device can read: a host pointer or another
+    // device's allocation passed with a device code would make the kernel fault.
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return reject(LB_ERR_CUDA, "lb_reduce_noalloc: cudaGetDevice failed");
+    for (const void* p : {f, F}) {
+        if (!p) continue;
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+            cudaGetLastError();  // clear the (non-sticky) error the failed query recorded
+            return reject(LB_ERR_ARG, "lb_reduce_noalloc: f or F is not a CUDA pointer");
+        }
+        const bool readable = (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) &&
+                              attr.device == cur;
+        if (!readable)
+            return reject(LB_ERR_ARG, "lb_reduce_noalloc: f and F must be device (or managed) memory of the current "
+                                      "device");
+    }
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess)
         return reject(LB_ERR_CUDA, "lb_reduce_noalloc: cudaGetSymbolAddress of the scratch array failed");

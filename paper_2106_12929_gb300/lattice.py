@@ -92,6 +92,9 @@ class Lattice:
         _lib.check(self._lib.lb_create(ctypes.byref(h), _lib.STENCIL[stencil], dims_arr, ctypes.c_double(tau),
                                        _lib.COLLISION[collision], ctypes.byref(opt)), "lb_create")
         self._h = h
+        # bumped by every call that changes the state, the force, the collision's parameters
+        # or the recording, so that a pending backward pass can tell that its run is gone
+        self.version = 0
 
     # ------------------------------------------------------------------ lifetime
     def close(self):
@@ -129,6 +132,7 @@ class Lattice:
 
     # ------------------------------------------------------------------ state
     def init_from_moments(self, rho, u):
+        self.version += 1
         r = _to_tensor(rho)
         v = _to_tensor(u, like=r)
         _lib.check(self._lib.lb_init_from_moments(self._h, r.data_ptr(), v.data_ptr(), _mem_code(r)),
@@ -137,6 +141,7 @@ class Lattice:
         return self
 
     def set_force(self, F):
+        self.version += 1
         if F is None:
             _lib.check(self._lib.lb_set_force(self._h, None, 0), "lb_set_force")
             return self
@@ -146,12 +151,14 @@ class Lattice:
         return self
 
     def set_mlp(self, params):
+        self.version += 1
         t = _to_tensor(params)
         _lib.check(self._lib.lb_set_mlp(self._h, t.data_ptr(), t.numel(), _mem_code(t)), "lb_set_mlp")
         return self
 
     def set_relaxation(self, params):
         """TRT: [Lambda]; MRT: [tau_6, tau_7, tau_8] (see lb_set_relaxation)."""
+        self.version += 1
         v = (ctypes.c_double * len(params))(*[float(x) for x in params])
         _lib.check(self._lib.lb_set_relaxation(self._h, v, len(params)), "lb_set_relaxation")
         return self
@@ -159,6 +166,7 @@ class Lattice:
     def set_solid(self, mask, wall_u=None):
         """Solid nodes (mask[N] nonzero) with halfway bounce-back; wall_u[d][N] moves them
         (float32/float64, like the other arrays); mask None removes all walls."""
+        self.version += 1
         if mask is None:
             _lib.check(self._lib.lb_set_solid(self._h, None, None, _lib.MEM["host_f64"]), "lb_set_solid")
             return self
@@ -180,12 +188,14 @@ class Lattice:
         return self
 
     def set_populations(self, f):
+        self.version += 1
         t = _to_tensor(f)
         _lib.check(self._lib.lb_set_populations(self._h, t.data_ptr(), _mem_code(t)), "lb_set_populations")
         self._keep = (t,)
         return self
 
     def step(self, n: int = 1):
+        self.version += 1
         _lib.check(self._lib.lb_step(self._h, int(n)), "lb_step")
         return self
 
@@ -210,6 +220,7 @@ class Lattice:
 
     def coarsen_from(self, fine: "Lattice"):
         """This (coarse) lattice's state <- f^eq of the 2x block-averaged moments of `fine`."""
+        self.version += 1
         _lib.check(self._lib.lb_coarsen_into(fine._h, self._h), "lb_coarsen_into")
         return self
 
@@ -228,6 +239,7 @@ class Lattice:
     def set_spectral_control(self, sigma0, cutoff: float = 2e-5, kappa: float = 5e-5):
         """Sec. 3.2: every later step collides at u + du, du = -kappa grad_u R, R the log-spectrum
         mismatch to sigma0 (n/2 shells) with cutoff c; sigma0 None turns it off."""
+        self.version += 1
         if sigma0 is None:
             _lib.check(self._lib.lb_set_spectral_control(self._h, None, 0, 0.0, 0.0), "lb_set_spectral_control")
             return self

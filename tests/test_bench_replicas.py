@@ -63,17 +63,21 @@ def _rank_retry(rank, world, port, out):
         def __init__(self, gpu_index):
             self.rec = records.pop(0)
 
-        def stop(self):
-            return self.rec
+        def wait_first_sample(self):
+            pass
+
+        def stop(self, window=None):
+            return dict(self.rec)
 
     class _Lat:
         def launch_count(self):
             return 0
 
     bench.ClockSampler = _Sampler
-    bench.time_steps = lambda lat, k, stream: 1.0
+    # the ranks' K-step regions take different times; the repeat count follows the slowest
+    bench.time_steps = lambda lat, k, stream: [0.1, 0.3][rank]
     t, clocks, _ = bench.timed_region(_Lat(), 5, None, 0, world, device="cpu")
-    out[rank] = (clocks["remeasured"], len(records))
+    out[rank] = (clocks["remeasured"], len(records), clocks["repeats"])
     dist.barrier()
     dist.destroy_process_group()
 
@@ -89,4 +93,5 @@ def test_a_rejected_clock_record_on_one_rank_retakes_the_region_on_all():
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
-    assert out[0] == (True, 0) and out[1] == (True, 0)
+    reps = max(3, -(-0.8 // 0.3))  # ceil(MIN_TIMED_SECONDS / slowest region), at least three
+    assert out[0] == (True, 0, reps) and out[1] == (True, 0, reps)

@@ -506,6 +506,28 @@ def test_autograd_network_gradient_matches_oracle():
     assert np.max(np.abs(theta.grad.cpu().numpy() - gth)) <= 1e-10 * np.max(np.abs(gth))
 
 
+def test_autograd_backward_after_another_run_raises():
+    """The lattice keeps one recorded run: a second lb_run with the same step count replaces it,
+    so the first result's backward pass must fail instead of returning the second run's gradient."""
+    from paper_2106_12929_gb300 import Lattice, lb_run
+    dims, rho, u = lbinputs.shear_layer(16, u0=0.05)
+    lat = Lattice("D2Q9", dims, 0.6, "bgk", storage="f64", record_every=2)
+    F1 = torch.tensor(lbinputs.smooth_force(dims, 1e-4, seed=3), device="cuda", requires_grad=True)
+    F2 = torch.tensor(lbinputs.smooth_force(dims, 1e-4, seed=4), device="cuda", requires_grad=True)
+    r0, v0 = torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda")
+    _, v1 = lb_run(lat, r0, v0, 5, F=F1)
+    _, v2 = lb_run(lat, r0, v0, 5, F=F2)
+    with pytest.raises(RuntimeError, match="recorded run is gone"):
+        (v1 ** 2).sum().backward()
+    (v2 ** 2).sum().backward()  # the latest run still differentiates
+    assert torch.isfinite(F2.grad).all() and F2.grad.abs().max() > 0
+    _, v3 = lb_run(lat, r0, v0, 5, F=F1)
+    lat.set_force(F2.detach())
+    with pytest.raises(RuntimeError, match="recorded run is gone"):
+        (v3 ** 2).sum().backward()
+    lat.close()
+
+
 @pytest.mark.parametrize("name,dims", [("D2Q9", (8, 3, 1)), ("D2Q9", (4, 5, 1)), ("D3Q19", (4, 3, 3)),
                                        ("D3Q19", (12, 2, 2)), ("D3Q27", (4, 5, 3))])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])

@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: the training driver's scale conventions and spectrum
 diagnostic, the workload generators' closed forms, and the benchmark's bookkeeping."""
 import math
+import statistics
 import os
 import sys
 
@@ -99,7 +100,7 @@ def test_every_experiment_is_reachable_from_the_command_line():
         assert callable(getattr(experiments, name)) and f'"{name}"' in src and name in experiments.__doc__
 
 
-def test_clock_sampler_reads_median_clock_and_active_reasons():
+def test_clock_sampler_keeps_the_samples_inside_the_timed_region():
     sys.path.insert(0, ROOT)
     import bench
 
@@ -107,16 +108,23 @@ def test_clock_sampler_reads_median_clock_and_active_reasons():
         def terminate(self):
             pass
 
-        def communicate(self, timeout=None):
-            return ("1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
-                    "2070, 2070, 1100.5, 0x4, Not Active, Not Active, Not Active, Active\n"
-                    "2070, 2070, 1180.0, 0x4, Not Active, Not Active, Not Active, Active\n"
-                    "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n", "")
+        def wait(self, timeout=None):
+            return 0
 
     s = bench.ClockSampler.__new__(bench.ClockSampler)
-    s.proc, s.out = _Proc(), []
-    got = s.stop()
-    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s.proc, s.thread = _Proc(), None
+    s.lines = [(1.0, "210, 2070, 90.0, 0x1, Not Active, Not Active, Not Active, Not Active\n"),  # idle, before
+               (2.0, "1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"),
+               (2.2, "2070, 2070, 1100.5, 0x4, Not Active, Not Active, Not Active, Active\n"),
+               (2.4, "2070, 2070, 1180.0, 0x4, Not Active, Not Active, Not Active, Active\n"),
+               (2.6, "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n"),
+               (9.0, "300, 2070, 95.0, 0x1, Active, Not Active, Not Active, Not Active\n")]  # after
+    got = s.stop(window=(1.5, 3.0))
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
+                   "in_timed_region": True}
+    # no sample inside the window: the summary of all samples, marked as such
+    got = s.stop(window=(5.0, 6.0))
+    assert got["samples"] == 5 and got["in_timed_region"] is False and "hw_slowdown" in got["reasons"]
 
 
 def test_clock_record_rejection_rule():
@@ -132,18 +140,29 @@ def test_clock_record_rejection_rule():
 
 
 @pytest.mark.parametrize("first_bad", [False, True])
-def test_timed_region_is_taken_once_more_after_a_rejected_clock_record(monkeypatch, first_bad):
+@pytest.mark.parametrize("region_s", [2.0, 0.05])
+def test_timed_region_repeats_and_is_taken_once_more_after_a_rejected_clock_record(monkeypatch, first_bad,
+                                                                                   region_s):
     sys.path.insert(0, ROOT)
     import bench
     records = [{"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"] if first_bad else []},
                {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}]
-    times = [2.0, 1.0]
+    # a K-step region of region_s seconds is repeated max(3, ceil(0.8 s / region_s)) times
+    reps = max(3, math.ceil(bench.MIN_TIMED_SECONDS / region_s))
+    first = [region_s * (1.0 + 0.01 * j) for j in range(reps)]  # median = the middle one
+    second = [t + 0.001 * region_s for t in first]  # the same repeat count, distinguishable times
+    times = first + second
+    windows = []
 
     class _Sampler:
         def __init__(self, gpu_index):
             self.rec = records.pop(0)
 
-        def stop(self):
+        def wait_first_sample(self):
+            pass
+
+        def stop(self, window=None):
+            windows.append(window)
             return self.rec
 
     class _Lat:
@@ -161,9 +180,67 @@ def test_timed_region_is_taken_once_more_after_a_rejected_clock_record(monkeypat
     monkeypatch.setattr(bench, "ClockSampler", _Sampler)
     monkeypatch.setattr(bench, "time_steps", _time_steps)
     t, clocks, launches = bench.timed_region(lat, 10, None, 0, world=1)
-    assert launches == 10 and clocks["remeasured"] is first_bad
-    assert t == (1.0 if first_bad else 2.0) and clocks["reasons"] == []
+    assert launches == 10 and clocks["remeasured"] is first_bad and clocks["repeats"] == reps
+    assert t == pytest.approx(statistics.median(second if first_bad else first)) and clocks["reasons"] == []
     assert len(records) == (0 if first_bad else 1)
+    assert all(w[0] <= w[1] for w in windows)
+    assert len(times) == (0 if first_bad else reps)
+
+
+def test_reference_arm_grid_fits_its_budget():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reference_grid(20, 5) == bench.N_GRID  # the driver's short run times the 256^3 grid itself
+    assert bench.reference_grid(2000, 10) == 128
+    assert bench.reference_grid(20000, 10) == 64
+    for k in (1, 20, 200, 2000, 20000):
+        n = bench.reference_grid(k, 10)
+        assert (k + 10) * n ** 3 <= bench.REFERENCE_LU_BUDGET or n == 32
+    cfg = bench.workload_config(1, 128)
+    assert cfg["grid"] == [128, 128, 128] and "128^3" in cfg["workload"] and cfg["nodes"] == 128 ** 3
+
+
+def test_lb_run_backward_refuses_a_replaced_run():
+    """The autograd wrapper's guard, with a stand-in lattice (no GPU): any state change after
+    the forward pass makes its backward pass raise instead of differentiating another run."""
+    import torch
+    from paper_2106_12929_gb300 import autograd
+
+    class _Lat:
+        storage, D, N, collision, device = "f64", 2, 4, "bgk", torch.device("cpu")
+
+        def __init__(self):
+            self.version = 0
+            self.adjoint_calls = 0
+
+        def set_force(self, F):
+            self.version += 1
+
+        def init_from_moments(self, r, u):
+            self.version += 1
+
+        def step(self, n):
+            self.version += 1
+
+        def moments(self, dtype, device):
+            return torch.ones(4, dtype=dtype), torch.zeros((2, 4), dtype=dtype)
+
+        def adjoint_seed_moments(self, g_rho, g_u, grad_F=None):
+            return torch.zeros((9, 4), dtype=torch.float64)
+
+        def step_adjoint(self, lam, n, grad_F=None, grad_theta=None, want_lambda0=True):
+            self.adjoint_calls += 1
+
+    lat = _Lat()
+    F = torch.zeros((2, 4), dtype=torch.float64, requires_grad=True)
+    _, u1 = autograd.lb_run(lat, torch.ones(4), torch.zeros((2, 4)), 3, F=F)
+    u1.sum().backward()  # nothing changed: the adjoint runs
+    assert lat.adjoint_calls == 1
+    _, u2 = autograd.lb_run(lat, torch.ones(4), torch.zeros((2, 4)), 3, F=F)
+    lat.step(1)
+    with pytest.raises(RuntimeError, match="recorded run is gone"):
+        u2.sum().backward()
+    assert lat.adjoint_calls == 1
 
 
 def test_build_rebuilds_an_object_only_when_a_dependency_is_newer(tmp_path):

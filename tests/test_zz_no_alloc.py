@@ -80,3 +80,36 @@ def test_noalloc_rejects_oversized_grids_and_host_arrays():
     host = np.zeros(9 * 16)
     ok_dims = (ctypes.c_int64 * 3)(4, 4, 1)
     assert lb.lb_reduce_noalloc(0, ok_dims, host.ctypes.data, None, lib.MEM["host_f64"], out, None) == 1
+
+
+@pytest.mark.parametrize("dims", [(2048, 1200, 1), (8192, 4096, 1)])
+def test_noalloc_matches_lb_reduce_at_many_blocks_and_at_capacity(dims):
+    """600 partial blocks (the final pass loops over more slots than it has threads) and exactly
+    the 33,554,432-node capacity (all 8192 slots), FP32 D2Q9 populations made on the device."""
+    N = int(np.prod(dims))
+    w = torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, dtype=torch.float32, device="cuda")
+    for seed in (5, 6):  # two calls in a row
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        f = w[:, None] * (1.0 + 0.05 * torch.randn((9, N), generator=gen, device="cuda", dtype=torch.float32))
+        rc, got = _noalloc("D2Q9", dims, f)
+        assert rc == 0
+        ref = _with_context("D2Q9", dims, f, storage="f32")
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+        del f
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_rejects_a_host_pointer_passed_as_device_memory():
+    """A host array with a device memory code is refused before any launch (the kernel would
+    otherwise read memory the GPU cannot address)."""
+    lib = _lib()
+    lb = lib.load()
+    out = (ctypes.c_double * 6)()
+    dims = (ctypes.c_int64 * 3)(4, 4, 1)
+    host = np.full(9 * 16, 1.0 / 9.0)
+    assert lb.lb_reduce_noalloc(0, dims, host.ctypes.data, None, lib.MEM["device_f64"], out, None) == 1
+    assert b"device" in lb.lb_last_error()
+    f = torch.full((9 * 16,), 1.0 / 9.0, dtype=torch.float64, device="cuda")
+    assert lb.lb_reduce_noalloc(0, dims, f.data_ptr(), host.ctypes.data, lib.MEM["device_f64"], out, None) == 1
+    rc = lb.lb_reduce_noalloc(0, dims, f.data_ptr(), None, lib.MEM["device_f64"], out, None)
+    assert rc == 0 and out[0] == pytest.approx(16.0, rel=1e-15)
