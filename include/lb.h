@@ -95,8 +95,9 @@ typedef enum {
 } lb_collision;
 
 /* Storage of the populations in device memory. Arithmetic is FP64 for LB_F64 and
- * FP32 otherwise. The half types store the shifted value f_i - w_i, rounded to
- * nearest even, and add w_i back on load. */
+ * FP32 otherwise. LB_F32 and the half types store the shifted value f_i - w_i (the
+ * deviation from rest, 10 to 40 times smaller than f_i near rest, so its rounding is that
+ * much smaller), rounded to nearest even; LB_F64 stores f_i. Every accessor exposes f_i. */
 typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16_SHIFTED = 2, LB_BF16_SHIFTED = 3 } lb_storage;
 
 /* LB_LAYOUT_AB: two population buffers, one fused pull-stream + collide launch per
@@ -128,9 +129,12 @@ typedef struct {
     int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
                              lb_step_adjoint can run backwards (AB layout only); 0 = off */
     int learned_tc;       /* LB_LEARNED_MRT(3), FP32/FP16/BF16 storage: 1 = evaluate the network's
-                             layers on the tensor cores with BF16 operands and FP32
-                             accumulation (an inference option: lb_step_adjoint and training use
-                             the FP32 network); 0 (default) = FP32 arithmetic throughout */
+                             layers with single BF16 operands and the hardware tanh (an inference
+                             option: lb_step_adjoint and training use the default path); 0
+                             (default) = the FP32 network: its matrix products on the tensor cores,
+                             each operand split into two FP16 terms and multiplied as
+                             hi.hi + hi.lo + lo.hi (about 2^-21 relative; operands scaled by
+                             powers of two into FP16 range), an FP32 tanh, FP32 everything else */
     int graphs;           /* 1 (default): lb_step(n >= 2) without checkpoints captures two steps once
                              into a CUDA graph and replays it (one launch per pair of steps instead
                              of one per kernel; same kernels, same results); 0 = direct launches */

@@ -75,6 +75,7 @@ struct lb_ctx {
     void* wall_u = nullptr;            // wall velocity [D][plane], arithmetic type
     std::vector<double> net;           // learned network (805 or 545 values), passed to kernels by value
     void* tc_table = nullptr;          // learned_tc: packed BF16 weight fragments on the device
+    void* x3_table = nullptr;          // learned, FP32 arithmetic: split BF16 weight fragments (device)
     unsigned* status = nullptr;
     double* partials = nullptr;
     int64_t partials_cap = 0;
@@ -176,6 +177,7 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     a.status = c->status;
     a.stream = c->stream;
     a.tc_table = c->tc_table;
+    a.x3_table = c->x3_table;
     return a;
 }
 
@@ -431,8 +433,8 @@ void lb_destroy(lb_ctx* c)
     cudaStreamSynchronize(c->stream);
     if (c->cycle) cudaGraphExecDestroy(c->cycle);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->status, c->partials, c->dsmall, c->lam[0], c->lam[1],
-                    c->gF, c->gtheta, c->links, c->wall_u, c->sc_spec, c->sc_small, c->sc_du};
+    void* ptrs[] = {c->ab[0], c->ab[1], c->F, c->tc_table, c->x3_table, c->status, c->partials, c->dsmall,
+                    c->lam[0], c->lam[1], c->gF, c->gtheta, c->links, c->wall_u, c->sc_spec, c->sc_small, c->sc_du};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->ckpt)
@@ -527,6 +529,16 @@ lb_status lb_set_mlp(lb_ctx* c, const void* params, int64_t n, lb_mem m)
         else lb::learned_tc_pack(v.data(), tab.data());
         // the previous table may still be read by queued steps: order the copy on the stream
         LB_CUDA(c, cudaMemcpyAsync(c->tc_table, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream), "weight table");
+        LB_CUDA(c, cudaStreamSynchronize(c->stream), "weight table");
+    }
+    if (c->opt.storage != LB_F64) {
+        // the FP32 arithmetic's tensor-core kernels read the weights split into BF16 terms
+        const bool three = c->coll == LB_LEARNED_MRT3;
+        const size_t bytes = lb::learned_x3_table_bytes(three);
+        if (!c->x3_table && (s = alloc(c, &c->x3_table, (int64_t)bytes, "split weight table")) != LB_OK) return s;
+        std::vector<unsigned char> tab(bytes);
+        lb::learned_x3_pack(v.data(), three, tab.data());
+        LB_CUDA(c, cudaMemcpyAsync(c->x3_table, tab.data(), bytes, cudaMemcpyHostToDevice, c->stream), "weight table");
         LB_CUDA(c, cudaStreamSynchronize(c->stream), "weight table");
     }
     c->net.swap(v);
@@ -1085,7 +1097,7 @@ lb_status lb_step_adjoint(lb_ctx* c, const void* lamT, int64_t n, void* lam0, vo
     int64_t nblk = 0;
     const int ntheta = net_theta(c->coll);
     if (is_learned(c->coll)) {
-        nblk = lb::learned_adj_partial_count(c->g);
+        nblk = lb::learned_adj_partial_count(c->g, c->opt.storage, c->sms, c->coll == LB_LEARNED_MRT3);
         const int64_t need = nblk * ntheta;
         // block partials, then the chunk sums of the deterministic reduction
         const int64_t bytes = need * real_bytes(c->opt.storage) + lb::learned_theta_chunk_doubles() * 8 + 256;

@@ -60,24 +60,30 @@ LB_HD constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); 
 
 // ----------------------------------------------------------------------------
 // Storage types. Real is the arithmetic type (FP64 only for FP64 storage).
-// Half types hold f_i - w_i.
+// FP32 and the half types hold f_i - w_i ("shifted"): near rest the deviation is 10 to 40
+// times smaller than f_i, so its rounding in storage is that much smaller too (for FP32
+// this is the difference between about 3e-8 and 1e-9 absolute per population and step,
+// which the non-equilibrium parts of f, often 1e-4 of it, feel directly). FP64 holds f_i.
 // ----------------------------------------------------------------------------
 template <class T> struct Store;
 template <> struct Store<double> {
     using Real = double;
     static constexpr bool shifted = false;
+    static constexpr bool half = false;
     LB_DEV static double load(const double* p) { return *p; }
     LB_DEV static void store(double* p, double v) { *p = v; }
 };
 template <> struct Store<float> {
     using Real = float;
-    static constexpr bool shifted = false;
+    static constexpr bool shifted = true;
+    static constexpr bool half = false;
     LB_DEV static float load(const float* p) { return *p; }
     LB_DEV static void store(float* p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
     using Real = float;
     static constexpr bool shifted = true;
+    static constexpr bool half = true;
     LB_DEV static float load(const __half* p) { return __half2float(*p); }
     LB_DEV static void store(__half* p, float v) { *p = __float2half_rn(v); }
     LB_DEV static void store(__half* p, double v) { *p = __double2half(v); }
@@ -85,6 +91,7 @@ template <> struct Store<__half> {
 template <> struct Store<__nv_bfloat16> {
     using Real = float;
     static constexpr bool shifted = true;
+    static constexpr bool half = true;
     LB_DEV static float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     LB_DEV static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     LB_DEV static void store(__nv_bfloat16* p, double v) { *p = __double2bfloat16(v); }
@@ -92,8 +99,8 @@ template <> struct Store<__nv_bfloat16> {
 
 // Collision arithmetic works on deviations from rest, delta_i = f_i - w_i: the
 // moment sums then add small numbers (rho - 1 = sum delta, j = sum c delta) and
-// FP32 keeps its relative precision. Unshifted storage converts on load/store;
-// shifted (half) storage holds delta itself.
+// FP32 keeps its relative precision. Unshifted (FP64) storage converts on load/store;
+// shifted storage holds delta itself.
 template <class St, class T>
 LB_DEV typename Store<T>::Real load_pop(const T* p, int i)
 {

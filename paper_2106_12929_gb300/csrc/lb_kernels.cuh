@@ -214,7 +214,7 @@ template <class St, class T, int COLL, bool FORCE, int MODE, bool WALLS = false>
 __global__ void __launch_bounds__(128) k_update_quad(const T* src, T* dst, const float* F, Geom g, Relax<float> rx,
                                                      unsigned* status)
 {
-    static_assert(Store<T>::shifted, "four-node kernel is for half-precision storage");
+    static_assert(Store<T>::half, "four-node kernel is for half-precision storage");
     constexpr int S = sizeof(T);
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x0 >= g.nx) return;
@@ -662,10 +662,10 @@ inline int update_shape(const OpArgs& a)
         // node make four nodes too many live registers, and with a body force (the Guo source
         // takes the four-node kernel to 168 registers: D3Q19 FP16 at 256^3 runs 64.0 GLUPS
         // with two nodes per thread, 60.5 with four)
-        const bool quad_ok = Store<T>::shifted && !(St::Q == 27 && COLL == KBC) && !a.force;
+        const bool quad_ok = Store<T>::half && !(St::Q == 27 && COLL == KBC) && !a.force;
         npt = small_grid(a) ? 1 : (quad_ok ? 4 : 2);
     }
-    if (npt == 4 && !(Store<T>::shifted && a.g.nx % 4 == 0)) npt = 2;
+    if (npt == 4 && !(Store<T>::half && a.g.nx % 4 == 0)) npt = 2;
     if (npt == 2 && a.g.nx % 2 != 0) npt = 1;
     return npt;
 }
@@ -679,7 +679,7 @@ cudaError_t launch_update(const OpArgs& a)
     const R* F = (const R*)a.F;
     const Relax<R> rx = relax_of<R>(a);
     const int npt = update_shape<St, T, COLL>(a);
-    if constexpr (Store<T>::shifted) {
+    if constexpr (Store<T>::half) {
         if (npt == 4) {
             // four nodes per thread for half storage
             const int quads = a.g.nx / 4;

@@ -18,8 +18,7 @@
 // the constant bank and feed the FMAs directly.
 #include <cstring>
 
-#include "lb_collide.cuh"
-#include "lb_learned.cuh"
+#include "lb_learned_node.cuh"
 
 namespace lb {
 
@@ -27,74 +26,6 @@ template <class R>
 struct Net {
     R v[kNetValues];
 };
-
-// Hermite higher-moment polynomials on D2Q9 and their weighted norms
-LB_HD constexpr double h6(int i) { return (c2(i, 0) * c2(i, 0) - 1.0 / 3.0) * c2(i, 1); }
-LB_HD constexpr double h7(int i) { return c2(i, 0) * (c2(i, 1) * c2(i, 1) - 1.0 / 3.0); }
-LB_HD constexpr double h8(int i) { return (c2(i, 0) * c2(i, 0) - 1.0 / 3.0) * (c2(i, 1) * c2(i, 1) - 1.0 / 3.0); }
-constexpr double kN6 = 2.0 / 27.0, kN7 = 2.0 / 27.0, kN8 = 4.0 / 81.0;
-
-// Activation: in FP32 the hardware tanh (PTX tanh.approx.f32, one SFU instruction,
-// max relative error about 2^-11) -- the forward pass, the adjoint (which uses
-// 1 - tanh^2 of the same values) and training all see the same function. FP64 keeps
-// the accurate tanh for the gradient checks against the oracle.
-template <class R> LB_DEV R act_tanh(R a);
-template <> LB_DEV float act_tanh<float>(float a)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(a));
-    return y;
-}
-template <> LB_DEV double act_tanh<double>(double a) { return tanh(a); }
-template <class R> LB_DEV R act_exp(R a);
-template <> LB_DEV float act_exp<float>(float a) { return expf(a); }
-template <> LB_DEV double act_exp<double>(double a) { return exp(a); }
-
-// The moments of one node that both networks read: density and velocity, equilibrium,
-// non-equilibrium stress Pi and higher moments g6, g7, g8.
-template <class R>
-struct LearnedMoments {
-    NodeMoments<D2Q9, R> m;
-    R feq[9];
-    R pxx, pxy, pyy, g6, g7, g8;
-};
-
-// Everything the forward pass of one node computes (kept for the adjoint).
-template <class R>
-struct LearnedNode : LearnedMoments<R> {
-    R x[kNetIn];
-    R h1[kNetHidden], h2[kNetHidden];
-    R z, ez, omg;
-};
-
-// Moments, equilibrium, stress and higher moments, and the six network inputs of one node.
-template <class R>
-LB_DEV void learned_inputs(const R* f, LearnedMoments<R>& s, R* I)
-{
-    R Fz[3] = {R(0), R(0), R(0)};
-    s.m = node_moments<D2Q9, false>(f, Fz);
-    equilibrium<D2Q9>(s.m, s.feq);
-    R pxx = R(0), pxy = R(0), pyy = R(0), g6 = R(0), g7 = R(0), g8 = R(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const R d = f[i] - s.feq[i];
-        const int cx = c2(i, 0), cy = c2(i, 1);
-        if (cx) pxx += d;
-        if (cy) pyy += d;
-        if (cx && cy) pxy += (cx == cy) ? d : -d;
-        g6 += R(h6(i)) * d;
-        g7 += R(h7(i)) * d;
-        g8 += R(h8(i)) * d;
-    }
-    s.pxx = pxx; s.pxy = pxy; s.pyy = pyy; s.g6 = g6; s.g7 = g7; s.g8 = g8;
-    const R ux = s.m.ux, uy = s.m.uy;
-    I[0] = s.m.rho1;
-    I[1] = R(3) * (ux * ux + uy * uy);
-    I[2] = R(3) * (pxx + pyy);
-    I[3] = R(9) * (pxx * pxx + R(2) * pxy * pxy + pyy * pyy);
-    I[4] = R(9) * (ux * ux * pxx + R(2) * ux * uy * pxy + uy * uy * pyy);
-    I[5] = g6 * g6 * R(1.0 / kN6) + g7 * g7 * R(1.0 / kN7) + g8 * g8 * R(1.0 / kN8);
-}
 
 template <class R>
 LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
@@ -133,25 +64,6 @@ LB_DEV void learned_forward(const R* f, const Net<R>& net, LearnedNode<R>& s)
     s.omg = recip(s.ez + R(0.5));  // correctly rounded, as 1 / x
 }
 
-template <class R>
-LB_DEV void learned_post(const LearnedNode<R>& s, R omega, R* f)
-{
-    const R ks = R(4.5) * (R(1) - omega);
-    const R kg = R(1) - s.omg;
-    const R tr3 = (s.pxx + s.pyy) * R(1.0 / 3.0);
-    const R q6 = s.g6 * R(1.0 / kN6), q7 = s.g7 * R(1.0 / kN7), q8 = s.g8 * R(1.0 / kN8);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = c2(i, 0), cy = c2(i, 1);
-        R qp = -tr3;
-        if (cx) qp += s.pxx;
-        if (cy) qp += s.pyy;
-        if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
-        const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
-        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + kg * ghost);
-    }
-}
-
 template <class T, int MODE>
 __global__ void __launch_bounds__(128) k_learned_update(const T* src, T* dst, Geom g, typename Store<T>::Real omega,
                                                         unsigned* status, const Net<typename Store<T>::Real> net)
@@ -166,7 +78,7 @@ __global__ void __launch_bounds__(128) k_learned_update(const T* src, T* dst, Ge
     load_node<D2Q9, MODE>(src, g, nb, n, f);
     LearnedNode<R> s;
     learned_forward(f, net, s);
-    learned_post(s, omega, f);
+    learned_post(s, s.omg, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
 }
@@ -392,7 +304,7 @@ __global__ void __launch_bounds__(128) k_learned_update_tc(const T* src, T* dst,
     s.ez = expf(z);
     s.omg = recip(s.ez + 0.5f);
     if (!valid) return;
-    learned_post(s, omega, f);
+    learned_post(s, s.omg, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(s.m.rho > 0.f && s.m.rho < 1e30f)) atomicOr(status, 1u);
 }
@@ -537,100 +449,6 @@ LB_DEV void block_theta_grad(AdjShared<R>& sh, int t, R* out)
     }
 }
 
-// Cotangents of the per-node quantities of the learned collision, built up by the adjoint:
-// density, velocity, non-equilibrium stress and higher moments; q_g are the adjoint's
-// projections sum_i mu_i w_i H_g(c_i) / |H_g|^2_w onto the higher rows.
-template <class R>
-struct LearnedCot {
-    R grho, gux, guy, gPxx, gPxy, gPyy, gg6, gg7, gg8;
-    R q6, q7, q8;
-};
-
-// The paths through the equilibrium and the stress rows of f*; the higher rows' terms
-// (which depend on the network) are added by the caller.
-template <class R>
-LB_DEV LearnedCot<R> learned_adj_head(const LearnedMoments<R>& s, const R* mu, R omega)
-{
-    const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
-    // sums of mu w over the basis
-    R smw = R(0), smwcx = R(0), smwcy = R(0), smwcucx = R(0), smwcucy = R(0), grho = R(0);
-    R sxx = R(0), syy = R(0), sxy = R(0), s6 = R(0), s7 = R(0), s8 = R(0);
-    const R base = R(1) - R(1.5) * (ux * ux + uy * uy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const R mw = mu[i] * R(D2Q9::w(i));
-        const int cx = c2(i, 0), cy = c2(i, 1);
-        const R cu = cdotu<D2Q9>(i, ux, uy, R(0));
-        grho += mw * (base + cu * (R(3) + R(4.5) * cu));
-        smw += mw;
-        smwcx += cx * mw;
-        smwcy += cy * mw;
-        smwcucx += cx * mw * cu;
-        smwcucy += cy * mw * cu;
-        if (cx) sxx += mw;
-        if (cy) syy += mw;
-        if (cx && cy) sxy += (cx == cy) ? mw : -mw;
-        s6 += R(h6(i)) * mw;
-        s7 += R(h7(i)) * mw;
-        s8 += R(h8(i)) * mw;
-    }
-    LearnedCot<R> c;
-    c.grho = grho;
-    // equilibrium path: d f^eq / d rho, d f^eq / d u
-    c.gux = rho * (R(3) * smwcx + R(9) * smwcucx - R(3) * ux * smw);
-    c.guy = rho * (R(3) * smwcy + R(9) * smwcucy - R(3) * uy * smw);
-    // stress path: cotangent of (Pxx, Pxy, Pyy) from 4.5 (1 - w_s) w_i Q_i : Pi
-    const R ks = R(4.5) * (R(1) - omega);
-    c.gPxx = ks * (sxx - smw * R(1.0 / 3.0));
-    c.gPyy = ks * (syy - smw * R(1.0 / 3.0));
-    c.gPxy = R(2) * ks * sxy;
-    c.q6 = s6 * R(1.0 / kN6);
-    c.q7 = s7 * R(1.0 / kN7);
-    c.q8 = s8 * R(1.0 / kN8);
-    return c;
-}
-
-// Back through the six network inputs (cotangent gI of the unstandardised invariants) and
-// the moments to lambda_i = d(mu . f*)/d f_i, written to lam_out[i][n].
-template <class R>
-LB_DEV void learned_adj_tail(const LearnedMoments<R>& s, LearnedCot<R> c, const R* gI, R* lam_out, int64_t plane,
-                             int n)
-{
-    const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
-    R grho = c.grho, gux = c.gux, guy = c.guy, gPxx = c.gPxx, gPyy = c.gPyy, gPxy = c.gPxy;
-    R gg6 = c.gg6, gg7 = c.gg7, gg8 = c.gg8;
-    grho += gI[0];
-    gux += R(6) * ux * gI[1];
-    guy += R(6) * uy * gI[1];
-    gPxx += R(3) * gI[2] + R(18) * s.pxx * gI[3] + R(9) * ux * ux * gI[4];
-    gPyy += R(3) * gI[2] + R(18) * s.pyy * gI[3] + R(9) * uy * uy * gI[4];
-    gPxy += R(36) * s.pxy * gI[3] + R(18) * ux * uy * gI[4];
-    gux += R(18) * (ux * s.pxx + uy * s.pxy) * gI[4];
-    guy += R(18) * (ux * s.pxy + uy * s.pyy) * gI[4];
-    gg6 += R(2) * s.g6 * R(1.0 / kN6) * gI[5];
-    gg7 += R(2) * s.g7 * R(1.0 / kN7) * gI[5];
-    gg8 += R(2) * s.g8 * R(1.0 / kN8) * gI[5];
-    // Pi = sum c c f - rho u u - rho I/3
-    grho -= gPxx * (ux * ux + R(1.0 / 3.0)) + gPxy * ux * uy + gPyy * (uy * uy + R(1.0 / 3.0));
-    gux -= rho * (R(2) * ux * gPxx + uy * gPxy);
-    guy -= rho * (ux * gPxy + R(2) * uy * gPyy);
-    const R inv = recip(rho);
-    const R gdotu = gux * ux + guy * uy;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = c2(i, 0), cy = c2(i, 1);
-        // direct paths: Pi (c c) and the higher moments (H_g); the equilibrium
-        // term of f* has no direct dependence on f
-        R v = R(0);
-        if (cx) v += gPxx;
-        if (cy) v += gPyy;
-        if (cx && cy) v += (cx == cy) ? gPxy : -gPxy;
-        v += R(h6(i)) * gg6 + R(h7(i)) * gg7 + R(h8(i)) * gg8;
-        v += grho + (cdotu<D2Q9>(i, gux, guy, R(0)) - gdotu) * inv;
-        lam_out[(int64_t)i * plane + n] = v;
-    }
-}
-
 template <class T>
 __global__ void __launch_bounds__(kAdjBlock, 4) k_learned_adjoint(const T* state, const typename Store<T>::Real* lam_in,
                                                                typename Store<T>::Real* lam_out, Geom g,
@@ -726,16 +544,6 @@ struct Net3 {
     R v[kNet3Values];
 };
 
-// higher row set by output o (0: row (cx^2 - 1/3) cy, 1: cx (cy^2 - 1/3), 2: the fourth-order row)
-LB_HD constexpr int net3_row(int o) { return o == 0 ? 2 : o - 1; }
-
-template <class R>
-struct Learned3Node : LearnedMoments<R> {
-    R x[kNetIn];
-    R h[kNet3Hidden];
-    R ez[3], omg[3];  // per higher row, in row order
-};
-
 template <class R>
 LB_DEV void learned3_forward(const R* f, const Net3<R>& net, Learned3Node<R>& s)
 {
@@ -768,26 +576,6 @@ LB_DEV void learned3_forward(const R* f, const Net3<R>& net, Learned3Node<R>& s)
     }
 }
 
-template <class R>
-LB_DEV void learned3_post(const Learned3Node<R>& s, R omega, R* f)
-{
-    const R ks = R(4.5) * (R(1) - omega);
-    const R tr3 = (s.pxx + s.pyy) * R(1.0 / 3.0);
-    const R q6 = (R(1) - s.omg[0]) * s.g6 * R(1.0 / kN6);
-    const R q7 = (R(1) - s.omg[1]) * s.g7 * R(1.0 / kN7);
-    const R q8 = (R(1) - s.omg[2]) * s.g8 * R(1.0 / kN8);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = c2(i, 0), cy = c2(i, 1);
-        R qp = -tr3;
-        if (cx) qp += s.pxx;
-        if (cy) qp += s.pyy;
-        if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
-        const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
-        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + ghost);
-    }
-}
-
 template <class T, int MODE>
 __global__ void __launch_bounds__(128) k_learned3_update(const T* src, T* dst, Geom g, typename Store<T>::Real omega,
                                                          unsigned* status, const Net3<typename Store<T>::Real> net)
@@ -802,7 +590,7 @@ __global__ void __launch_bounds__(128) k_learned3_update(const T* src, T* dst, G
     load_node<D2Q9, MODE>(src, g, nb, n, f);
     Learned3Node<R> s;
     learned3_forward(f, net, s);
-    learned3_post(s, omega, f);
+    learned3_post(s, s.omg, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
 }
@@ -933,7 +721,7 @@ __global__ void __launch_bounds__(128) k_learned3_update_tc(const T* src, T* dst
         s.omg[r] = recip(s.ez[r] + 0.5f);
     }
     if (!valid) return;
-    learned3_post(s, omega, f);
+    learned3_post(s, s.omg, omega, f);
     store_node<D2Q9, MODE>(dst, g, nb, n, f);
     if (!(s.m.rho > 0.f && s.m.rho < 1e30f)) atomicOr(status, 1u);
 }
@@ -1114,43 +902,43 @@ template <class T>
 static cudaError_t launch_learned(const OpArgs& a, const double* netv, bool tc)
 {
     using R = typename Store<T>::Real;
-    const Net<R> net = make_net<R>(netv);
     const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
     if constexpr (sizeof(R) == 4) {
-        if (tc && a.op == OP_UPDATE) {
-            if (!a.tc_table) return cudaErrorInvalidValue;
-            const uint32_t* tab = (const uint32_t*)a.tc_table;
-            const T* src = (const T*)a.src;
-            T* dst = (T*)a.dst;
-            if (a.mode == AB)
-                k_learned_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-            else if (a.mode == AA_EVEN)
-                k_learned_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
-                                                                         tab);
-            else
-                k_learned_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
-                                                                        tab);
-            return cudaGetLastError();
-        }
-    }
-    if (a.op == OP_UPDATE) {
+        if (!(tc && a.op == OP_UPDATE)) return run_learned_x3(a, false);
+        if (!a.tc_table) return cudaErrorInvalidValue;
+        const Net<float> net = make_net<float>(netv);
+        const uint32_t* tab = (const uint32_t*)a.tc_table;
         const T* src = (const T*)a.src;
         T* dst = (T*)a.dst;
-        if (a.mode == AB) k_learned_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        if (a.mode == AB)
+            k_learned_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
         else if (a.mode == AA_EVEN)
-            k_learned_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
-        else k_learned_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            k_learned_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
+        else
+            k_learned_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
         return cudaGetLastError();
+    } else {
+        const Net<R> net = make_net<R>(netv);
+        if (a.op == OP_UPDATE) {
+            const T* src = (const T*)a.src;
+            T* dst = (T*)a.dst;
+            if (a.mode == AB) k_learned_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            else if (a.mode == AA_EVEN)
+                k_learned_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            else k_learned_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            return cudaGetLastError();
+        }
+        if (a.op == OP_ADJ_STEP) {
+            const size_t smem = sizeof(AdjShared<R>);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_learned_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_learned_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
+                                                             (R)a.omega, (R*)a.gth, net);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
     }
-    if (a.op == OP_ADJ_STEP) {
-        const size_t smem = sizeof(AdjShared<R>);
-        cudaError_t e = cudaFuncSetAttribute(k_learned_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_learned_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
-                                                         (R)a.omega, (R*)a.gth, net);
-        return cudaGetLastError();
-    }
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc)
@@ -1177,44 +965,43 @@ template <class T>
 static cudaError_t launch_learned3(const OpArgs& a, const double* netv, bool tc)
 {
     using R = typename Store<T>::Real;
-    const Net3<R> net = make_net3<R>(netv);
     const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
     if constexpr (sizeof(R) == 4) {
-        if (tc && a.op == OP_UPDATE) {
-            if (!a.tc_table) return cudaErrorInvalidValue;
-            const uint32_t* tab = (const uint32_t*)a.tc_table;
-            const T* src = (const T*)a.src;
-            T* dst = (T*)a.dst;
-            if (a.mode == AB)
-                k_learned3_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-            else if (a.mode == AA_EVEN)
-                k_learned3_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
-                                                                          tab);
-            else
-                k_learned3_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net,
-                                                                         tab);
-            return cudaGetLastError();
-        }
-    }
-    if (a.op == OP_UPDATE) {
+        if (!(tc && a.op == OP_UPDATE)) return run_learned_x3(a, true);
+        if (!a.tc_table) return cudaErrorInvalidValue;
+        const Net3<float> net = make_net3<float>(netv);
+        const uint32_t* tab = (const uint32_t*)a.tc_table;
         const T* src = (const T*)a.src;
         T* dst = (T*)a.dst;
-        if (a.mode == AB) k_learned3_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+        if (a.mode == AB)
+            k_learned3_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
         else if (a.mode == AA_EVEN)
-            k_learned3_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
-        else k_learned3_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            k_learned3_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
+        else
+            k_learned3_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
         return cudaGetLastError();
+    } else {
+        const Net3<R> net = make_net3<R>(netv);
+        if (a.op == OP_UPDATE) {
+            const T* src = (const T*)a.src;
+            T* dst = (T*)a.dst;
+            if (a.mode == AB) k_learned3_update<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            else if (a.mode == AA_EVEN)
+                k_learned3_update<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            else k_learned3_update<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (R)a.omega, a.status, net);
+            return cudaGetLastError();
+        }
+        if (a.op == OP_ADJ_STEP) {
+            const size_t smem = sizeof(Adj3Shared<R>);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_learned3_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_learned3_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
+                                                              (R)a.omega, (R*)a.gth, net);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
     }
-    if (a.op == OP_ADJ_STEP) {
-        const size_t smem = sizeof(Adj3Shared<R>);
-        cudaError_t e =
-            cudaFuncSetAttribute(k_learned3_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_learned3_adjoint<T><<<gr, bl, smem, a.stream>>>((const T*)a.src, (const R*)a.lam_in, (R*)a.lam_out, a.g,
-                                                          (R)a.omega, (R*)a.gth, net);
-        return cudaGetLastError();
-    }
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc)
@@ -1229,8 +1016,9 @@ cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc)
     }
 }
 
-int64_t learned_adj_partial_count(const Geom& g)
+int64_t learned_adj_partial_count(const Geom& g, int storage, int sms, bool three)
 {
+    if (storage != S_F64) return learned_x3_partial_count(g, storage, sms, three);
     return (int64_t)((g.nx + kAdjBlock - 1) / kAdjBlock) * g.ny;
 }
 

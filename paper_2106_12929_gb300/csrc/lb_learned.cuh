@@ -18,8 +18,10 @@ constexpr int kNet3Values = kNet3Theta + 2 * kNetIn;
 static_assert(kNet3Theta == 533, "6-53-3 network has 533 parameters");
 
 // forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
-// net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint)
-// tc = 1: forward step with the network's hidden layers on the tensor cores (BF16 x BF16 -> FP32)
+// net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint).
+// FP64 storage runs the scalar FP64 kernels, the other storage types the tensor-core
+// kernels of the FP32 arithmetic (run_learned_x3); tc = 1: forward step with single BF16
+// operands instead (the learned_tc inference option)
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc = false);
 // the same for the one-hidden-layer network with three outputs (net = kNet3Values doubles)
 cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc = false);
@@ -32,8 +34,15 @@ size_t learned3_tc_table_bytes();
 void learned3_tc_pack(const double* net, void* out);
 // out[6][N] <- the six network inputs (moment invariants) of every node of the state a.src
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
-// number of blocks of the learned adjoint launch (rows of the gradient partials)
-int64_t learned_adj_partial_count(const Geom& g);
+// FP32 arithmetic (FP32 / FP16 / BF16 storage): the networks on the tensor cores with
+// split BF16 operands (lb_learned_x3.cu). Weight table bytes and host packing (once per
+// lb_set_mlp), the forward / adjoint step (a.x3_table), and the rows of its gradient partials.
+size_t learned_x3_table_bytes(bool three);
+void learned_x3_pack(const double* net, bool three, void* out);
+cudaError_t run_learned_x3(const OpArgs& a, bool three);
+int64_t learned_x3_partial_count(const Geom& g, int storage, int sms, bool three);
+// rows of the gradient partials of the learned adjoint launch (blocks of the launch)
+int64_t learned_adj_partial_count(const Geom& g, int storage, int sms, bool three);
 // out[ntheta] (+)= sum over blocks of partials[block][ntheta] (two deterministic passes
 // through `chunk`, learned_theta_chunk_doubles() doubles of scratch; ntheta <= kNetTheta)
 int64_t learned_theta_chunk_doubles();

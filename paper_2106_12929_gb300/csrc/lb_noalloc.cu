@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kNoallocThreads) k_noalloc_partial(const T* f,
         if (n >= N) break;
         R d[St::Q];
 #pragma unroll
-        for (int i = 0; i < St::Q; ++i) d[i] = load_pop<St>(f + (int64_t)i * N + n, i);
+        for (int i = 0; i < St::Q; ++i) d[i] = (R)f[(int64_t)i * N + n] - R(St::w(i));  // caller's f, unshifted
         R Fl[3] = {R(0), R(0), R(0)};
         if constexpr (FORCE) {
             Fl[0] = F[n];

@@ -44,6 +44,7 @@ struct OpArgs {
     void* gF = nullptr;             // adjoint: force gradient accumulator [D][plane], arithmetic type
     void* gth = nullptr;            // learned adjoint: per-block network-gradient partials
     const void* tc_table = nullptr; // learned collision on tensor cores: packed weight table (device)
+    const void* x3_table = nullptr; // learned collision, FP32 arithmetic: split BF16 weight table (device)
     Geom g{};
     double omega = 1.0;
     double rx[3] = {0.0, 0.0, 0.0};  // further constants of the collision (lb_collide.cuh, Relax)

@@ -143,7 +143,9 @@ def test_adjoint_fp64_matches_oracle():
 
 
 def test_adjoint_fp32_parameter_gradient():
-    """FP32 (hardware tanh, about 2^-11 relative) against the FP64 oracle on a 64^2 shear layer."""
+    """FP32 arithmetic (network products on the tensor cores with split BF16 operands, FP32 tanh)
+    against the FP64 oracle on a 64^2 shear layer: relative L2 error of the parameter gradient
+    within the 1e-4 gradient bar."""
     dims, rho, u = lbinputs.shear_layer(64, u0=0.05)
     N = oracle.n_nodes(dims)
     tau = 0.55
@@ -160,8 +162,36 @@ def test_adjoint_fp32_parameter_gradient():
     f0 = oracle.init_eq(NAME, dims, rho, u)
     _, _, ref = oracle.adjoint(NAME, dims, tau, "learned3", f0, n, lamT, mlp=net)
     rel = np.linalg.norm(gth.cpu().numpy() - ref) / np.linalg.norm(ref)
-    print("learned3 FP32 parameter-gradient relative error", rel)  # 2.2e-4 measured on GB300
-    assert rel <= 2e-3
+    print("learned3 FP32 parameter-gradient relative error", rel)
+    assert rel <= 1e-4
+
+
+def test_adjoint_fp32_matches_oracle_elementwise():
+    """lambda_0 and every parameter-gradient entry of the FP32 adjoint against the FP64 oracle,
+    on a grid with more warp tiles than the persistent grid has warps and a ragged last tile."""
+    dims = (1100, 40, 1)
+    N = oracle.n_nodes(dims)
+    tau = 0.6
+    net = net3(tau, seed=8, taus=(0.9, 0.7, 1.3))
+    f0 = near_eq(dims, seed=81)
+    lamT = lbinputs.random_field((9, N), seed=82)
+    n = 6
+    lat = L(NAME, dims, tau, "learned3", storage="f32", record_every=4)
+    lat.set_mlp(net)
+    lat.set_populations(f0)
+    lat.step(n)
+    gth = torch.zeros(533, dtype=torch.float32, device="cuda")
+    lam0 = lat.step_adjoint(torch.tensor(lamT, dtype=torch.float32, device="cuda"), n, grad_theta=gth)
+    f0_32 = f0.astype(np.float32).astype(np.float64)
+    ref_lam, _, ref_th = oracle.adjoint(NAME, dims, tau, "learned3", f0_32, n,
+                                        lamT.astype(np.float32).astype(np.float64), mlp=net)
+    got_th, got_lam = gth.cpu().numpy().astype(np.float64), lam0.cpu().numpy().astype(np.float64)
+    err_th = np.max(np.abs(got_th - ref_th)) / np.max(np.abs(ref_th))
+    err_lam = np.max(np.abs(got_lam - ref_lam)) / np.max(np.abs(ref_lam))
+    print(f"learned3 FP32 adjoint: theta {err_th:.2e}, lambda {err_lam:.2e}")
+    assert err_th <= 1e-4 and err_lam <= 1e-4
+    for lo, hi in ((0, 318), (318, 371), (371, 530), (530, 533)):
+        assert np.max(np.abs(got_th[lo:hi])) > 0.0
 
 
 def test_autograd_parameter_gradient_matches_oracle():

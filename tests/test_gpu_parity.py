@@ -62,7 +62,9 @@ def test_streaming_bit_exact(name, storage, layout):
         N = oracle.n_nodes(dims)
         f0 = lbinputs.random_populations(w, N, seed=3)
         if storage == "f32":
-            f0 = f0.astype(np.float32).astype(np.float64)
+            # FP32 storage holds f - w: values whose deviation is an FP32 number (f = w + that
+            # deviation is then exact in FP64) move through it unchanged
+            f0 = w[:, None] + (f0 - w[:, None]).astype(np.float32).astype(np.float64)
         lat = L(name, dims, 0.8, "none", storage=storage, layout=layout)
         lat.set_populations(f0)
         np.testing.assert_array_equal(gpu_pops(lat), f0)
@@ -318,6 +320,38 @@ def test_learned_adjoint_fp64_matches_oracle():
     ref_lam, _, ref_th = oracle.adjoint(name, dims, tau, "learned", f0, 5, lamT, mlp=net)
     assert np.max(np.abs(lam0.numpy() - ref_lam)) <= 1e-11 * np.max(np.abs(ref_lam))
     assert np.max(np.abs(gth.numpy() - ref_th)) <= 1e-10 * np.max(np.abs(ref_th))
+
+
+@pytest.mark.parametrize("dims", [(131, 24, 1), (1100, 40, 1)])
+def test_learned_adjoint_fp32_matches_oracle(dims):
+    """The FP32 adjoint of the 6-24-24-1 network (the one training runs: network products on the
+    tensor cores with split BF16 operands, FP32 tanh) against the FP64 oracle, element by element
+    on lambda_0 and the parameter gradient. Both grids end in a ragged warp tile; the second has
+    more warp tiles than the persistent grid has warps, so warps sum several tiles."""
+    name = "D2Q9"
+    N = oracle.n_nodes(dims)
+    tau = 0.6
+    net = _net(tau, seed=8)
+    f0 = near_eq(name, dims, seed=71)
+    lamT = lbinputs.random_field((9, N), seed=72)
+    n = 6
+    lat = L(name, dims, tau, "learned", storage="f32", record_every=4)  # a partial last segment
+    lat.set_mlp(net)
+    lat.set_populations(f0)
+    lat.step(n)
+    gth = torch.zeros(793, dtype=torch.float32, device="cuda")
+    lam0 = lat.step_adjoint(torch.tensor(lamT, dtype=torch.float32, device="cuda"), n, grad_theta=gth)
+    f0_32 = f0.astype(np.float32).astype(np.float64)  # the FP32 state starts from f0 rounded
+    ref_lam, _, ref_th = oracle.adjoint(name, dims, tau, "learned", f0_32, n, lamT.astype(np.float32).astype(np.float64),
+                                        mlp=net)
+    got_th, got_lam = gth.cpu().numpy().astype(np.float64), lam0.cpu().numpy().astype(np.float64)
+    err_th = np.max(np.abs(got_th - ref_th)) / np.max(np.abs(ref_th))
+    err_lam = np.max(np.abs(got_lam - ref_lam)) / np.max(np.abs(ref_lam))
+    rel_l2 = np.linalg.norm(got_th - ref_th) / np.linalg.norm(ref_th)
+    print(f"learned FP32 adjoint {dims}: theta max {err_th:.2e} L2 {rel_l2:.2e}, lambda {err_lam:.2e}")
+    assert err_th <= 1e-4 and rel_l2 <= 1e-4 and err_lam <= 1e-4
+    for lo, hi in ((0, 144), (144, 168), (168, 744), (744, 768), (768, 792), (792, 793)):
+        assert np.max(np.abs(got_th[lo:hi])) > 0.0  # every parameter group carries gradient
 
 
 def test_adjoint_fp32_gradient_within_1e_4_of_fp64_reference():

@@ -60,12 +60,14 @@ def test_noalloc_matches_lb_reduce_on_two_calls(stencil, dims, forced):
         assert rc == 0, call
         ref = _with_context(stencil, dims, f, F)
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-15)
-        # FP32 arrays: against lb_reduce of an FP32 context holding the same FP32 values
+        # FP32 arrays: against lb_reduce of an FP32 context given the same values; the context
+        # stores f - w in FP32 (its own rounding of the same numbers), so the two agree to FP32
+        # rounding per node: 1e-6 relative, and 1e-9 N absolute for the near-cancelling momenta
         f32, F32 = f.float(), None if F is None else F.float()
         rc32, got32 = _noalloc(stencil, dims, f32, F32)
         assert rc32 == 0
         ref32 = _with_context(stencil, dims, f32, F32, storage="f32")
-        np.testing.assert_allclose(got32, ref32, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(got32, ref32, rtol=1e-6, atol=1e-9 * N)
 
 
 def test_noalloc_rejects_oversized_grids_and_host_arrays():
@@ -93,8 +95,8 @@ def test_noalloc_matches_lb_reduce_at_many_blocks_and_at_capacity(dims):
         f = w[:, None] * (1.0 + 0.05 * torch.randn((9, N), generator=gen, device="cuda", dtype=torch.float32))
         rc, got = _noalloc("D2Q9", dims, f)
         assert rc == 0
-        ref = _with_context("D2Q9", dims, f, storage="f32")
-        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+        ref = _with_context("D2Q9", dims, f, storage="f32")  # holds f - w in FP32: see above
+        np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-9 * N)
         del f
     torch.cuda.empty_cache()
 
