@@ -447,6 +447,9 @@ def side_measurements(lat_ab, stream, dims, tau, rho_d, u_d, args, glups_ab):
         r = learned_throughput(stream, n=2048, steps=100, tc=tc, net=net)
         out[f"{key}_forward_glups"] = r["forward_glups"]
         out[f"{key}_backward_ms_per_step"] = r["backward_ms_per_step"]
+        if not tc:  # the training path: its forward step is the one the ratio divides by
+            out[f"{key}_backward_over_forward"] = r["backward_over_forward"]
+            out[f"{key}_backward_over_forward_every_state_stored"] = r["backward_over_forward_every_state_stored"]
     # FP32 FMA peak of this GPU for the ALU-bound learned forward kernels: cuBLAS SGEMM with
     # TF32 off (plain FP32 FMAs), 8192^3, best of 5
     peak = fp32_fma_peak(stream)
@@ -523,26 +526,37 @@ def learned_throughput(stream, n=2048, steps=200, tc=False, net="learned"):
     lat.step(5)
     t = time_steps(lat, steps, stream)
     fwd = n * n * steps / t / 1e9
-    # adjoint: recorded run of k steps, then the backward pass
-    k = 50
-    lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
-    lat.step(k)
-    lam = torch.zeros((9, n * n), dtype=torch.float32, device="cuda")
-    lam[0] = 1.0
-    gth = torch.zeros(N_THETA[net], dtype=torch.float32, device="cuda")
-    lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)  # allocates the buffers
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    bwd = e0.elapsed_time(e1) / 1e3
     lat.close()
+    # adjoint: recorded run of k steps, then the backward pass; checkpoints every 10 steps (the
+    # backward pass recomputes 9 of every 10 states) and every step (no recomputation: 50 stored
+    # states, 7.5 GB at 2048^2, which HBM holds easily)
+    k = 50
+    bwd = {}
+    for every in (10, 1):
+        lat = Lattice("D2Q9", dims, tau, net, storage="f32", record_every=every, learned_tc=tc)
+        lat.set_mlp(values)
+        lat.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+        lat.step(k)
+        lam = torch.zeros((9, n * n), dtype=torch.float32, device="cuda")
+        lam[0] = 1.0
+        gth = torch.zeros(N_THETA[net], dtype=torch.float32, device="cuda")
+        lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)  # allocates the buffers
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step_adjoint(lam, k, grad_theta=gth, want_lambda0=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bwd[every] = e0.elapsed_time(e1) / 1e3 / k
+        lat.close()
+    fwd_ms = n * n / fwd / 1e9 * 1e3
     return {"grid": [n, n], "forward_glups": round(fwd, 3),
             "forward_tflops": round(fwd * LEARNED_FLOP_PER_LU[net] / 1e3, 2),
-            "backward_ms_per_step": round(bwd / k * 1e3, 4),
-            "forward_ms_per_step": round(n * n / fwd / 1e9 * 1e3, 4)}
+            "backward_ms_per_step": round(bwd[10] * 1e3, 4),
+            "backward_over_forward": round(bwd[10] * 1e3 / fwd_ms, 3),
+            "backward_ms_per_step_every_state_stored": round(bwd[1] * 1e3, 4),
+            "backward_over_forward_every_state_stored": round(bwd[1] * 1e3 / fwd_ms, 3),
+            "forward_ms_per_step": round(fwd_ms, 4)}
 
 
 def fp32_fma_peak(stream, n=8192, reps=5):

@@ -289,6 +289,25 @@ LB_DEV Nbr make_nbr(const Geom& g, int x, int y, int z)
     return n;
 }
 
+// the same for a 2D grid (nz == 1): the three rows only
+template <int S = 4>
+LB_DEV Nbr make_nbr_2d(const Geom& g, int x, int y)
+{
+    Nbr n;
+    n.x[0] = x == 0 ? g.nx - 1 : x - 1; n.x[1] = x; n.x[2] = x == g.nx - 1 ? 0 : x + 1;
+    n.y[0] = y == 0 ? g.ny - 1 : y - 1; n.y[1] = y; n.y[2] = y == g.ny - 1 ? 0 : y + 1;
+    n.z[0] = n.z[1] = n.z[2] = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n.xo[k] = (int64_t)n.x[k] * S;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t r = (int64_t)n.y[a] * g.nx * S;
+        n.ro[a][0] = n.ro[a][1] = n.ro[a][2] = r;
+    }
+    n.pb = g.plane * S;
+    return n;
+}
+
 template <class T>
 LB_DEV const T* at(const T* buf, const Nbr& nb, int slot, int dx, int dy, int dz)
 {

@@ -46,23 +46,21 @@ LB_DEV float rcp_approx(float a)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
     return y;
 }
+constexpr float kTwoOverLn2 = 2.8853900817779268f;
+// tanh a from t = 2a / ln 2 (callers that form a as a fused multiply-add fold the factor in)
+LB_DEV float tanh_of_t(float t) { return 1.0f - 2.0f * rcp_approx(ex2_approx(t) + 1.0f); }
 template <class R> LB_DEV R act_tanh(R a);
-template <> LB_DEV float act_tanh<float>(float a)
-{
-    const float e = ex2_approx(a * 2.8853900817779268f);  // 2 / ln 2
-    return 1.0f - 2.0f * rcp_approx(e + 1.0f);
-}
+template <> LB_DEV float act_tanh<float>(float a) { return tanh_of_t(a * kTwoOverLn2); }
 template <> LB_DEV double act_tanh<double>(double a) { return tanh(a); }
 template <class R> LB_DEV R act_exp(R a);
 template <> LB_DEV float act_exp<float>(float a) { return expf(a); }
 template <> LB_DEV double act_exp<double>(double a) { return exp(a); }
 
-// The moments of one node that both networks read: density and velocity, equilibrium,
-// non-equilibrium stress Pi and higher moments g6, g7, g8.
+// The moments of one node that both networks read: density and velocity, non-equilibrium
+// stress Pi and higher moments g6, g7, g8.
 template <class R>
 struct LearnedMoments {
     NodeMoments<D2Q9, R> m;
-    R feq[9];
     R pxx, pxy, pyy, g6, g7, g8;
 };
 
@@ -74,27 +72,31 @@ struct LearnedNode : LearnedMoments<R> {
     R z, ez, omg;
 };
 
-// Moments, equilibrium, stress and higher moments, and the six network inputs of one node.
+// Moments, stress and higher moments, and the six network inputs of one node, from the
+// deviations delta_i = f_i - w_i. The second-order equilibrium's moments are closed forms:
+// sum c c (f^eq - w) = rho u u + (rho - 1)/3 I, and its higher Hermite moments vanish, so
+// Pi = sum c c delta - rho u u - (rho - 1)/3 I and g = sum H delta.
 template <class R>
 LB_DEV void learned_inputs(const R* f, LearnedMoments<R>& s, R* I)
 {
     R Fz[3] = {R(0), R(0), R(0)};
     s.m = node_moments<D2Q9, false>(f, Fz);
-    equilibrium<D2Q9>(s.m, s.feq);
-    R pxx = R(0), pxy = R(0), pyy = R(0), g6 = R(0), g7 = R(0), g8 = R(0);
+    R sxx = R(0), sxy = R(0), syy = R(0), g6 = R(0), g7 = R(0), g8 = R(0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const R d = f[i] - s.feq[i];
+        const R d = f[i];
         const int cx = c2(i, 0), cy = c2(i, 1);
-        if (cx) pxx += d;
-        if (cy) pyy += d;
-        if (cx && cy) pxy += (cx == cy) ? d : -d;
+        if (cx) sxx += d;
+        if (cy) syy += d;
+        if (cx && cy) sxy += (cx == cy) ? d : -d;
         g6 += R(h6(i)) * d;
         g7 += R(h7(i)) * d;
         g8 += R(h8(i)) * d;
     }
+    const R ux = s.m.ux, uy = s.m.uy, rho = s.m.rho;
+    const R r3 = s.m.rho1 * R(1.0 / 3.0);
+    const R pxx = sxx - rho * ux * ux - r3, pyy = syy - rho * uy * uy - r3, pxy = sxy - rho * ux * uy;
     s.pxx = pxx; s.pxy = pxy; s.pyy = pyy; s.g6 = g6; s.g7 = g7; s.g8 = g8;
-    const R ux = s.m.ux, uy = s.m.uy;
     I[0] = s.m.rho1;
     I[1] = R(3) * (ux * ux + uy * uy);
     I[2] = R(3) * (pxx + pyy);
@@ -111,6 +113,8 @@ LB_DEV void learned_post(const LearnedMoments<R>& s, R omg, R omega, R* f)
     const R kg = R(1) - omg;
     const R tr3 = (s.pxx + s.pyy) * R(1.0 / 3.0);
     const R q6 = s.g6 * R(1.0 / kN6), q7 = s.g7 * R(1.0 / kN7), q8 = s.g8 * R(1.0 / kN8);
+    R feq[9];
+    equilibrium<D2Q9>(s.m, feq);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = c2(i, 0), cy = c2(i, 1);
@@ -119,7 +123,7 @@ LB_DEV void learned_post(const LearnedMoments<R>& s, R omg, R omega, R* f)
         if (cy) qp += s.pyy;
         if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
         const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
-        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + kg * ghost);
+        f[i] = feq[i] + R(D2Q9::w(i)) * (ks * qp + kg * ghost);
     }
 }
 
@@ -237,6 +241,8 @@ LB_DEV void learned3_post(const LearnedMoments<R>& s, const R* omg, R omega, R* 
     const R q6 = (R(1) - omg[0]) * s.g6 * R(1.0 / kN6);
     const R q7 = (R(1) - omg[1]) * s.g7 * R(1.0 / kN7);
     const R q8 = (R(1) - omg[2]) * s.g8 * R(1.0 / kN8);
+    R feq[9];
+    equilibrium<D2Q9>(s.m, feq);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = c2(i, 0), cy = c2(i, 1);
@@ -245,7 +251,7 @@ LB_DEV void learned3_post(const LearnedMoments<R>& s, const R* omg, R omega, R* 
         if (cy) qp += s.pyy;
         if (cx && cy) qp += (cx == cy) ? R(2) * s.pxy : R(-2) * s.pxy;
         const R ghost = R(h6(i)) * q6 + R(h7(i)) * q7 + R(h8(i)) * q8;
-        f[i] = s.feq[i] + R(D2Q9::w(i)) * (ks * qp + ghost);
+        f[i] = feq[i] + R(D2Q9::w(i)) * (ks * qp + ghost);
     }
 }
 

@@ -179,13 +179,15 @@ LB_DEV Pair ones_t(int lane) { return {(lane >> 2) == 0 ? 0x3C003C00u : 0u, 0u};
 //   w2f: layer 2, B[k][j] = W2[j][k], n-tile t, k-step s
 //   w2b: backward through layer 2, B[k][j] = W2[k][j] (k: layer-2 unit, j: layer-1 unit)
 //   w1b: backward through layer 1, B[j][m] = W1[j][m] (m: input, one n-tile), k-step s
+// Biases b1t, b2t are the hidden layers' biases times 2 / ln 2 (tanh_of_t takes that
+// argument); iw2t = iw2 2 / ln 2.
 struct Tab1 {
     uint32_t w1f[3][2][32];
     uint32_t w2f[3][2][2][2][32];
     uint32_t w2b[3][2][2][2][32];
     uint32_t w1b[2][2][2][32];
-    float b1[24], b2[24], w3[24], shift[6], scale[6];
-    float b3, iw1, iw2, pad;
+    float b1t[24], b2t[24], w3[24], shift[6], scale[6];
+    float b3, iw1, iw2, iw2t;
 };
 // 6-53-3 (hidden units padded to 56, outputs to 8):
 //   w1f: B[k][j] = W1[j][k] (k < 6), n-tile t < 7
@@ -197,7 +199,7 @@ struct Tab3 {
     uint32_t w2f[4][2][2][32];
     uint32_t w2b[7][2][32];
     uint32_t w1b[4][2][2][32];
-    float b1[56], b2[8], shift[6], scale[6];
+    float b1t[56], b2[8], shift[6], scale[6];  // b1t = b1 2 / ln 2
     float iw1, iw2, pad[2];
 };
 static_assert(sizeof(Tab1) % 16 == 0 && sizeof(Tab3) % 16 == 0, "tables copy as 16-byte vectors");
@@ -267,8 +269,8 @@ void pack1(const double* v, Tab1& t)
             for (int r = 0; r < 2; ++r) put(&t.w1b[s][r][0][0], lane, w1b, 16 * s + 8 * r + 2 * q, g, s1);
     }
     for (int k = 0; k < 24; ++k) {
-        t.b1[k] = (float)b1[k];
-        t.b2[k] = (float)b2[k];
+        t.b1t[k] = (float)b1[k] * kTwoOverLn2;
+        t.b2t[k] = (float)b2[k] * kTwoOverLn2;
         t.w3[k] = (float)W3[k];
     }
     for (int k = 0; k < 6; ++k) {
@@ -278,6 +280,7 @@ void pack1(const double* v, Tab1& t)
     t.b3 = (float)b3[0];
     t.iw1 = (float)(1.0 / s1);
     t.iw2 = (float)(1.0 / s2);
+    t.iw2t = t.iw2 * kTwoOverLn2;
 }
 
 void pack3(const double* v, Tab3& t)
@@ -307,7 +310,7 @@ void pack3(const double* v, Tab3& t)
                 put(&t.w1b[s][r][0][0], lane, w1b, 16 * s + 8 * r + 2 * q, g, s1);
             }
     }
-    for (int k = 0; k < 56; ++k) t.b1[k] = k < H ? (float)b1[k] : 0.f;
+    for (int k = 0; k < 56; ++k) t.b1t[k] = k < H ? (float)b1[k] * kTwoOverLn2 : 0.f;
     for (int k = 0; k < 8; ++k) t.b2[k] = k < 3 ? (float)b2[k] : 0.f;
     for (int k = 0; k < 6; ++k) {
         t.shift[k] = (float)shift[k];
@@ -336,14 +339,15 @@ struct TileNode {
     Nbr nb;
 };
 template <class T>
-LB_DEV TileNode tile_node(const Geom& g, int64_t wt, int ntx, int lane)
+LB_DEV TileNode tile_node(const Geom& g, unsigned wt, unsigned ntx, int lane)
 {
     TileNode t;
-    t.y = (int)(wt / ntx);
-    t.x = (int)(wt % ntx) * 32 + lane;
+    const unsigned y = wt / ntx;
+    t.y = (int)y;
+    t.x = (int)(wt - y * ntx) * 32 + lane;
     t.valid = t.x < g.nx;
     const int xs = t.valid ? t.x : 0;
-    t.nb = make_nbr<sizeof(T)>(g, xs, t.y, 0);
+    t.nb = make_nbr_2d<sizeof(T)>(g, xs, t.y);
     t.n = xs + g.nx * t.y;
     return t;
 }
@@ -397,8 +401,8 @@ LB_DEV float to_node(const float* v, int lane)
 
 // ---------------------------------------------------------------- 6-24-24-1
 // The network of row tile m: h1, h2 (accumulator layout) and the partial output sums of rows
-// g and g + 8 over the lane's columns; kx = 1 / (input scale x W1 scale).
-LB_DEV void net1_forward(const Tab1& tb, const AFrag& ax, float kx, int lane, float (*h1)[4], float (*h2)[4],
+// g and g + 8 over the lane's columns; kxt = 2 / ln 2 / (input scale x W1 scale).
+LB_DEV void net1_forward(const Tab1& tb, const AFrag& ax, float kxt, int lane, float (*h1)[4], float (*h2)[4],
                          float& z0, float& z1)
 {
     const int q = lane & 3;
@@ -406,11 +410,11 @@ LB_DEV void net1_forward(const Tab1& tb, const AFrag& ax, float kx, int lane, fl
     for (int t = 0; t < 3; ++t) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         mma3(c, ax, b_load0(&tb.w1f[t][0][0], lane));
-        const float b0 = tb.b1[8 * t + 2 * q], b1 = tb.b1[8 * t + 2 * q + 1];
-        h1[t][0] = act_tanh(fmaf(c[0], kx, b0));
-        h1[t][1] = act_tanh(fmaf(c[1], kx, b1));
-        h1[t][2] = act_tanh(fmaf(c[2], kx, b0));
-        h1[t][3] = act_tanh(fmaf(c[3], kx, b1));
+        const float b0 = tb.b1t[8 * t + 2 * q], b1 = tb.b1t[8 * t + 2 * q + 1];
+        h1[t][0] = tanh_of_t(fmaf(c[0], kxt, b0));
+        h1[t][1] = tanh_of_t(fmaf(c[1], kxt, b1));
+        h1[t][2] = tanh_of_t(fmaf(c[2], kxt, b0));
+        h1[t][3] = tanh_of_t(fmaf(c[3], kxt, b1));
     }
     const AFrag a0 = a_from_c<3>(h1, 0), a1 = a_from_c<3>(h1, 1);
     z0 = 0.f;
@@ -420,11 +424,11 @@ LB_DEV void net1_forward(const Tab1& tb, const AFrag& ax, float kx, int lane, fl
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         mma3(c, a0, b_load(&tb.w2f[t][0][0][0][0], lane));
         mma3(c, a1, b_load(&tb.w2f[t][1][0][0][0], lane));
-        const float b0 = tb.b2[8 * t + 2 * q], b1 = tb.b2[8 * t + 2 * q + 1];
-        h2[t][0] = act_tanh(fmaf(c[0], tb.iw2, b0));
-        h2[t][1] = act_tanh(fmaf(c[1], tb.iw2, b1));
-        h2[t][2] = act_tanh(fmaf(c[2], tb.iw2, b0));
-        h2[t][3] = act_tanh(fmaf(c[3], tb.iw2, b1));
+        const float b0 = tb.b2t[8 * t + 2 * q], b1 = tb.b2t[8 * t + 2 * q + 1];
+        h2[t][0] = tanh_of_t(fmaf(c[0], tb.iw2t, b0));
+        h2[t][1] = tanh_of_t(fmaf(c[1], tb.iw2t, b1));
+        h2[t][2] = tanh_of_t(fmaf(c[2], tb.iw2t, b0));
+        h2[t][3] = tanh_of_t(fmaf(c[3], tb.iw2t, b1));
         const float wa = tb.w3[8 * t + 2 * q], wb = tb.w3[8 * t + 2 * q + 1];
         z0 += wa * h2[t][0] + wb * h2[t][1];
         z1 += wa * h2[t][2] + wb * h2[t][3];
@@ -444,14 +448,14 @@ LB_DEV float reduce_z(float* zp, int lane)
 
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_learned_fwd_x3(const T* src, T* dst, Geom g, float omega, unsigned* status,
-                                                             const uint32_t* __restrict__ table, int ntx, int64_t ntiles)
+                                                             const uint32_t* __restrict__ table, unsigned ntx, unsigned ntiles)
 {
     __shared__ __align__(16) uint32_t stab[sizeof(Tab1) / 4];
     __shared__ uint32_t sx[kWarps][2][32][4];
     stage_table<Tab1>(stab, table);
     const Tab1& tb = *reinterpret_cast<const Tab1*>(stab);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t wt = (int64_t)blockIdx.x * kWarps + warp; wt < ntiles; wt += (int64_t)gridDim.x * kWarps) {
+    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += gridDim.x * kWarps) {
         const TileNode nd = tile_node<T>(g, wt, ntx, lane);
         float f[9];
         if (nd.valid) load_node<D2Q9, MODE>(src, g, nd.nb, nd.n, f);
@@ -463,12 +467,12 @@ __global__ void __launch_bounds__(kThreads) k_learned_fwd_x3(const T* src, T* ds
         learned_inputs(f, s, I);
         const Scale sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
         __syncwarp();
-        const float kx = sx_sc.inv * tb.iw1;
+        const float kxt = sx_sc.inv * tb.iw1 * kTwoOverLn2;
         float zp[4];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             float h1[3][4], h2[3][4];
-            net1_forward(tb, a_inputs(sx[warp], m, lane), kx, lane, h1, h2, zp[2 * m], zp[2 * m + 1]);
+            net1_forward(tb, a_inputs(sx[warp], m, lane), kxt, lane, h1, h2, zp[2 * m], zp[2 * m + 1]);
         }
         __syncwarp();  // the staged inputs are read before the next tile overwrites them
         const float z = reduce_z(zp, lane) + tb.b3;
@@ -482,61 +486,92 @@ __global__ void __launch_bounds__(kThreads) k_learned_fwd_x3(const T* src, T* ds
 }
 
 // Adjoint step with the parameter gradient (6-24-24-1). Partials: one row of kNetTheta
-// floats per block, added to.
+// floats per block, added to. The hidden activations of the tile wait in shared memory
+// (accumulator layout, one float4 per lane and tile) while the node-parallel adjoint runs;
+// the backward pass then takes one 16-node row tile at a time.
+struct Adj1Smem {
+    uint32_t stab[sizeof(Tab1) / 4];
+    uint32_t sx[kWarps][2][32][4];
+    union {
+        float sh[kWarps][2][2][3][32][4];  // [warp][h1, h2][row tile][n-tile][lane], during the loop
+        float red[kWarps][kNetTheta];      // the warps' sums, after it
+    };
+    float sg[kWarps][32][9];
+    float acc[kWarps][36][32];  // dW2^T (24 values) and dW1^T (12) per lane
+};
+
 template <class T>
-__global__ void __launch_bounds__(kThreads, 2) k_learned_adj_x3(const T* state, const float* lam_in, float* lam_out,
+__global__ void __launch_bounds__(kThreads, 3) k_learned_adj_x3(const T* state, const float* lam_in, float* lam_out,
                                                                 Geom g, float omega, float* gth_partials,
-                                                                const uint32_t* __restrict__ table, int ntx,
-                                                                int64_t ntiles)
+                                                                const uint32_t* __restrict__ table, unsigned ntx,
+                                                                unsigned ntiles)
 {
-    __shared__ __align__(16) uint32_t stab[sizeof(Tab1) / 4];
-    __shared__ uint32_t sx[kWarps][2][32][4];
-    __shared__ float sg[kWarps][32][9];
-    __shared__ float red[kWarps][kNetTheta];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Adj1Smem& sm = *reinterpret_cast<Adj1Smem*>(smem_raw);
+    auto& stab = sm.stab;
+    auto& sx = sm.sx;
+    auto& sh = sm.sh;
+    auto& sg = sm.sg;
+    auto& red = sm.red;
+    auto& acc = sm.acc;
     stage_table<Tab1>(stab, table);
     const Tab1& tb = *reinterpret_cast<const Tab1*>(stab);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, q = lane & 3;
     // parameter-gradient accumulators: dW2^T (rows k < 24, row 24 = b2; columns j) and
-    // dW1^T (rows m < 6, row 6 = b1; columns j) in accumulator layout, dW3 over the
-    // lane's columns, b3 over the lane's nodes
-    float aW2[2][3][4], aW1[3][4], aW3[3][2], aB3 = 0.f;
+    // dW1^T (rows m < 6, row 6 = b1; columns j) in accumulator layout, one shared-memory slot
+    // per lane and value (registers are the occupancy limit); dW3 over the lane's columns and
+    // b3 over the lane's nodes in registers
+    float* aW2 = &acc[warp][0][lane];   // value 12 mm + 4 t + e at aW2[32 (12 mm + 4 t + e)]
+    float* aW1 = &acc[warp][24][lane];  // value 4 t + e at aW1[32 (4 t + e)]
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int v = 0; v < 36; ++v) acc[warp][v][lane] = 0.f;
+    float aW3[3][2], aB3 = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            aW2[0][t][e] = 0.f;
-            aW2[1][t][e] = 0.f;
-            aW1[t][e] = 0.f;
-        }
-        aW3[t][0] = aW3[t][1] = 0.f;
-    }
-    for (int64_t wt = (int64_t)blockIdx.x * kWarps + warp; wt < ntiles; wt += (int64_t)gridDim.x * kWarps) {
+    for (int t = 0; t < 3; ++t) aW3[t][0] = aW3[t][1] = 0.f;
+    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += gridDim.x * kWarps) {
         const TileNode nd = tile_node<T>(g, wt, ntx, lane);
-        float f[9], mu[9];
-        if (nd.valid) {
-            load_node<D2Q9, AB>(state, g, nd.nb, nd.n, f);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nd.nb.node(g, c2(i, 0), c2(i, 1), 0)];
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = mu[i] = 0.f;
-        }
         LearnedMoments<float> s;
-        float I[kNetIn];
-        learned_inputs(f, s, I);
-        const Scale sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
-        __syncwarp();
-        const float kx = sx_sc.inv * tb.iw1;
-        float h1[2][3][4], h2[2][3][4], zp[4];
+        Scale sx_sc;
+        float z;
+        {
+            float f[9];
+            if (nd.valid) load_node<D2Q9, AB>(state, g, nd.nb, nd.n, f);
+            else
 #pragma unroll
-        for (int m = 0; m < 2; ++m)
-            net1_forward(tb, a_inputs(sx[warp], m, lane), kx, lane, h1[m], h2[m], zp[2 * m], zp[2 * m + 1]);
-        const float z = reduce_z(zp, lane) + tb.b3;
+                for (int i = 0; i < 9; ++i) f[i] = 0.f;
+            float I[kNetIn];
+            learned_inputs(f, s, I);
+            sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
+            __syncwarp();
+            const float kxt = sx_sc.inv * tb.iw1 * kTwoOverLn2;
+            float zp[4];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                float h1[3][4], h2[3][4];
+                net1_forward(tb, a_inputs(sx[warp], m, lane), kxt, lane, h1, h2, zp[2 * m], zp[2 * m + 1]);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    *reinterpret_cast<float4*>(&sh[warp][0][m][t][lane][0]) = make_float4(h1[t][0], h1[t][1], h1[t][2], h1[t][3]);
+                    *reinterpret_cast<float4*>(&sh[warp][1][m][t][lane][0]) = make_float4(h2[t][0], h2[t][1], h2[t][2], h2[t][3]);
+                }
+            }
+            z = reduce_z(zp, lane) + tb.b3;
+        }
         const float ez = expf(z);
         const float omg = recip(ez + 0.5f);
         // the node's adjoint through the equilibrium, the stress rows and the higher rows
-        LearnedCot<float> c = learned_adj_head(s, mu, omega);
+        LearnedCot<float> c;
+        {
+            float mu[9];
+            if (nd.valid)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nd.nb.node(g, c2(i, 0), c2(i, 1), 0)];
+            else
+#pragma unroll
+                for (int i = 0; i < 9; ++i) mu[i] = 0.f;
+            c = learned_adj_head(s, mu, omega);
+        }
         const float kg = 1.f - omg;
         c.gg6 = kg * c.q6;
         c.gg7 = kg * c.q7;
@@ -544,86 +579,100 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned_adj_x3(const T* state, 
         const float gomg = -(c.q6 * s.g6 + c.q7 * s.g7 + c.q8 * s.g8);
         const float gz = nd.valid ? gomg * (-ez * omg * omg) : 0.f;  // d w_g / dz = -e^z w_g^2
         aB3 += gz;
-        // back through W3 and the second tanh: ga2 = gz W3 (1 - h2^2); dW3 += gz h2
-        float ga2[2][3][4];
-#pragma unroll
+        const Pair one = ones_t(lane);
+#pragma unroll 1
         for (int m = 0; m < 2; ++m) {
-            const float gr0 = __shfl_sync(0xffffffffu, gz, 16 * m + gq);
-            const float gr1 = __shfl_sync(0xffffffffu, gz, 16 * m + 8 + gq);
+            float h[3][4];
+            // back through W3 and the second tanh: ga2 = gz W3 (1 - h2^2); dW3 += gz h2
+            float ga[3][4];
+            {
+                const float gr0 = __shfl_sync(0xffffffffu, gz, 16 * m + gq);
+                const float gr1 = __shfl_sync(0xffffffffu, gz, 16 * m + 8 + gq);
 #pragma unroll
-            for (int t = 0; t < 3; ++t)
+                for (int t = 0; t < 3; ++t) {
+                    const float4 v = *reinterpret_cast<const float4*>(&sh[warp][1][m][t][lane][0]);
+                    const float hv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float gr = (e < 2) ? gr0 : gr1;
-                    const float hv = h2[m][t][e];
-                    ga2[m][t][e] = gr * tb.w3[8 * t + 2 * q + (e & 1)] * (1.f - hv * hv);
-                    aW3[t][e & 1] += gr * hv;
+                    for (int e = 0; e < 4; ++e) {
+                        const float gr = (e < 2) ? gr0 : gr1;
+                        ga[t][e] = gr * tb.w3[8 * t + 2 * q + (e & 1)] * (1.f - hv[e] * hv[e]);
+                        aW3[t][e & 1] += gr * hv[e];
+                    }
                 }
-        }
-        // back through W2 and the first tanh: ga1 = (ga2 W2) (1 - h1^2); dW2 (and b2) with the
-        // nodes as the contraction: D[k][j] = sum_n [h1 | 1][n][k] ga2[n][j]
-        const Scale s2 = warp_scale(fmaxf(absmax<3>(ga2[0]), absmax<3>(ga2[1])));
-        const float k2 = s2.inv * tb.iw2;
-        float ga1[2][3][4];
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const AFrag g0 = a_from_c<3>(ga2[m], 0, s2.s), g1 = a_from_c<3>(ga2[m], 1, s2.s);
+            }
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-                float cc[4] = {0.f, 0.f, 0.f, 0.f};
-                mma3(cc, g0, b_load(&tb.w2b[t][0][0][0][0], lane));
-                mma3(cc, g1, b_load(&tb.w2b[t][1][0][0][0], lane));
-#pragma unroll
-                for (int e = 0; e < 4; ++e) ga1[m][t][e] = cc[e] * k2 * (1.f - h1[m][t][e] * h1[m][t][e]);
+                const float4 v = *reinterpret_cast<const float4*>(&sh[warp][0][m][t][lane][0]);
+                h[t][0] = v.x;
+                h[t][1] = v.y;
+                h[t][2] = v.z;
+                h[t][3] = v.w;
             }
-            // row tile m of the forward is k-step m of the node contraction
-            Pair u[3][2], v[3][2];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                u[t][0] = trans(split(h1[m][t][0], h1[m][t][1]));
-                u[t][1] = trans(split(h1[m][t][2], h1[m][t][3]));
-            }
-            v[0][0] = trans(g0.r[0]);
-            v[0][1] = trans(g0.r[1]);
-            v[1][0] = trans(g0.r[2]);
-            v[1][1] = trans(g0.r[3]);
-            v[2][0] = trans(g1.r[0]);
-            v[2][1] = trans(g1.r[1]);
-            const Pair one = ones_t(lane);
-            const AFrag au[2] = {{{u[0][0], u[1][0], u[0][1], u[1][1]}}, {{u[2][0], one, u[2][1], one}}};
-#pragma unroll
-            for (int mm = 0; mm < 2; ++mm)
+            // back through W2 and the first tanh: ga1 = (ga2 W2) (1 - h1^2); dW2 (and b2) with
+            // the nodes as the contraction, this row tile being its k-step:
+            // D[k][j] = sum_n [h1 | 1][n][k] ga2[n][j]
+            {
+                const Scale s2 = warp_scale(absmax<3>(ga));
+                const AFrag g0 = a_from_c<3>(ga, 0, s2.s), g1 = a_from_c<3>(ga, 1, s2.s);
+                const float k2 = s2.inv * tb.iw2;
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     float cc[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma3(cc, au[mm], BFrag{{v[t][0], v[t][1]}});
+                    mma3(cc, g0, b_load(&tb.w2b[t][0][0][0][0], lane));
+                    mma3(cc, g1, b_load(&tb.w2b[t][1][0][0][0], lane));
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) aW2[mm][t][e] = fmaf(cc[e], s2.inv, aW2[mm][t][e]);
+                    for (int e = 0; e < 4; ++e) ga[t][e] = cc[e] * k2 * (1.f - h[t][e] * h[t][e]);  // now ga1
                 }
-        }
-        // back through W1: gI = (ga1 W1) scale; dW1 (and b1): D[m][j] = sum_n [x | 1][n][m] ga1[n][j]
-        const Scale s1 = warp_scale(fmaxf(absmax<3>(ga1[0]), absmax<3>(ga1[1])));
-        const float k1 = s1.inv * tb.iw1, kd1 = s1.inv * sx_sc.inv;
+                const BFrag bv[3] = {{{trans(g0.r[0]), trans(g0.r[1])}}, {{trans(g0.r[2]), trans(g0.r[3])}},
+                                     {{trans(g1.r[0]), trans(g1.r[1])}}};
+                Pair u[3][2];
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const AFrag g0 = a_from_c<3>(ga1[m], 0, s1.s), g1 = a_from_c<3>(ga1[m], 1, s1.s);
-            float cc[4] = {0.f, 0.f, 0.f, 0.f};
-            mma3(cc, g0, b_load(&tb.w1b[0][0][0][0], lane));
-            mma3(cc, g1, b_load(&tb.w1b[1][0][0][0], lane));
-            sg[warp][16 * m + gq][2 * q] = cc[0] * k1;
-            sg[warp][16 * m + gq][2 * q + 1] = cc[1] * k1;
-            sg[warp][16 * m + gq + 8][2 * q] = cc[2] * k1;
-            sg[warp][16 * m + gq + 8][2 * q + 1] = cc[3] * k1;
-            const AFrag ax = a_inputs(sx[warp], m, lane);
-            const AFrag au = {{trans(ax.r[0]), kZero, trans(ax.r[1]), kZero}};
-            const BFrag bv[3] = {{{trans(g0.r[0]), trans(g0.r[1])}}, {{trans(g0.r[2]), trans(g0.r[3])}},
-                                 {{trans(g1.r[0]), trans(g1.r[1])}}};
+                for (int t = 0; t < 3; ++t) {
+                    u[t][0] = trans(split(h[t][0], h[t][1]));
+                    u[t][1] = trans(split(h[t][2], h[t][3]));
+                }
+                const AFrag au[2] = {{{u[0][0], u[1][0], u[0][1], u[1][1]}}, {{u[2][0], one, u[2][1], one}}};
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                float cw[4] = {0.f, 0.f, 0.f, 0.f};
-                mma3(cw, au, bv[t]);
+                for (int mm = 0; mm < 2; ++mm)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) aW1[t][e] = fmaf(cw[e], kd1, aW1[t][e]);
+                    for (int t = 0; t < 3; ++t) {
+                        float cc[4] = {0.f, 0.f, 0.f, 0.f};
+                        mma3(cc, au[mm], bv[t]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float& a = aW2[32 * (12 * mm + 4 * t + e)];
+                            a = fmaf(cc[e], s2.inv, a);
+                        }
+                    }
+            }
+            // back through W1: gI = (ga1 W1) scale (into sg); dW1 (and b1):
+            // D[m][j] = sum_n [x | 1][n][m] ga1[n][j]
+            {
+                const Scale s1 = warp_scale(absmax<3>(ga));
+                const AFrag g0 = a_from_c<3>(ga, 0, s1.s), g1 = a_from_c<3>(ga, 1, s1.s);
+                float cc[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(cc, g0, b_load(&tb.w1b[0][0][0][0], lane));
+                mma3(cc, g1, b_load(&tb.w1b[1][0][0][0], lane));
+                const float k1 = s1.inv * tb.iw1;
+                sg[warp][16 * m + gq][2 * q] = cc[0] * k1;
+                sg[warp][16 * m + gq][2 * q + 1] = cc[1] * k1;
+                sg[warp][16 * m + gq + 8][2 * q] = cc[2] * k1;
+                sg[warp][16 * m + gq + 8][2 * q + 1] = cc[3] * k1;
+                const AFrag ax = a_inputs(sx[warp], m, lane);
+                const AFrag au = {{trans(ax.r[0]), kZero, trans(ax.r[1]), kZero}};
+                const BFrag bv[3] = {{{trans(g0.r[0]), trans(g0.r[1])}}, {{trans(g0.r[2]), trans(g0.r[3])}},
+                                     {{trans(g1.r[0]), trans(g1.r[1])}}};
+                const float kd1 = s1.inv * sx_sc.inv;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    float cw[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma3(cw, au, bv[t]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float& a = aW1[32 * (4 * t + e)];
+                        a = fmaf(cw[e], kd1, a);
+                    }
+                }
             }
         }
         __syncwarp();
@@ -631,9 +680,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned_adj_x3(const T* state, 
 #pragma unroll
         for (int k = 0; k < kNetIn; ++k) gI[k] = sg[warp][lane][k] * tb.scale[k];
         if (nd.valid) learned_adj_tail(s, c, gI, lam_out, g.plane, nd.n);
-        __syncwarp();  // staged inputs and gI rows are read before the next tile overwrites them
+        __syncwarp();  // staged inputs, activations and gI rows are read before the next tile writes them
     }
-    // the warp's sums into red[warp][.] in parameter order
+    // the warp's sums into red[warp][.] in parameter order (red overlays the activations, which
+    // every warp of the block has finished with)
+    __syncthreads();
     constexpr int oW1 = 0, ob1 = 24 * 6, oW2 = ob1 + 24, ob2 = oW2 + 24 * 24, oW3 = ob2 + 24, ob3 = oW3 + 24;
     float* rw = red[warp];
 #pragma unroll
@@ -643,16 +694,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned_adj_x3(const T* state, 
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = 16 * mm + gq + 8 * (e >> 1), j = 8 * t + 2 * q + (e & 1);
-                if (k < 24) rw[oW2 + j * 24 + k] = aW2[mm][t][e];
-                else if (k == 24) rw[ob2 + j] = aW2[mm][t][e];
+                const float v = aW2[32 * (12 * mm + 4 * t + e)];
+                if (k < 24) rw[oW2 + j * 24 + k] = v;
+                else if (k == 24) rw[ob2 + j] = v;
             }
 #pragma unroll
     for (int t = 0; t < 3; ++t)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {  // rows 8..15 (e >= 2) hold nothing
             const int mrow = gq, j = 8 * t + 2 * q + e;
-            if (mrow < 6) rw[oW1 + j * 6 + mrow] = aW1[t][e];
-            else if (mrow == 6) rw[ob1 + j] = aW1[t][e];
+            const float v = aW1[32 * (4 * t + e)];
+            if (mrow < 6) rw[oW1 + j * 6 + mrow] = v;
+            else if (mrow == 6) rw[ob1 + j] = v;
         }
 #pragma unroll
     for (int t = 0; t < 3; ++t)
@@ -667,25 +720,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned_adj_x3(const T* state, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) aB3 += __shfl_xor_sync(0xffffffffu, aB3, o);
     if (lane == 0) rw[ob3] = aB3;
-    __syncthreads();
+    __syncthreads();  // every warp's sums are in red
     float* out = gth_partials + (int64_t)blockIdx.x * kNetTheta;
     for (int o = threadIdx.x; o < kNetTheta; o += kThreads) out[o] += ((red[0][o] + red[1][o]) + red[2][o]) + red[3][o];
 }
 
 // ---------------------------------------------------------------- 6-53-3
-// layer 1 of row tile m: h (accumulator layout, 7 tiles, units >= 53 are zero)
-LB_DEV void net3_layer1(const Tab3& tb, const AFrag& ax, float kx, int lane, float (*h)[4])
+// layer 1 of row tile m: h (accumulator layout, 7 tiles, units >= 53 are zero); kxt as above
+LB_DEV void net3_layer1(const Tab3& tb, const AFrag& ax, float kxt, int lane, float (*h)[4])
 {
     const int q = lane & 3;
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         mma3(c, ax, b_load0(&tb.w1f[t][0][0], lane));
-        const float b0 = tb.b1[8 * t + 2 * q], b1 = tb.b1[8 * t + 2 * q + 1];
-        h[t][0] = act_tanh(fmaf(c[0], kx, b0));
-        h[t][1] = act_tanh(fmaf(c[1], kx, b1));
-        h[t][2] = act_tanh(fmaf(c[2], kx, b0));
-        h[t][3] = act_tanh(fmaf(c[3], kx, b1));
+        const float b0 = tb.b1t[8 * t + 2 * q], b1 = tb.b1t[8 * t + 2 * q + 1];
+        h[t][0] = tanh_of_t(fmaf(c[0], kxt, b0));
+        h[t][1] = tanh_of_t(fmaf(c[1], kxt, b1));
+        h[t][2] = tanh_of_t(fmaf(c[2], kxt, b0));
+        h[t][3] = tanh_of_t(fmaf(c[3], kxt, b1));
     }
 }
 
@@ -725,14 +778,14 @@ LB_DEV void net3_outputs(const float (*zc)[4], int lane, float* z)
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_learned3_fwd_x3(const T* src, T* dst, Geom g, float omega,
                                                               unsigned* status, const uint32_t* __restrict__ table,
-                                                              int ntx, int64_t ntiles)
+                                                              unsigned ntx, unsigned ntiles)
 {
     __shared__ __align__(16) uint32_t stab[sizeof(Tab3) / 4];
     __shared__ uint32_t sx[kWarps][2][32][4];
     stage_table<Tab3>(stab, table);
     const Tab3& tb = *reinterpret_cast<const Tab3*>(stab);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t wt = (int64_t)blockIdx.x * kWarps + warp; wt < ntiles; wt += (int64_t)gridDim.x * kWarps) {
+    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += gridDim.x * kWarps) {
         const TileNode nd = tile_node<T>(g, wt, ntx, lane);
         float f[9];
         if (nd.valid) load_node<D2Q9, MODE>(src, g, nd.nb, nd.n, f);
@@ -744,12 +797,12 @@ __global__ void __launch_bounds__(kThreads) k_learned3_fwd_x3(const T* src, T* d
         learned_inputs(f, s, I);
         const Scale sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
         __syncwarp();
-        const float kx = sx_sc.inv * tb.iw1;
+        const float kxt = sx_sc.inv * tb.iw1 * kTwoOverLn2;
         float zc[2][4];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             float h[7][4];
-            net3_layer1(tb, a_inputs(sx[warp], m, lane), kx, lane, h);
+            net3_layer1(tb, a_inputs(sx[warp], m, lane), kxt, lane, h);
             net3_layer2(tb, h, lane, zc[m]);
         }
         __syncwarp();
@@ -767,34 +820,45 @@ __global__ void __launch_bounds__(kThreads) k_learned3_fwd_x3(const T* src, T* d
 
 // Adjoint step with the parameter gradient (6-53-3). The hidden activations of the tile are
 // kept in shared memory (accumulator layout, one float4 per lane and tile).
+struct Adj3Smem {
+    uint32_t stab[sizeof(Tab3) / 4];
+    uint32_t sx[kWarps][2][32][4];
+    uint32_t sz[kWarps][2][32][4];  // output cotangents gz_0..2, scaled and split, per node
+    union {
+        float sh[kWarps][2][7][32][4];  // hidden activations per row tile, during the loop
+        float red[kWarps][kNet3Theta];  // the warps' sums, after it
+    };
+    float sg[kWarps][32][9];
+    float acc[kWarps][44][32];  // dW1^T (28 values) and dW2^T (16) per lane
+};
+
 template <class T>
-__global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state, const float* lam_in,
+__global__ void __launch_bounds__(kThreads, 3) k_learned3_adj_x3(const T* state, const float* lam_in,
                                                                  float* lam_out, Geom g, float omega,
                                                                  float* gth_partials,
-                                                                 const uint32_t* __restrict__ table, int ntx,
-                                                                 int64_t ntiles)
+                                                                 const uint32_t* __restrict__ table, unsigned ntx,
+                                                                 unsigned ntiles)
 {
-    __shared__ __align__(16) uint32_t stab[sizeof(Tab3) / 4];
-    __shared__ uint32_t sx[kWarps][2][32][4];
-    __shared__ uint32_t sz[kWarps][2][32][4];  // output cotangents gz_0..2, scaled and split, per node
-    __shared__ __align__(16) float sh[kWarps][2][7][32][4];  // hidden activations per row tile
-    __shared__ float sg[kWarps][32][9];
-    __shared__ float red[kWarps][kNet3Theta];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Adj3Smem& sm = *reinterpret_cast<Adj3Smem*>(smem_raw);
+    auto& stab = sm.stab;
+    auto& sx = sm.sx;
+    auto& sz = sm.sz;
+    auto& sh = sm.sh;
+    auto& sg = sm.sg;
+    auto& red = sm.red;
+    auto& acc = sm.acc;
     stage_table<Tab3>(stab, table);
     const Tab3& tb = *reinterpret_cast<const Tab3*>(stab);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, q = lane & 3;
-    // dW1^T: rows m < 6 (row 6 = b1), columns j < 53; dW2^T: rows j < 53 (row 56 = b2), columns o < 3
-    float aW1[7][4], aW2[4][4];
+    // dW1^T: rows m < 6 (row 6 = b1), columns j < 53; dW2^T: rows j < 53 (row 56 = b2), columns
+    // o < 3; in accumulator layout, one shared-memory slot per lane and value
+    float* aW1 = &acc[warp][0][lane];   // value 4 t + e at aW1[32 (4 t + e)]
+    float* aW2 = &acc[warp][28][lane];  // value 4 mm + e at aW2[32 (4 mm + e)]
 #pragma unroll
-    for (int t = 0; t < 7; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) aW1[t][e] = 0.f;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) aW2[t][e] = 0.f;
-    for (int64_t wt = (int64_t)blockIdx.x * kWarps + warp; wt < ntiles; wt += (int64_t)gridDim.x * kWarps) {
+    for (int v = 0; v < 44; ++v) acc[warp][v][lane] = 0.f;
+    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += gridDim.x * kWarps) {
         const TileNode nd = tile_node<T>(g, wt, ntx, lane);
         float f[9], mu[9];
         if (nd.valid) {
@@ -810,12 +874,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
         learned_inputs(f, s, I);
         const Scale sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
         __syncwarp();
-        const float kx = sx_sc.inv * tb.iw1;
+        const float kxt = sx_sc.inv * tb.iw1 * kTwoOverLn2;
         float zc[2][4];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             float h[7][4];
-            net3_layer1(tb, a_inputs(sx[warp], m, lane), kx, lane, h);
+            net3_layer1(tb, a_inputs(sx[warp], m, lane), kxt, lane, h);
             net3_layer2(tb, h, lane, zc[m]);
 #pragma unroll
             for (int t = 0; t < 7; ++t)
@@ -852,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
         }
         __syncwarp();
         const float kz = sgz.inv * tb.iw2;
-#pragma unroll
+#pragma unroll 1
         for (int m = 0; m < 2; ++m) {
             float h[7][4];
 #pragma unroll
@@ -900,7 +964,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
                     float cw[4] = {0.f, 0.f, 0.f, 0.f};
                     mma3(cw, au, bv);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) aW1[t][e] = fmaf(cw[e], kd1, aW1[t][e]);
+                    for (int e = 0; e < 4; ++e) {
+                        float& a = aW1[32 * (4 * t + e)];
+                        a = fmaf(cw[e], kd1, a);
+                    }
                 }
             }
             // dW2: D[j][o] = sum_n [h | 1][n][j] gz[n][o] (the constant 1 at unit 56)
@@ -922,7 +989,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
                     float cw[4] = {0.f, 0.f, 0.f, 0.f};
                     mma3(cw, au, bz);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) aW2[mm][e] = fmaf(cw[e], sgz.inv, aW2[mm][e]);
+                    for (int e = 0; e < 4; ++e) {
+                        float& a = aW2[32 * (4 * mm + e)];
+                        a = fmaf(cw[e], sgz.inv, a);
+                    }
                 }
             }
         }
@@ -933,6 +1003,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
         if (nd.valid) learned_adj_tail(s, c, gI, lam_out, g.plane, nd.n);
         __syncwarp();
     }
+    __syncthreads();  // red overlays the activations, which every warp has finished with
     constexpr int H = kNet3Hidden;
     constexpr int oW1 = 0, ob1 = H * 6, oW2 = ob1 + H, ob2 = oW2 + 3 * H;
     float* rw = red[warp];
@@ -942,8 +1013,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
         for (int e = 0; e < 2; ++e) {  // rows 8..15 (e >= 2) hold nothing
             const int mrow = gq, j = 8 * t + 2 * q + e;
             if (j < H) {
-                if (mrow < 6) rw[oW1 + j * 6 + mrow] = aW1[t][e];
-                else if (mrow == 6) rw[ob1 + j] = aW1[t][e];
+                const float v = aW1[32 * (4 * t + e)];
+                if (mrow < 6) rw[oW1 + j * 6 + mrow] = v;
+                else if (mrow == 6) rw[ob1 + j] = v;
             }
         }
 #pragma unroll
@@ -952,11 +1024,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
         for (int e = 0; e < 4; ++e) {
             const int j = 16 * mm + gq + 8 * (e >> 1), o = 2 * q + (e & 1);
             if (o < 3) {
-                if (j < H) rw[oW2 + o * H + j] = aW2[mm][e];
-                else if (j == 56) rw[ob2 + o] = aW2[mm][e];
+                const float v = aW2[32 * (4 * mm + e)];
+                if (j < H) rw[oW2 + o * H + j] = v;
+                else if (j == 56) rw[ob2 + o] = v;
             }
         }
-    __syncthreads();
+    __syncthreads();  // every warp's sums are in red
     float* out = gth_partials + (int64_t)blockIdx.x * kNet3Theta;
     for (int o = threadIdx.x; o < kNet3Theta; o += kThreads)
         out[o] += ((red[0][o] + red[1][o]) + red[2][o]) + red[3][o];
@@ -964,13 +1037,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_learned3_adj_x3(const T* state,
 
 // ---------------------------------------------------------------- launch
 // Persistent grid: as many blocks as fit on the device at once (from the occupancy of the
-// kernel), at most one per four warp tiles. The same grid for every launch on a device keeps
-// the parameter-gradient sums in a fixed order.
+// kernel with its dynamic shared memory), at most one per four warp tiles. The same grid for
+// every launch on a device keeps the parameter-gradient sums in a fixed order.
 template <class K>
-int grid_for(K kernel, int sms, int64_t ntiles)
+int grid_for(K kernel, int sms, int64_t ntiles, size_t smem = 0)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+    if (smem > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int64_t want = (ntiles + kWarps - 1) / kWarps;
     const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * per_sm;
@@ -1008,13 +1082,13 @@ cudaError_t launch_x3(const OpArgs& a, bool three)
     if (a.op == OP_ADJ_STEP) {
         const T* st = (const T*)a.src;
         if (three) {
-            const int grid = grid_for(k_learned3_adj_x3<T>, a.sms, ntiles);
-            k_learned3_adj_x3<T><<<grid, kThreads, 0, a.stream>>>(st, (const float*)a.lam_in, (float*)a.lam_out, a.g,
-                                                                  omega, (float*)a.gth, tab, ntx, ntiles);
+            const int grid = grid_for(k_learned3_adj_x3<T>, a.sms, ntiles, sizeof(Adj3Smem));
+            k_learned3_adj_x3<T><<<grid, kThreads, sizeof(Adj3Smem), a.stream>>>(
+                st, (const float*)a.lam_in, (float*)a.lam_out, a.g, omega, (float*)a.gth, tab, ntx, ntiles);
         } else {
-            const int grid = grid_for(k_learned_adj_x3<T>, a.sms, ntiles);
-            k_learned_adj_x3<T><<<grid, kThreads, 0, a.stream>>>(st, (const float*)a.lam_in, (float*)a.lam_out, a.g,
-                                                                 omega, (float*)a.gth, tab, ntx, ntiles);
+            const int grid = grid_for(k_learned_adj_x3<T>, a.sms, ntiles, sizeof(Adj1Smem));
+            k_learned_adj_x3<T><<<grid, kThreads, sizeof(Adj1Smem), a.stream>>>(
+                st, (const float*)a.lam_in, (float*)a.lam_out, a.g, omega, (float*)a.gth, tab, ntx, ntiles);
         }
         return cudaGetLastError();
     }
@@ -1025,7 +1099,8 @@ template <class T>
 int64_t adj_grid(const Geom& g, int sms, bool three)
 {
     const int64_t ntiles = (int64_t)((g.nx + 31) / 32) * g.ny;
-    return three ? grid_for(k_learned3_adj_x3<T>, sms, ntiles) : grid_for(k_learned_adj_x3<T>, sms, ntiles);
+    return three ? grid_for(k_learned3_adj_x3<T>, sms, ntiles, sizeof(Adj3Smem))
+                 : grid_for(k_learned_adj_x3<T>, sms, ntiles, sizeof(Adj1Smem));
 }
 
 }  // namespace
