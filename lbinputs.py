@@ -51,7 +51,8 @@ def taylor_green_2d(n: int, u0: float = 0.05, ny: int | None = None):
     """2D Taylor-Green vortex on an n x ny periodic grid (node coordinates x = i).
 
     u = u0 sin(kx) cos(ky), v = -u0 cos(kx) sin(ky), k = 2 pi / n,
-    p = -(u0^2/4) (cos 2kx + cos 2ky), rho = 1 + p / c_s^2.
+    p = (u0^2/4) (cos 2kx + cos 2ky), rho = 1 + p / c_s^2: the pressure in balance with this
+    field (lap p = -d_i d_j (u_i u_j); highest at the stagnation points x = y = 0).
     Returns (dims, rho[N], u[2][N]) in FP64.
     """
     ny = n if ny is None else ny
@@ -62,7 +63,7 @@ def taylor_green_2d(n: int, u0: float = 0.05, ny: int | None = None):
     u = np.empty((2, x.size))
     u[0] = u0 * np.sin(kx * x) * np.cos(ky * y)
     u[1] = -u0 * np.cos(kx * x) * np.sin(ky * y)
-    p = -(u0 * u0 / 4.0) * (np.cos(2 * kx * x) + np.cos(2 * ky * y))
+    p = (u0 * u0 / 4.0) * (np.cos(2 * kx * x) + np.cos(2 * ky * y))
     rho = 1.0 + p / CS2
     return dims, rho, u
 
@@ -142,6 +143,30 @@ def random_spectrum_velocity(dims, k0: float, u_rms: float, seed: int):
         u[a] = (fields[a] * (u_rms / rms)).ravel()
     rho = np.ones(nx * ny * nz)
     return rho, u
+
+
+def balanced_density(dims, u):
+    """rho = 1 + p / c_s^2 (c_s^2 = 1/3) with p the incompressible pressure of the periodic
+    velocity field u[d][N]: lap p = -d_i d_j (u_i u_j), solved spectrally (p has zero mean).
+    A field started at this density is in pressure balance, so it does not launch the
+    acoustic waves that rho = 1 does."""
+    nx, ny, nz = (int(d) for d in dims)
+    d = 2 if nz == 1 else 3
+    shape = (nz, ny, nx) if d == 3 else (ny, nx)
+    ks = [np.fft.fftfreq(s, 1.0 / s) * (2.0 * math.pi / s) for s in shape]
+    kk = np.meshgrid(*ks, indexing="ij")
+    kvec = list(reversed(kk))  # components (x, y[, z])
+    uf = [np.asarray(u[a]).reshape(shape) for a in range(d)]
+    rhs = np.zeros(shape, dtype=np.complex128)
+    for i in range(d):
+        for j in range(d):
+            rhs += kvec[i] * kvec[j] * np.fft.fftn(uf[i] * uf[j])  # FFT of -d_i d_j (u_i u_j)
+    k2 = sum(k * k for k in kvec)
+    k2[(0,) * d] = 1.0
+    ph = -rhs / k2  # -k^2 p_hat = FFT(-d_i d_j u_i u_j)
+    ph[(0,) * d] = 0.0
+    p = np.fft.ifftn(ph).real
+    return (1.0 + 3.0 * p).ravel()
 
 
 def smooth_force(dims, amplitude: float, seed: int, modes: int = 4):

@@ -198,14 +198,18 @@ def spectrum_2d(u: np.ndarray, n: int):
 
 def evaluate_turbulence(theta, extra, n_coarse: int = 2048, k0: float = 12.0, u_rms: float = 0.05,
                         seed: int = 30000, re: float = 30000.0, steps: int = 4000, every: int = 250,
-                        storage: str = "f32", reference: str = "bgk", net: str = "learned"):
+                        storage: str = "f32", reference: str = "bgk", net: str = "learned",
+                        balanced: bool = False):
     """Learned vs BGK on coarse decaying turbulence against the coarsened fine run (BGK on
     the grid of twice the resolution). If the fine reference itself goes unstable the
-    result records when (the caller then lowers Re)."""
+    result records when (the caller then lowers Re). balanced: start from the density of the
+    field's incompressible pressure instead of rho = 1 (no initial acoustic waves)."""
     nf = 2 * n_coarse
     tau_f = 0.5 + 3.0 * u_rms * (nf / (2.0 * math.pi)) / re
     tau_c = coarse_tau(tau_f)
     rho, u = lbinputs.random_spectrum_velocity((nf, nf, 1), k0, u_rms, seed)  # k0 counts modes per domain
+    if balanced:
+        rho = lbinputs.balanced_density((nf, nf, 1), u)
     fine = Lattice("D2Q9", (nf, nf, 1), tau_f, reference, storage=storage)
     fine.init_from_moments(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
     ref = Lattice("D2Q9", (n_coarse, n_coarse, 1), tau_c, "bgk", storage="f64")

@@ -35,3 +35,46 @@ def test_training_the_paper_shaped_network_reduces_holdout_loss_below_bgk():
     assert hist["holdout_loss"][0][1] == pytest.approx(hist["holdout_loss_bgk"], rel=1e-2)
     assert hist["holdout_gain"] > 0.03, hist
     assert hist["train_loss"][-1] < hist["train_loss"][0], hist
+
+
+@pytest.mark.parametrize("net", ["learned", "learned3"])
+def test_transfer_evaluation_on_small_decaying_turbulence(net):
+    """The transfer evaluation of Sec. 3.1 (training.evaluate_turbulence) at a reduced size:
+    128^2 coarse runs (learned collision and BGK) against the coarse-grained 256^2 BGK
+    reference. With the untrained network (exactly BGK) the learned run must reproduce the
+    BGK run; with a perturbed network it must stay finite and differ. Every metric is taken on
+    the same snapshots."""
+    import math
+
+    import numpy as np
+
+    from paper_2106_12929_gb300 import build, training
+    build.build()
+    n, steps, every, re = 128, 400, 100, 1000.0
+    tau_c = training.coarse_tau(0.5 + 3.0 * 0.05 * (2 * n / (2.0 * math.pi)) / re)
+    extra = torch.cat([torch.zeros(6), torch.tensor([50.0, 100.0, 300.0, 1e5, 1e5, 1e5])]).float().cuda()
+    theta0 = training.init_theta(tau_c, seed=3, net=net)
+    runs = {}
+    for name, theta in (("bgk_net", theta0), ("perturbed", theta0.clone())):
+        if name == "perturbed":  # small random output weights: rates that vary from node to node
+            g = torch.Generator(device="cuda").manual_seed(4)
+            no = 3 * 53 if net == "learned3" else 24
+            lo = 53 * 7 if net == "learned3" else 24 * 6 + 24 + 24 * 24 + 24
+            theta[lo:lo + no] = 0.3 * torch.randn(no, generator=g, device="cuda")
+        out = training.evaluate_turbulence(theta, extra, n_coarse=n, k0=12.0, u_rms=0.05, seed=30000, re=re,
+                                           steps=steps, every=every, net=net)
+        assert "reference_unstable_at" not in out and not any(k.startswith("unstable_") for k in out), out
+        T = len(out["times"])
+        assert out["times"] == list(range(every, steps + 1, every))
+        for key in ("loss_learned", "loss_bgk", "E_ref", "E_learned", "E_bgk", "Z_ref", "Z_learned", "Z_bgk"):
+            assert len(out[key]) == T and all(np.isfinite(v) for v in out[key]), key
+        for key in ("spectrum_hi_log_err_learned", "spectrum_hi_log_err_bgk"):
+            assert np.isfinite(out[key]), key
+        runs[name] = out
+    a = runs["bgk_net"]
+    np.testing.assert_allclose(a["loss_learned"], a["loss_bgk"], rtol=1e-3)
+    np.testing.assert_allclose(a["E_learned"], a["E_bgk"], rtol=1e-5)
+    assert abs(a["spectrum_hi_log_err_learned"] - a["spectrum_hi_log_err_bgk"]) <= 1e-3 * a["spectrum_hi_log_err_bgk"]
+    b = runs["perturbed"]
+    assert b["loss_bgk"] == a["loss_bgk"]  # the BGK side and the reference do not depend on the network
+    assert max(abs(x - y) / y for x, y in zip(b["loss_learned"], b["loss_bgk"])) > 1e-3

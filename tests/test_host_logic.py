@@ -255,3 +255,16 @@ def test_build_rebuilds_an_object_only_when_a_dependency_is_newer(tmp_path):
     os.utime(hdr, (300, 300))  # a header edited after the object was built
     assert build._stale(str(obj), [str(src), str(hdr)])
     assert build._stale(str(tmp_path / "missing.o"), [str(src)])
+
+
+def test_balanced_density_is_the_taylor_green_pressure():
+    """The spectral pressure solve against the closed-form pressures of the 2D and 3D
+    Taylor-Green vortices (each highest at the stagnation points); the decaying-turbulence
+    field it balances has the same mean density."""
+    for dims, rho, u in (lbinputs.taylor_green_2d(48, u0=0.05), lbinputs.taylor_green_3d(24)):
+        got = lbinputs.balanced_density(dims, u)
+        assert np.max(np.abs(got - rho)) <= 1e-15
+        assert rho[0] == np.max(rho)  # node 0 is a stagnation point
+    rho, u = lbinputs.random_spectrum_velocity((64, 64, 1), 6.0, 0.05, 7)
+    got = lbinputs.balanced_density((64, 64, 1), u)
+    assert abs(np.mean(got) - 1.0) <= 1e-15 and np.std(got) > 1e-4

@@ -387,6 +387,9 @@ def test_taylor_green_decay_rate_matches_viscosity():
 
 
 def test_taylor_green_decay_error_is_second_order():
+    # the decay-rate error falls at least as fast as k^2 (second order in space, diffusive
+    # time scaling); with the balanced initial pressure no acoustic transient adds a slower
+    # term, and the finest grid's error falls faster still (4.4x, then 6.5x)
     tau = 0.8
     nu = CS2 * (tau - 0.5)
     errs = []
@@ -394,7 +397,7 @@ def test_taylor_green_decay_error_is_second_order():
         k = 2 * math.pi / n
         errs.append(abs(_tgv_decay_slope(n, tau, steps, steps // 10) / (-4 * nu * k * k) - 1))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
-    assert 3.0 < r1 < 5.5 and 3.0 < r2 < 5.5, errs
+    assert r1 > 3.5 and r2 > 3.5 and errs[2] < 5e-4, errs
 
 
 # ----------------------------------------------------------------------------- moments / reduce
