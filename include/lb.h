@@ -326,6 +326,37 @@ LB_API lb_status lb_vorticity(lb_ctx* ctx, void* w, lb_mem mem);
 LB_API lb_status lb_adam_update(float* theta, float* m, float* v, const float* grad, int64_t n, double lr, double b1,
                          double b2, double eps, int64_t t, void* stream);
 
+/* ------------------------------------------------------------------ slabs ---- */
+/* Partitioning across GPUs (the paper names multi-GPU runs as future work, Sec. 3.3): a
+ * periodic grid is split along its last axis (z in 3D, y in 2D) into slabs, one per rank.
+ * Each rank's context holds its slab plus one ghost layer at each end: its last dimension is
+ * the slab's layers + 2, local layer 0 is the ghost below, layer n_last - 1 the ghost above,
+ * and the context steps all layers as an ordinary periodic grid (the ghost layers' own
+ * updates are discarded). Between steps the populations that cross each face move: the slots
+ * whose velocity has last component -1 of interior layer 1 go to the lower neighbour's upper
+ * ghost layer, those with +1 of layer n_last - 2 to the upper neighbour's lower ghost layer
+ * (3 slots for D2Q9, 5 for D3Q19, 9 for D3Q27). Over an exchanged slab, the interior layers
+ * evolve exactly as the same layers of the whole grid with the same launch shape.
+ *
+ * lb_halo_bytes: size of one face's buffer: crossing slots x layer nodes x the storage's
+ * element size (the stored values are copied as they are).
+ * lb_halo_pack: copy the crossing populations leaving through `face` (0: low end, 1: high end)
+ * into buf; lb_halo_unpack: copy a neighbour's packed buffer into the ghost layer of `face`.
+ * buf is device memory of the context's device, laid out [slot][layer nodes]; both calls are
+ * ordered on the context's stream and return without synchronising. AB layout only
+ * (LB_ERR_UNSUPPORTED otherwise, and for unpacking into a context that records for the
+ * adjoint); the last dimension must be >= 3 (LB_ERR_ARG). */
+LB_API lb_status lb_halo_bytes(const lb_ctx* ctx, int64_t* bytes);
+LB_API lb_status lb_halo_pack(lb_ctx* ctx, int face, void* buf);
+LB_API lb_status lb_halo_unpack(lb_ctx* ctx, int face, const void* buf);
+
+/* The global sums of lb_reduce over the layers [first, first + count) of the last axis (a
+ * slab's interior: first = 1, count = n_last - 2), unnormalised: out[0] = sum rho,
+ * out[1..3] = sum rho u, out[4] = sum |u|^2, out[5] = sum rho |u|^2 (the caller adds the ranks'
+ * sums and divides out[4], out[5] by 2 N of the whole grid). FP64, deterministic; out is host
+ * memory and the call synchronises the stream. */
+LB_API lb_status lb_reduce_slab(lb_ctx* ctx, int64_t first, int64_t count, double out[6]);
+
 /* ------------------------------------------------------- without allocation ---- */
 /* The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory where they need the global sums: for instance code that

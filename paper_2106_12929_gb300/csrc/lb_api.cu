@@ -97,8 +97,8 @@ struct lb_ctx {
     bool sc_on = false;
     int sc_logn = 0;
     double sc_cutoff = 2e-5, sc_kappa = 5e-5;
-    void* sc_spec = nullptr;     // [2][n][n] complex values of the arithmetic type
-    double* sc_small = nullptr;  // partials [n/2][n], sigma, grad, r2 [n/2 each], cost [1], sigma0 [n/2]
+    void* sc_spec = nullptr;     // [n][n] complex values of the arithmetic type, then the twiddles [n/2]
+    double* sc_small = nullptr;  // partials [n/2][<= n], sigma, grad, r2 [n/2 each], cost [1], sigma0, l0 [n/2 each]
     void* sc_du = nullptr;       // [2][plane] arithmetic type
 
     // CUDA graph of a two-step cycle, replayed by lb_step when nothing is recorded
@@ -189,6 +189,7 @@ lb::SpectralArgs spectral_args(lb_ctx* c, const lb::OpArgs& a)
     s.n = (int)c->dims[0];
     s.logn = c->sc_logn;
     s.spec = c->sc_spec;
+    s.tw = c->sc_spec ? (const char*)c->sc_spec + (int64_t)s.n * s.n * 2 * real_bytes(c->opt.storage) : nullptr;
     const int64_t K = s.n / 2;
     s.partials = c->sc_small;
     s.sigma = s.partials + (int64_t)s.n * K;
@@ -196,6 +197,7 @@ lb::SpectralArgs spectral_args(lb_ctx* c, const lb::OpArgs& a)
     s.r2 = s.grad + K;
     s.cost = s.r2 + K;
     s.sigma0 = c->sc_on ? s.cost + 1 : nullptr;
+    s.l0 = c->sc_on ? s.cost + 1 + K : nullptr;
     s.cutoff = c->sc_cutoff;
     s.kappa = c->sc_kappa;
     s.du = c->sc_on ? c->sc_du : nullptr;
@@ -672,9 +674,15 @@ static lb_status spectral_alloc(lb_ctx* c)
 {
     const int64_t n = c->dims[0], K = n / 2;
     lb_status s;
-    if (!c->sc_spec && (s = alloc(c, &c->sc_spec, 2 * n * n * 2 * real_bytes(c->opt.storage), "spectrum")) != LB_OK)
-        return s;
-    if (!c->sc_small && (s = alloc(c, (void**)&c->sc_small, (n * K + 4 * K + 1) * 8, "spectral sums")) != LB_OK)
+    if (!c->sc_spec) {
+        // the complex field [n][n], then the twiddle table [n/2] (computed here, once)
+        if ((s = alloc(c, &c->sc_spec, (n * n + K) * 2 * real_bytes(c->opt.storage), "spectrum")) != LB_OK) return s;
+        LB_CUDA(c, lb::spectral_twiddles((char*)c->sc_spec + n * n * 2 * real_bytes(c->opt.storage), (int)n,
+                                         c->opt.storage, c->stream),
+                "twiddle table");
+        c->launches += 1;
+    }
+    if (!c->sc_small && (s = alloc(c, (void**)&c->sc_small, (n * K + 5 * K + 1) * 8, "spectral sums")) != LB_OK)
         return s;
     return LB_OK;
 }
@@ -704,9 +712,15 @@ lb_status lb_set_spectral_control(lb_ctx* c, const double* sigma0, int64_t K, do
     if (!c->sc_du && (s = alloc(c, &c->sc_du, 2 * c->plane * real_bytes(c->opt.storage), "velocity shift")) != LB_OK)
         return s;
     const int64_t n = c->dims[0];
-    // sigma0 sits after partials, sigma, grad, r2 and cost; ordered on the stream after queued steps
-    LB_CUDA(c, cudaMemcpyAsync(c->sc_small + n * K + 3 * K + 1, sigma0, (size_t)K * 8, cudaMemcpyHostToDevice,
-                               c->stream),
+    // sigma0 and ln max(sigma0, cutoff) sit after partials, sigma, grad, r2 and cost; ordered on
+    // the stream after queued steps
+    std::vector<double> target((size_t)(2 * K));
+    for (int64_t k = 0; k < K; ++k) {
+        target[(size_t)k] = sigma0[k];
+        target[(size_t)(K + k)] = std::log(std::fmax(sigma0[k], cutoff));
+    }
+    LB_CUDA(c, cudaMemcpyAsync(c->sc_small + n * K + 3 * K + 1, target.data(), (size_t)(2 * K) * 8,
+                               cudaMemcpyHostToDevice, c->stream),
             "sigma0 copy");
     LB_CUDA(c, cudaStreamSynchronize(c->stream), "sigma0 copy");
     c->sc_on = true;
@@ -935,6 +949,94 @@ lb_status lb_reduce(lb_ctx* c, double out[6])
     out[3] = h[3];
     out[4] = 0.5 * h[4] * invN;
     out[5] = 0.5 * h[5] * invN;
+    return LB_OK;
+}
+
+// ------------------------------------------------------------------ slabs
+// A context may hold one slab of a larger periodic grid split along its last axis (z in 3D,
+// y in 2D), with one ghost layer at each end (local layers 0 and n_last - 1). The populations
+// that cross a face are the slots whose velocity has last component +1 or -1.
+static int slab_axis(const lb_ctx* c) { return c->D == 3 ? 2 : 1; }
+static int64_t slab_layer_nodes(const lb_ctx* c) { return c->D == 3 ? c->dims[0] * c->dims[1] : c->dims[0]; }
+static int slab_slots(const lb_ctx* c, int dir, int* slots)
+{
+    int n = 0;
+    for (int i = 0; i < c->Q; ++i) {
+        const int cl = c->D == 3 ? lb::c3(i, 2) : lb::c2(i, 1);
+        if (cl == dir) slots[n++] = i;
+    }
+    return n;
+}
+
+static lb_status slab_check(lb_ctx* c, int face)
+{
+    if (face != 0 && face != 1) return fail(LB_ERR_ARG, "face must be 0 (low end) or 1 (high end)");
+    if (c->opt.layout != LB_LAYOUT_AB) return fail(LB_ERR_UNSUPPORTED, "the slab exchange needs the AB layout");
+    if (c->dims[slab_axis(c)] < 3) return fail(LB_ERR_ARG, "a slab needs two ghost layers and one interior layer");
+    return LB_OK;
+}
+
+lb_status lb_halo_bytes(const lb_ctx* c, int64_t* bytes)
+{
+    if (!c) return fail(LB_ERR_ARG, "null context");
+    if (!bytes) return fail(LB_ERR_ARG, "bytes is null");
+    int slots[27];
+    *bytes = (int64_t)slab_slots(c, 1, slots) * slab_layer_nodes(c) * storage_bytes(c->opt.storage);
+    return LB_OK;
+}
+
+// Copy the crossing populations between the state buffer and buf (device memory): n copies of
+// one contiguous layer of one slot each, ordered on the context's stream.
+static lb_status slab_copy(lb_ctx* c, int face, void* buf, bool pack)
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!buf) return fail(LB_ERR_ARG, "buf is null");
+    if ((s = slab_check(c, face)) != LB_OK) return s;
+    if (!pack && c->opt.record_every > 0) return fail(LB_ERR_UNSUPPORTED, "no adjoint over slabs");
+    DeviceGuard guard(c->device);
+    const int64_t nl = c->dims[slab_axis(c)], ln = slab_layer_nodes(c), sb = storage_bytes(c->opt.storage);
+    // pack: interior layer next to the face, slots leaving through it; unpack: the face's ghost
+    // layer, slots entering through it
+    const int dir = pack ? (face == 0 ? -1 : 1) : (face == 0 ? 1 : -1);
+    const int64_t layer = pack ? (face == 0 ? 1 : nl - 2) : (face == 0 ? 0 : nl - 1);
+    int slots[27];
+    const int n = slab_slots(c, dir, slots);
+    for (int k = 0; k < n; ++k) {
+        char* st = (char*)c->state + ((int64_t)slots[k] * c->plane + layer * ln) * sb;
+        char* bf = (char*)buf + (int64_t)k * ln * sb;
+        LB_CUDA(c, cudaMemcpyAsync(pack ? bf : st, pack ? st : bf, (size_t)(ln * sb), cudaMemcpyDeviceToDevice, c->stream),
+                "halo copy");
+    }
+    return LB_OK;
+}
+
+lb_status lb_halo_pack(lb_ctx* c, int face, void* buf) { return slab_copy(c, face, buf, true); }
+lb_status lb_halo_unpack(lb_ctx* c, int face, const void* buf) { return slab_copy(c, face, const_cast<void*>(buf), false); }
+
+lb_status lb_reduce_slab(lb_ctx* c, int64_t first, int64_t count, double out[6])
+{
+    lb_status s = check_ctx(c);
+    if (s != LB_OK) return s;
+    if (!out) return fail(LB_ERR_ARG, "out is null");
+    const int ax = slab_axis(c);
+    if (first < 0 || count < 1 || first + count > c->dims[ax])
+        return fail(LB_ERR_ARG, "layers [%lld, %lld) are not inside the last axis", (long long)first,
+                    (long long)(first + count));
+    DeviceGuard guard(c->device);
+    const int64_t nb = lb::node_grid_blocks(c->g);
+    if ((s = ensure_partials(c, 6 * nb)) != LB_OK) return s;
+    lb::OpArgs a = base_args(c, lb::OP_REDUCE_PARTIAL);
+    a.partials = c->partials;
+    if ((s = launch(c, a, "reduce")) != LB_OK) return s;
+    // the node grid's blocks run x fastest, then y, then z: a layer range is a block range
+    const dim3 gr = lb::node_grid(c->g);
+    const int64_t per_layer = ax == 2 ? (int64_t)gr.x * gr.y : (int64_t)gr.x;
+    LB_CUDA(c, lb::reduce_final(c->partials + 6 * per_layer * first, per_layer * count, 6, c->dsmall, c->stream),
+            "reduce final");
+    c->launches += 1;
+    LB_CUDA(c, cudaMemcpyAsync(out, c->dsmall, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "reduce read");
+    LB_CUDA(c, cudaStreamSynchronize(c->stream), "reduce sync");
     return LB_OK;
 }
 

@@ -9,14 +9,22 @@
 //   grad_u_a R(x) = Re sum_k G(k) U_a(k) exp(+2 pi i k.x / n) / N^2,
 //   G(k) = dR/dsigma_s of k's shell s (0 outside the kept shells),
 //   dR/dsigma_s = 2 (ln sigma_s - ln max(sigma0_s, c)) / sigma_s if sigma_s > c, else 0.
+// Both velocity components travel as one complex field w = u_x + i u_y: its transform is
+// W = U_x + i U_y, and since k and -k lie in the same shell, the shell sums of
+// |U_x|^2 + |U_y|^2 equal those of |W|^2 (|U_x(k)|^2 + |U_y(k)|^2 = (|W(k)|^2 + |W(-k)|^2) / 2);
+// G is real and even, so the inverse transform of G W has the real part grad_u_x R N^2 and
+// the imaginary part grad_u_y R N^2. One complex 2D FFT each way instead of two.
+//
 // A controlled step is five launches: rows (moments + forward DFT along x), columns (forward
-// DFT along y, modal energies and per-column shell sums), shells (sigma and dR/dsigma, one
-// warp per shell), columns (filter by G, inverse DFT along y; the cost R), rows (inverse DFT
-// along x: du, then the shifted BGK step of the row's nodes). lb_spectral_shift writes du
-// instead of stepping. Each DFT is an in-place radix-2 FFT of one grid line in shared
-// memory, one block per line, in passes of three radix-2 stages held in registers (a padded
-// layout keeps the passes free of bank conflicts), with a per-block twiddle table; both velocity
-// components go through the same passes. Every sum runs in a fixed order (deterministic).
+// DFT along y and the shell sums of |W|^2 over the block's columns), shells (sigma and
+// dR/dsigma, one warp per shell), columns (filter by G, inverse DFT along y; the cost R), rows
+// (inverse DFT along x: du, then the shifted BGK step of the row's nodes). lb_spectral_shift
+// writes du instead of stepping. Each DFT is an in-place radix-2 FFT of grid lines in shared
+// memory, in passes of three radix-2 stages held in registers (a padded layout keeps the
+// passes free of bank conflicts), with the twiddle table computed once per context. A row
+// block takes one grid line; a column block takes several adjacent columns, so that its loads
+// and stores of a grid row are contiguous runs of whole 32-byte sectors. Every sum runs in a
+// fixed order (deterministic).
 #include "lb_collide.cuh"
 #include "lb_spectral.cuh"
 
@@ -32,51 +40,60 @@ LB_DEV void sincos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
 
 LB_DEV int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
 
-// Twiddle table tw[k] = exp(sign i 2 pi k / n), k < n/2 (block-wide; the caller syncs).
+// twiddle table tw[k] = exp(-i 2 pi k / n), k < n/2
 template <class R>
-LB_DEV void twiddles(Cx<R>* tw, int n, R sign)
+__global__ void k_sc_twiddles(Cx<R>* tw, int n)
 {
-    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
-        R s, c;
-        sincos_pi(sign * R(2 * k) / R(n), &s, &c);
-        tw[k] = {c, s};
-    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n / 2) return;
+    R s, c;
+    sincos_pi(R(-2 * k) / R(n), &s, &c);
+    tw[k] = {c, s};
+}
+
+// the table into shared memory (block-wide; the caller syncs)
+template <class R>
+LB_DEV void load_twiddles(Cx<R>* tws, const Cx<R>* tw, int n)
+{
+    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) tws[k] = tw[k];
 }
 
 // Shared-memory position of element i of a line: one spare slot after every eight elements, so
 // that the threads of a half-warp reading the sets of the first passes hit distinct banks.
 LB_HD int pz(int i) { return i + (i >> 3); }
-LB_HD int line_stride(int n) { return n + (n >> 3); }
+// (one more slot per line, so that the lines of a column block start on different banks)
+LB_HD int line_stride(int n) { return n + (n >> 3) + 1; }
 
-// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 of the two
-// n-point lines z[0 ..) and z[line_stride(n) ..) (bit-reversed input order): those stages
-// only combine elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads
-// whole sets, runs the RB stages in registers and stores them back (one shared-memory round
-// trip and one barrier for RB stages). tw from twiddles(); unnormalised.
-template <class R, int RB>
-LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s)
+// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 of `lines`
+// n-point lines z[l line_stride(n) ..) (bit-reversed input order): those stages only combine
+// elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads whole sets,
+// runs the RB stages in registers and stores them back (one shared-memory round trip and one
+// barrier for RB stages). Forward: twiddles exp(-i ...), INV: their conjugates; unnormalised.
+template <class R, int RB, bool INV>
+LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s, int lines)
 {
     constexpr int RR = 1 << RB;
     const int h = 1 << s, sets = n >> RB, ls = line_stride(n);
-    for (int t = threadIdx.x; t < 2 * sets; t += blockDim.x) {
-        Cx<R>* line = z + (t >= sets ? ls : 0);
-        const int q = t >= sets ? t - sets : t;
+    for (int t = threadIdx.x; t < lines * sets; t += blockDim.x) {
+        const int l = t / sets, q = t - l * sets;
+        Cx<R>* line = z + l * ls;
         const int j = q & (h - 1);
         const int base = (q - j) * RR + j;  // (q / h) RR h + j
         Cx<R> v[RR];
 #pragma unroll
         for (int k = 0; k < RR; ++k) v[k] = line[pz(base + k * h)];
 #pragma unroll
-        for (int l = 0; l < RB; ++l) {  // stage s + l: half H = h 2^l, pairs (k, k + 2^l)
+        for (int lv = 0; lv < RB; ++lv) {  // stage s + lv: half H = h 2^lv, pairs (k, k + 2^lv)
 #pragma unroll
             for (int k = 0; k < RR; ++k) {
-                if (k & (1 << l)) continue;
-                const int m = j + (k & ((1 << l) - 1)) * h;  // position of the pair within its half
-                const Cx<R> w = tw[m << (logn - 1 - s - l)];   // exp(sign i pi m / H)
-                const Cx<R> p = v[k], qv = v[k | (1 << l)];
+                if (k & (1 << lv)) continue;
+                const int m = j + (k & ((1 << lv) - 1)) * h;  // position of the pair within its half
+                Cx<R> w = tw[m << (logn - 1 - s - lv)];       // exp(-+ i pi m / H)
+                if (INV) w.im = -w.im;
+                const Cx<R> p = v[k], qv = v[k | (1 << lv)];
                 const R tr = w.re * qv.re - w.im * qv.im, ti = w.re * qv.im + w.im * qv.re;
                 v[k] = {p.re + tr, p.im + ti};
-                v[k | (1 << l)] = {p.re - tr, p.im - ti};
+                v[k | (1 << lv)] = {p.re - tr, p.im - ti};
             }
         }
 #pragma unroll
@@ -85,15 +102,15 @@ LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s)
     __syncthreads();
 }
 
-// FFT of the two lines (bit-reversed input order, loaded and synchronised by the caller):
+// FFT of `lines` lines (bit-reversed input order, loaded and synchronised by the caller):
 // passes of three stages, the last one of one or two.
-template <class R>
-LB_DEV void fft2_lines(Cx<R>* z, const Cx<R>* tw, int n, int logn)
+template <class R, bool INV>
+LB_DEV void fft_lines(Cx<R>* z, const Cx<R>* tw, int n, int logn, int lines)
 {
     int s = 0;
-    for (; s + 3 <= logn; s += 3) fft_pass<R, 3>(z, tw, n, logn, s);
-    if (logn - s == 2) fft_pass<R, 2>(z, tw, n, logn, s);
-    else if (logn - s == 1) fft_pass<R, 1>(z, tw, n, logn, s);
+    for (; s + 3 <= logn; s += 3) fft_pass<R, 3, INV>(z, tw, n, logn, s, lines);
+    if (logn - s == 2) fft_pass<R, 2, INV>(z, tw, n, logn, s, lines);
+    else if (logn - s == 1) fft_pass<R, 1, INV>(z, tw, n, logn, s, lines);
 }
 
 // round(|k|) of the mode (kx, ky) (signed wavenumbers), in exact integer arithmetic: an FP32
@@ -110,117 +127,162 @@ LB_DEV int shell_of(int kx, int ky)
 
 LB_DEV int signed_k(int k, int n) { return k < n / 2 ? k : k - n; }
 
-// rows, forward: moments of every node of row y, DFT along x -> spec[a][y][kx]
+// rows, forward: moments of every node of row y, w = u_x + i u_y, DFT along x -> spec[y][kx]
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) k_sc_rows_fwd(const T* buf, Geom g, int logn,
+                                                     const Cx<typename Store<T>::Real>* tw,
                                                      Cx<typename Store<T>::Real>* spec)
 {
     using R = typename Store<T>::Real;
     extern __shared__ __align__(16) unsigned char sc_smem[];
     const int n = g.nx, y = blockIdx.x;
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n);
-    Cx<R>* tw = z + 2 * ls;
-    twiddles(tw, n, R(-1));
+    Cx<R>* tws = z + line_stride(n);
+    load_twiddles(tws, tw, n);
+#pragma unroll 2
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
+        Nbr nb = make_nbr_2d<sizeof(T)>(g, x, y);
         R f[9], Fz[3] = {R(0), R(0), R(0)};
         load_node<D2Q9, MODE>(buf, g, nb, x + n * y, f);
         const NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
-        const int r = bitrev(x, logn);
-        z[pz(r)] = {m.ux, R(0)};
-        z[ls + pz(r)] = {m.uy, R(0)};
+        z[pz(bitrev(x, logn))] = {m.ux, m.uy};
     }
     __syncthreads();
-    fft2_lines(z, tw, n, logn);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        spec[(int64_t)y * n + k] = z[pz(k)];
-        spec[((int64_t)n + y) * n + k] = z[ls + pz(k)];
-    }
+    fft_lines<R, false>(z, tws, n, logn, 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) spec[(int64_t)y * n + k] = z[pz(k)];
 }
 
-// first |ky| in [0, n/2] whose mode (kx, ky) lies in shell s or above (the shell grows with |ky|)
+// first |ky| in [0, n/2 + 1] whose mode (kx, ky) lies in shell s or above (the shell grows
+// with |ky|): shell_of is floor(sqrt(m) + 1/2), so for s >= 1 the condition is
+// 4 (kx^2 + ky^2) >= (2s - 1)^2, solved for ky in integers (an FP32 square root, then exact
+// corrections)
 LB_DEV int first_m(int kxs, int s, int n)
 {
-    int lo = 0, hi = n / 2 + 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (shell_of(kxs, mid) >= s) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+    if (s <= 0) return 0;
+    const int d = (2 * s - 1) * (2 * s - 1) - 4 * kxs * kxs;  // need 4 ky^2 >= d
+    if (d <= 0) return 0;
+    int ky = (int)ceilf(0.5f * sqrtf((float)d));
+    while (ky > 0 && 4 * (ky - 1) * (ky - 1) >= d) --ky;
+    while (4 * ky * ky < d) ++ky;
+    return ky < n / 2 + 1 ? ky : n / 2 + 1;
 }
 
-// columns, forward: DFT along y of column kx, modal energies, shell sums of the column into
-// partials[s][kx] (the modes of shell s in this column are one run of |ky|; summed in order
-// of |ky|, +ky before -ky)
+// load the C columns kx0 .. kx0 + C - 1 of spec into lines 0 .. C - 1 (bit-reversed order along
+// y), each value times G of its shell if grad is given: thread t takes row t / C, column t % C,
+// so the threads of a warp read runs of C adjacent values of a row
 template <class R>
-__global__ void __launch_bounds__(256) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, double* partials)
+LB_DEV void load_columns(Cx<R>* z, const Cx<R>* spec, int n, int logn, int kx0, int C, const double* grad)
+{
+    const int ls = line_stride(n), K = n / 2, total = n * C;
+    constexpr int U = 4;  // loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
+        Cx<R> v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < total) {
+                const int y = t / C, c = t - y * C;
+                v[u] = spec[(int64_t)y * n + kx0 + c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < total) {
+                const int y = t / C, c = t - y * C;
+                if (grad) {
+                    const int sh = shell_of(signed_k(kx0 + c, n), signed_k(y, n));
+                    const R G = sh < K ? (R)__ldg(grad + sh) : R(0);
+                    v[u].re *= G;
+                    v[u].im *= G;
+                }
+                z[c * ls + pz(bitrev(y, logn))] = v[u];
+            }
+        }
+    }
+}
+
+template <class R>
+LB_DEV void store_columns(const Cx<R>* z, Cx<R>* spec, int n, int kx0, int C)
+{
+    const int ls = line_stride(n);
+    for (int t = threadIdx.x; t < n * C; t += blockDim.x) {
+        const int y = t / C, c = t - y * C;
+        spec[(int64_t)y * n + kx0 + c] = z[c * ls + pz(y)];
+    }
+}
+
+// columns, forward: DFT along y of the block's C columns, then the shell sums of |W|^2 / (2 N^2)
+// over those columns into partials[s][block] (per column the modes of shell s are one run of
+// |ky|, summed in order of |ky|, +ky before -ky; the columns in order)
+template <class R>
+__global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, int C, const Cx<R>* tw,
+                                                     double* partials)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n);
-    Cx<R>* tw = z + 2 * ls;
-    double* e = reinterpret_cast<double*>(tw + n / 2);
-    const int kx = blockIdx.x, K = n / 2;
-    twiddles(tw, n, R(-1));
-    for (int y = threadIdx.x; y < n; y += blockDim.x) {
-        const int r = bitrev(y, logn);
-        z[pz(r)] = spec[(int64_t)y * n + kx];
-        z[ls + pz(r)] = spec[((int64_t)n + y) * n + kx];
-    }
+    const int ls = line_stride(n), K = n / 2, kx0 = blockIdx.x * C, nblk = gridDim.x;
+    Cx<R>* tws = z + C * ls;
+    load_twiddles(tws, tw, n);
+    load_columns<R>(z, spec, n, logn, kx0, C, nullptr);
     __syncthreads();
-    fft2_lines(z, tw, n, logn);
-    const double inv_n4 = 1.0 / ((double)n * n * (double)n * n);
-    for (int ky = threadIdx.x; ky < n; ky += blockDim.x) {
-        const Cx<R> a = z[pz(ky)], b = z[ls + pz(ky)];
-        spec[(int64_t)ky * n + kx] = a;
-        spec[((int64_t)n + ky) * n + kx] = b;
-        e[ky] = 0.5 * ((double)a.re * a.re + (double)a.im * a.im + (double)b.re * b.re + (double)b.im * b.im) * inv_n4;
-    }
-    __syncthreads();
-    const int kxs = signed_k(kx, n);
+    fft_lines<R, false>(z, tws, n, logn, C);
+    store_columns<R>(z, spec, n, kx0, C);
+    // modal energies |W|^2 and the runs' sums in the arithmetic type (a few to a few hundred
+    // terms; FP64 is a slow pipe on this part), the block's total per shell in FP64
+    const double scale = 0.5 / ((double)n * n * (double)n * n);
     for (int s = threadIdx.x; s < K; s += blockDim.x) {
-        const int m0 = first_m(kxs, s, n), m1 = first_m(kxs, s + 1, n);
         double acc = 0.0;
-        for (int m = m0; m < m1; ++m) {
-            acc += e[m];
-            if (m > 0 && m < n / 2) acc += e[n - m];
+        for (int c = 0; c < C; ++c) {
+            const Cx<R>* line = z + c * ls;
+            const int kxs = signed_k(kx0 + c, n);
+            const int m0 = first_m(kxs, s, n), m1 = first_m(kxs, s + 1, n);
+            R run = R(0);
+            for (int m = m0; m < m1; ++m) {
+                const Cx<R> a = line[pz(m)];
+                run += a.re * a.re + a.im * a.im;
+                if (m > 0 && m < n / 2) {
+                    const Cx<R> b = line[pz(n - m)];
+                    run += b.re * b.re + b.im * b.im;
+                }
+            }
+            acc += (double)run * scale;
         }
-        partials[(int64_t)s * n + kx] = acc;
+        partials[(int64_t)s * nblk + blockIdx.x] = acc;
     }
 }
 
-// shells: sigma_s = sum over the columns (one warp per shell: lane l takes kx = l, l + 32, ...
-// into four running sums in a fixed order, then a fixed shuffle tree), dR/dsigma_s and the
-// shell's term of R
-__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, const double* sigma0, double c,
-                                                   double* sigma, double* grad, double* r2)
+// shells: sigma_s = sum over the column blocks (one warp per shell: lane l takes blocks l, l + 32,
+// ... into four running sums in a fixed order, then a fixed shuffle tree), dR/dsigma_s and the
+// shell's term of R. l0_s = ln max(sigma0_s, c) comes from the host; the logarithm of sigma and
+// the gradient run in the arithmetic type R (the FP64 pipe is slow on this part, and FP32
+// storage needs no more).
+template <class R>
+__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
+                                                   double c, double* sigma, double* grad, double* r2)
 {
     const int K = n / 2, lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= K) return;
-    // four independent running sums per lane keep four loads in flight
-    const double* p = partials + (int64_t)s * n;
+    const double* p = partials + (int64_t)s * nblk;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int kx = lane;
-    for (; kx + 96 < n; kx += 128) {
-        a0 += p[kx];
-        a1 += p[kx + 32];
-        a2 += p[kx + 64];
-        a3 += p[kx + 96];
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+        a0 += p[b];
+        a1 += p[b + 32];
+        a2 += p[b + 64];
+        a3 += p[b + 96];
     }
-    for (; kx < n; kx += 32) a0 += p[kx];
+    for (; b < nblk; b += 32) a0 += p[b];
     double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane != 0) return;
     sigma[s] = acc;
-    if (sigma0) {
-        const double l0 = log(fmax(sigma0[s], c));
-        const double d = log(fmax(acc, c)) - l0;
-        r2[s] = d * d;
-        grad[s] = acc > c ? 2.0 * (log(acc) - l0) / acc : 0.0;
+    if (l0) {
+        const R d = log((R)fmax(acc, c)) - (R)l0[s];
+        r2[s] = (double)d * (double)d;
+        grad[s] = acc > c ? (double)(R(2) * d / (R)acc) : 0.0;
     }
 }
 
@@ -237,56 +299,40 @@ LB_DEV void sum_cost(const double* r2, int K, double* cost)
 // cost R = sum_s r2[s] (one warp, fixed order)
 __global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost) { sum_cost(r2, K, cost); }
 
-// columns, inverse: multiply by G(k), inverse DFT along y; block 0's first warp also totals
-// the cost R (cost non-null)
+// columns, inverse: multiply by G(k), inverse DFT along y of the block's C columns; block 0's
+// first warp also totals the cost R (cost non-null)
 template <class R>
-__global__ void __launch_bounds__(256) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const double* grad,
-                                                     const double* r2, double* cost)
+__global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int logn, int C, const Cx<R>* tw,
+                                                     const double* grad, const double* r2, double* cost)
 {
     if (cost && blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n);
-    Cx<R>* tw = z + 2 * ls;
-    const int kx = blockIdx.x, K = n / 2, kxs = signed_k(kx, n);
-    twiddles(tw, n, R(1));
-    for (int ky = threadIdx.x; ky < n; ky += blockDim.x) {
-        const int sh = shell_of(kxs, signed_k(ky, n));
-        const R G = sh < K ? (R)grad[sh] : R(0);
-        const int r = bitrev(ky, logn);
-        const Cx<R> a = spec[(int64_t)ky * n + kx], b = spec[((int64_t)n + ky) * n + kx];
-        z[pz(r)] = {G * a.re, G * a.im};
-        z[ls + pz(r)] = {G * b.re, G * b.im};
-    }
+    const int ls = line_stride(n), kx0 = blockIdx.x * C;
+    Cx<R>* tws = z + C * ls;
+    load_twiddles(tws, tw, n);
+    load_columns<R>(z, spec, n, logn, kx0, C, grad);
     __syncthreads();
-    fft2_lines(z, tw, n, logn);
-    for (int y = threadIdx.x; y < n; y += blockDim.x) {
-        spec[(int64_t)y * n + kx] = z[pz(y)];
-        spec[((int64_t)n + y) * n + kx] = z[ls + pz(y)];
-    }
+    fft_lines<R, true>(z, tws, n, logn, C);
+    store_columns<R>(z, spec, n, kx0, C);
 }
 
-// rows, inverse: inverse DFT along x, du_a = scale Re(.), scale = -kappa / N^2
+// rows, inverse: inverse DFT along x, du_x = scale Re(.), du_y = scale Im(.), scale = -kappa / N^2
 template <class R>
-__global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, int logn, R scale, R* du,
-                                                     int64_t plane)
+__global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, int logn, const Cx<R>* tw, R scale,
+                                                     R* du, int64_t plane)
 {
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n);
-    Cx<R>* tw = z + 2 * ls;
+    Cx<R>* tws = z + line_stride(n);
     const int y = blockIdx.x;
-    twiddles(tw, n, R(1));
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int r = bitrev(k, logn);
-        z[pz(r)] = spec[(int64_t)y * n + k];
-        z[ls + pz(r)] = spec[((int64_t)n + y) * n + k];
-    }
+    load_twiddles(tws, tw, n);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) z[pz(bitrev(k, logn))] = spec[(int64_t)y * n + k];
     __syncthreads();
-    fft2_lines(z, tw, n, logn);
+    fft_lines<R, true>(z, tws, n, logn, 1);
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
         du[(int64_t)y * n + x] = scale * z[pz(x)].re;
-        du[plane + (int64_t)y * n + x] = scale * z[ls + pz(x)].re;
+        du[plane + (int64_t)y * n + x] = scale * z[pz(x)].im;
     }
 }
 
@@ -296,7 +342,7 @@ LB_DEV void shifted_bgk_node(const T* src, T* dst, const Geom& g, typename Store
                              typename Store<T>::Real dux, typename Store<T>::Real duy, unsigned* status)
 {
     using R = typename Store<T>::Real;
-    Nbr nb = make_nbr<sizeof(T)>(g, x, y, 0);
+    Nbr nb = make_nbr_2d<sizeof(T)>(g, x, y);
     const int n = x + g.nx * y;
     R f[9], feq[9], Fz[3] = {R(0), R(0), R(0)};
     load_node<D2Q9, MODE>(src, g, nb, n, f);
@@ -317,30 +363,44 @@ LB_DEV void shifted_bgk_node(const T* src, T* dst, const Geom& g, typename Store
 // one-kernel AA update)
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) k_sc_rows_inv_step(const Cx<typename Store<T>::Real>* spec, int logn,
+                                                          const Cx<typename Store<T>::Real>* tw,
                                                           typename Store<T>::Real scale, const T* src, T* dst,
                                                           Geom g, typename Store<T>::Real omega, unsigned* status)
 {
     using R = typename Store<T>::Real;
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int n = g.nx, ls = line_stride(n);
-    Cx<R>* tw = z + 2 * ls;
+    const int n = g.nx;
+    Cx<R>* tws = z + line_stride(n);
     const int y = blockIdx.x;
-    twiddles(tw, n, R(1));
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int r = bitrev(k, logn);
-        z[pz(r)] = spec[(int64_t)y * n + k];
-        z[ls + pz(r)] = spec[((int64_t)n + y) * n + k];
-    }
+    load_twiddles(tws, tw, n);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) z[pz(bitrev(k, logn))] = spec[(int64_t)y * n + k];
     __syncthreads();
-    fft2_lines(z, tw, n, logn);
+    fft_lines<R, true>(z, tws, n, logn, 1);
+#pragma unroll 2
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        const R dux = scale * z[pz(x)].re, duy = scale * z[ls + pz(x)].re;
-        shifted_bgk_node<T, MODE>(src, dst, g, omega, x, y, dux, duy, status);
+        const Cx<R> d = z[pz(x)];
+        shifted_bgk_node<T, MODE>(src, dst, g, omega, x, y, scale * d.re, scale * d.im, status);
     }
 }
 
-static int line_threads(int n) { return n < 256 ? n : 256; }
+// threads of a block that FFTs `lines` lines of n points (passes of three stages: n / 8 sets
+// per line, one per thread up to 512)
+static int fft_threads(int n, int lines)
+{
+    const int t = lines * n / 8;
+    return t < 32 ? 32 : (t > 512 ? 512 : t);
+}
+
+// columns per column block: four (whole 32-byte sectors of FP32 values, two of FP64), fewer
+// where four lines would not fit in shared memory
+template <class R>
+static int column_block(int n)
+{
+    int C = 4;
+    while (C > 1 && (size_t)C * line_stride(n) * sizeof(Cx<R>) > 160 * 1024) C >>= 1;
+    return C < n ? C : n;
+}
 
 template <class K>
 static cudaError_t smem_attr(K kernel, size_t bytes)
@@ -355,25 +415,30 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
 {
     using R = typename Store<T>::Real;
     const OpArgs& a = s.a;
-    const int n = s.n, logn = s.logn, th = line_threads(n), K = n / 2;
+    const int n = s.n, logn = s.logn, K = n / 2;
+    const int C = column_block<R>(n), nblk = n / C;
+    // row blocks also load and step the row's nodes: a thread per node up to 256
+    const int th_row = n < 256 ? (n < 32 ? 32 : n) : 256, th_col = fft_threads(n, C);
     Cx<R>* spec = (Cx<R>*)s.spec;
-    const size_t lines = (2 * (size_t)line_stride(n) + (size_t)K) * sizeof(Cx<R>);  // two lines + twiddles
+    const Cx<R>* tw = (const Cx<R>*)s.tw;
+    const size_t row_smem = ((size_t)line_stride(n) + (size_t)K) * sizeof(Cx<R>);  // one line + twiddles
+    const size_t col_smem = ((size_t)C * line_stride(n) + (size_t)K) * sizeof(Cx<R>);
     cudaError_t e;
     const T* buf = (const T*)a.src;
     if (a.mode == AB) {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AB>, lines)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AB><<<n, th, lines, a.stream>>>(buf, a.g, logn, spec);
+        if ((e = smem_attr(k_sc_rows_fwd<T, AB>, row_smem)) != cudaSuccess) return e;
+        k_sc_rows_fwd<T, AB><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
     } else if (a.mode == AA_EVEN) {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AA_EVEN>, lines)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AA_EVEN><<<n, th, lines, a.stream>>>(buf, a.g, logn, spec);
+        if ((e = smem_attr(k_sc_rows_fwd<T, AA_EVEN>, row_smem)) != cudaSuccess) return e;
+        k_sc_rows_fwd<T, AA_EVEN><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
     } else {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AA_ODD>, lines)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AA_ODD><<<n, th, lines, a.stream>>>(buf, a.g, logn, spec);
+        if ((e = smem_attr(k_sc_rows_fwd<T, AA_ODD>, row_smem)) != cudaSuccess) return e;
+        k_sc_rows_fwd<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
     }
-    const size_t cols = lines + (size_t)n * sizeof(double);
-    if ((e = smem_attr(k_sc_cols_fwd<R>, cols)) != cudaSuccess) return e;
-    k_sc_cols_fwd<R><<<n, th, cols, a.stream>>>(spec, n, logn, s.partials);
-    k_sc_shells<<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, s.sigma0, s.cutoff, s.sigma, s.grad, s.r2);
+    if ((e = smem_attr(k_sc_cols_fwd<R>, col_smem)) != cudaSuccess) return e;
+    k_sc_cols_fwd<R><<<nblk, th_col, col_smem, a.stream>>>(spec, n, logn, C, tw, s.partials);
+    k_sc_shells<R><<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, nblk, s.sigma0 ? s.l0 : nullptr, s.cutoff,
+                                                      s.sigma, s.grad, s.r2);
     *launches += 3;
     if (!s.sigma0) return cudaGetLastError();
     if (!s.du && !step) {
@@ -381,30 +446,31 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
         *launches += 1;
         return cudaGetLastError();
     }
-    if ((e = smem_attr(k_sc_cols_inv<R>, lines)) != cudaSuccess) return e;
-    k_sc_cols_inv<R><<<n, th, lines, a.stream>>>(spec, n, logn, s.grad, s.r2, s.cost);
+    if ((e = smem_attr(k_sc_cols_inv<R>, col_smem)) != cudaSuccess) return e;
+    k_sc_cols_inv<R><<<nblk, th_col, col_smem, a.stream>>>(spec, n, logn, C, tw, s.grad, s.r2, s.cost);
     const R scale = (R)(-s.kappa / ((double)n * n * (double)n * n));
     if (step) {  // inverse rows fused with the step
         const T* src = (const T*)a.src;
         T* dst = (T*)a.dst;
         const R om = (R)a.omega;
         if (a.mode == AB) {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AB>, lines)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AB><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om, a.status);
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AB>, row_smem)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AB><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g, om,
+                                                                         a.status);
         } else if (a.mode == AA_EVEN) {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_EVEN>, lines)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AA_EVEN><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om,
-                                                                       a.status);
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_EVEN>, row_smem)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AA_EVEN><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g,
+                                                                              om, a.status);
         } else {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_ODD>, lines)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AA_ODD><<<n, th, lines, a.stream>>>(spec, logn, scale, src, dst, a.g, om,
-                                                                      a.status);
+            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_ODD>, row_smem)) != cudaSuccess) return e;
+            k_sc_rows_inv_step<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g,
+                                                                             om, a.status);
         }
         *launches += 2;
         return cudaGetLastError();
     }
-    if ((e = smem_attr(k_sc_rows_inv<R>, lines)) != cudaSuccess) return e;
-    k_sc_rows_inv<R><<<n, th, lines, a.stream>>>(spec, n, logn, scale, (R*)s.du, a.g.plane);
+    if ((e = smem_attr(k_sc_rows_inv<R>, row_smem)) != cudaSuccess) return e;
+    k_sc_rows_inv<R><<<n, th_row, row_smem, a.stream>>>(spec, n, logn, tw, scale, (R*)s.du, a.g.plane);
     *launches += 2;
     return cudaGetLastError();
 }
@@ -414,6 +480,7 @@ static cudaError_t shift_or_step(const SpectralArgs& s, int* launches, bool step
     if (s.a.g.nx != s.n || s.a.g.ny != s.n || s.a.g.nz != 1 || s.n < 4 || s.n > kSpecMaxN || (1 << s.logn) != s.n)
         return cudaErrorInvalidValue;
     if (step && !s.sigma0) return cudaErrorInvalidValue;
+    if (!s.tw) return cudaErrorInvalidValue;
     switch (s.a.storage) {
     case S_F64: return shift_typed<double>(s, launches, step);
     case S_F32: return shift_typed<float>(s, launches, step);
@@ -426,5 +493,14 @@ static cudaError_t shift_or_step(const SpectralArgs& s, int* launches, bool step
 cudaError_t spectral_shift(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, false); }
 
 cudaError_t spectral_step(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, true); }
+
+cudaError_t spectral_twiddles(void* tw, int n, int storage, cudaStream_t st)
+{
+    if (n < 4 || n > kSpecMaxN) return cudaErrorInvalidValue;
+    const int blocks = (n / 2 + 127) / 128;
+    if (storage == S_F64) k_sc_twiddles<double><<<blocks, 128, 0, st>>>((Cx<double>*)tw, n);
+    else k_sc_twiddles<float><<<blocks, 128, 0, st>>>((Cx<float>*)tw, n);
+    return cudaGetLastError();
+}
 
 }  // namespace lb

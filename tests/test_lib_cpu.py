@@ -100,6 +100,11 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lb_spectrum(None, sig, None) == 1
     assert lib.lb_spectral_shift(None, None, 0) == 1
     assert lib.lb_set_mlp(None, None, 545, 0) == 1
+    nbytes = ctypes.c_int64()
+    assert lib.lb_halo_bytes(None, ctypes.byref(nbytes)) == 1
+    assert lib.lb_halo_pack(None, 0, None) == 1
+    assert lib.lb_halo_unpack(None, 1, None) == 1
+    assert lib.lb_reduce_slab(None, 1, 1, (ctypes.c_double * 6)()) == 1
     lib.lb_destroy(None)
 
 
