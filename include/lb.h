@@ -145,7 +145,9 @@ typedef struct {
                              1, 2 or 4 = forced, falling back to the next smaller shape the grid
                              allows (2 needs an even nx; 4 needs half storage and nx % 4 == 0).
                              LB_NONE and the learned collisions always run one node per thread.
-                             Every shape gives bit-identical results */
+                             The shapes agree to the last bits of the arithmetic type (the
+                             compiler contracts multiply-adds differently per shape); one
+                             shape always gives the same bits */
 } lb_options;
 
 /* Fill *opt with the defaults listed above (learned_tc = 0, graphs = 1, nodes_per_thread = 0). */
@@ -218,20 +220,26 @@ LB_API lb_status lb_step(lb_ctx* ctx, int64_t n);
 LB_API lb_status lb_moments(lb_ctx* ctx, void* rho, void* u, lb_mem mem);
 
 /* Global sums of the current state, accumulated in FP64 in a fixed order
- * (deterministic): out[0] = sum rho, out[1..3] = sum rho u (x, y, z; z = 0 in 2D),
+ * (deterministic): the mass and momentum that the collision conserves (Sec. 2.1) and the
+ * kinetic energy the paper reports as its observable (Sec. 2.2, the energy of the Taylor-Green
+ * vortex): out[0] = sum rho, out[1..3] = sum rho u (x, y, z; z = 0 in 2D),
  * out[4] = (1/2N) sum |u|^2 (incompressible kinetic energy), out[5] = (1/2N) sum rho |u|^2.
  * out is host memory; the call synchronises the stream. */
 LB_API lb_status lb_reduce(lb_ctx* ctx, double out[6]);
 
-/* Copy the current pre-collision state out as f[Q][N] (natural layout, unshifted). */
+/* Copy the current pre-collision state f^n of Eq. 1 out as f[Q][N] (natural layout,
+ * unshifted), e.g. for a checkpoint; the paper has no counterpart for the copy itself. */
 LB_API lb_status lb_get_populations(lb_ctx* ctx, void* f, lb_mem mem);
 
-/* Replace the state by f[Q][N] (pre-collision, natural layout). Resets the step
- * counter and any recording. */
+/* Replace the state by f[Q][N], taken as the pre-collision f^n of Eq. 1 (natural layout;
+ * a checkpoint's restart or an arbitrary initial state, where lb_init_from_moments gives only
+ * equilibria). Resets the step counter and any recording. */
 LB_API lb_status lb_set_populations(lb_ctx* ctx, const void* f, lb_mem mem);
 
 /* Synchronise the stream and report LB_ERR_UNSTABLE if any node of any step since
- * the last check had a non-finite or non-positive density (the flag is then cleared). */
+ * the last check had a non-finite or non-positive density (the flag is then cleared).
+ * Failure detection of this library; the paper has no counterpart (a BGK run that leaves its
+ * stability range, Sec. 3.1, shows up here). */
 LB_API lb_status lb_check(lb_ctx* ctx);
 
 /* Steps taken since the last initialisation. */
