@@ -29,6 +29,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 from dataclasses import asdict, dataclass, field
 
@@ -39,6 +40,7 @@ import lbinputs
 
 from . import _lib
 from .lattice import Lattice, adam_update
+from .slab import allreduce_gradient
 
 
 def coarse_tau(tau_f: float) -> float:
@@ -124,12 +126,44 @@ def rollout_loss(lat: Lattice, s: Sample, horizon: int, grad=None):
     return L
 
 
-def mean_loss(lat: Lattice, samples, horizon: int):
-    return float(np.mean([rollout_loss(lat, s, horizon) for s in samples]))
+def rank_world(group) -> tuple[int, int]:
+    """(rank, world size) of a torch.distributed group; (0, 1) for group None (one process)."""
+    if group is None:
+        return 0, 1
+    import torch.distributed as dist
+    return dist.get_rank(group), dist.get_world_size(group)
 
 
-def train(cfg: TrainConfig, samples=None, extra=None, log=None):
-    """Train the network on the shear-layer samples; returns theta, extra and a history."""
+def sharded_mean(loss_of, items, group=None, g=None, device="cuda"):
+    """Data-parallel batch: rank r of `group` evaluates loss_of(item, g) for items r, r + world, ...
+    (every rank holds the same list), and every rank gets back the mean over all items. If g is
+    given, each call adds its item's dL/dtheta to g and g ends as the sum over all items on every
+    rank (FP64 all-reduce), so the update that follows is the same on every rank as in one process."""
+    rank, world = rank_world(group)
+    mine = items[rank::world]
+    Ls = [loss_of(it, g) for it in mine]
+    if world == 1:
+        return float(np.mean(Ls))
+    import torch.distributed as dist
+    if g is not None:
+        allreduce_gradient(g, group)
+    tot = torch.tensor([float(sum(Ls)), float(len(Ls))], dtype=torch.float64, device=device)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM, group=group)
+    return float(tot[0] / tot[1])
+
+
+def mean_loss(lat: Lattice, samples, horizon: int, group=None):
+    return sharded_mean(lambda s, _: rollout_loss(lat, s, horizon), samples, group)
+
+
+def train(cfg: TrainConfig, samples=None, extra=None, log=None, group=None):
+    """Train the network on the shear-layer samples; returns theta, extra and a history.
+
+    group: a torch.distributed process group for data-parallel training, or None for one
+    process. Every rank builds the same samples and draws the same batches (same seed); each
+    runs its share of a batch's rollouts and adjoints on its own GPU, the parameter gradients
+    are summed across the ranks, and every rank then takes the same Adam step. Held-out and
+    validation rollouts are shared out the same way."""
     if samples is None:
         samples, extra = make_shear_data(cfg)
     nc = cfg.n_fine // 2
@@ -145,8 +179,8 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
     rng = np.random.default_rng(cfg.seed)
     hist = {"train_loss": [], "holdout_loss": []}
     lat.set_mlp(torch.cat([theta, extra]))
-    base_hold = mean_loss(lat, hold, cfg.horizon)
-    base_val = mean_loss(lat, val, cfg.horizon)
+    base_hold = mean_loss(lat, hold, cfg.horizon, group)
+    base_val = mean_loss(lat, val, cfg.horizon, group)
     hist["holdout_loss"].append((0, base_hold))
     hist["val_loss"] = [(0, base_val)]
     best = (base_val, 0, theta.clone())  # early stopping on the validation loss
@@ -155,15 +189,15 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
         lat.set_mlp(torch.cat([theta, extra]))
         g = torch.zeros(_lib.n_theta(cfg.net), dtype=torch.float32, device="cuda")
         pick = rng.choice(len(train_set), size=min(cfg.batch, len(train_set)), replace=False)
-        Ls = [rollout_loss(lat, train_set[j], cfg.horizon, grad=g) for j in pick]
+        L = sharded_mean(lambda j, gr: rollout_loss(lat, train_set[j], cfg.horizon, grad=gr), list(pick), group, g)
         if not torch.isfinite(g).all():
             raise FloatingPointError(f"non-finite gradient at iteration {it}")
         adam_update(theta, m, v, g, it, lr=cfg.lr)
-        hist["train_loss"].append(float(np.mean(Ls)))
+        hist["train_loss"].append(L)
         if it % max(1, cfg.iters // 20) == 0 or it == cfg.iters:
             lat.set_mlp(torch.cat([theta, extra]))
-            hl = mean_loss(lat, hold, cfg.horizon)
-            vl = mean_loss(lat, val, cfg.horizon)
+            hl = mean_loss(lat, hold, cfg.horizon, group)
+            vl = mean_loss(lat, val, cfg.horizon, group)
             hist["holdout_loss"].append((it, hl))
             hist["val_loss"].append((it, vl))
             if vl < best[0]:
@@ -175,11 +209,11 @@ def train(cfg: TrainConfig, samples=None, extra=None, log=None):
     theta = best[2]
     hist["best_iter"] = best[1]
     lat.set_mlp(torch.cat([theta, extra]))
-    final_hold = mean_loss(lat, hold, cfg.horizon)
+    final_hold = mean_loss(lat, hold, cfg.horizon, group)
     lat.close()
     # the same held-out rollouts with the plain BGK operator (the method without the network)
     bgk = Lattice("D2Q9", (nc, nc, 1), tau_c, "bgk", storage=cfg.storage)
-    bgk_hold = mean_loss(bgk, hold, cfg.horizon)
+    bgk_hold = mean_loss(bgk, hold, cfg.horizon, group)
     bgk.close()
     hist.update({"holdout_loss_bgk": bgk_hold, "holdout_loss_learned": final_hold,
                  "holdout_gain": 1.0 - final_hold / bgk_hold})
@@ -283,10 +317,20 @@ def main():
     ap.add_argument("--net", choices=["learned", "learned3"], default="learned")
     ap.add_argument("--save", type=str, default=None, help="write theta + input scaling (805 / 545 floats) here")
     a = ap.parse_args()
+    group = None
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # launched by torchrun: one rank per GPU, data-parallel over the batch's rollouts
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+        group = dist.group.WORLD
+    rank0 = group is None or rank_world(group)[0] == 0
     cfg = TrainConfig(n_fine=a.n_fine, iters=a.iters, tau_fine=a.tau_fine, horizon=a.horizon,
                       spinup=max(1000, 4 * a.n_fine), snap_every=max(2 * a.horizon + 50, a.n_fine // 2), net=a.net)
     t0 = time.perf_counter()
-    theta, extra, hist = train(cfg, log=lambda s: print(s, flush=True))
+    theta, extra, hist = train(cfg, log=(lambda s: print(s, flush=True)) if rank0 else None, group=group)
+    if not rank0:
+        return
     res = {"train": {k: v for k, v in hist.items() if k != "train_loss"}, "config": asdict(cfg)}
     res["train"]["train_loss_first_last"] = [hist["train_loss"][0], hist["train_loss"][-1]]
     if a.save:

@@ -94,3 +94,60 @@ def test_layer_bookkeeping():
     assert torch.equal(with_ghosts(t, 4, 2, 6, 3), torch.tensor(with_ghosts(a, 4, 2, 6, 3)))
     s = normalise_sums([10.0, 1.0, 2.0, 3.0, 8.0, 16.0], 4)
     assert list(s) == [10.0, 1.0, 2.0, 3.0, 1.0, 2.0]
+
+
+def _fake_rollout(j, g):
+    """Stand-in for one rollout + adjoint: adds an item-dependent gradient, returns its loss."""
+    if g is not None:
+        g += (j + 1) * torch.arange(793, dtype=torch.float32) / 793.0
+    return float(j) ** 2
+
+
+BATCH = [5, 2, 7, 0, 3]  # five rollouts: the ranks' shares differ in size
+
+
+def _dp_rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2106_12929_gb300.training import rank_world, sharded_mean
+    group = dist.group.WORLD
+    calls = []
+    g = torch.zeros(793, dtype=torch.float32)
+    L = sharded_mean(lambda j, gr: calls.append(j) or _fake_rollout(j, gr), BATCH, group, g, device="cpu")
+    Lv = sharded_mean(_fake_rollout, BATCH, group, device="cpu")  # evaluation: no gradient
+    out[rank] = (rank_world(group), calls, L, Lv, g.tolist())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_data_parallel_batch_matches_one_process(world):
+    """training.sharded_mean over gloo ranks: each rank runs only its share of the batch, and
+    every rank ends with the one-process batch loss and summed parameter gradient."""
+    sys.path.insert(0, ROOT)
+    from paper_2106_12929_gb300.training import rank_world, sharded_mean
+    assert rank_world(None) == (0, 1)
+    g1 = torch.zeros(793, dtype=torch.float32)
+    L1 = sharded_mean(_fake_rollout, BATCH, None, g1, device="cpu")
+    assert L1 == np.mean([j * j for j in BATCH])
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_dp_rank, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    seen = []
+    for r in range(world):
+        rw, calls, L, Lv, g = out[r]
+        assert rw == (r, world)
+        assert calls == BATCH[r::world]
+        seen += calls
+        assert L == pytest.approx(L1, rel=1e-15) and Lv == pytest.approx(L1, rel=1e-15)
+        np.testing.assert_allclose(g, g1.numpy(), rtol=1e-6, atol=0)
+    assert sorted(seen) == sorted(BATCH)  # every rollout ran exactly once
