@@ -128,10 +128,11 @@ typedef struct {
                              and returns LB_ERR_UNSTABLE if a node went bad; 0 (default) = never */
     int record_every;     /* >0: lb_step records a checkpoint every record_every steps so that
                              lb_step_adjoint can run backwards (AB layout only); 0 = off */
-    int learned_tc;       /* LB_LEARNED_MRT(3), FP32/FP16/BF16 storage: 1 = evaluate the network's
-                             layers with single BF16 operands and the hardware tanh (an inference
-                             option: lb_step_adjoint and training use the default path); 0
-                             (default) = the FP32 network: its matrix products on the tensor cores,
+    int learned_tc;       /* LB_LEARNED_MRT(3), FP32/FP16/BF16 storage: 1 = evaluate the network in
+                             half precision (FP16 operands, FP16 accumulation in the hidden layers,
+                             the hardware tanh; an inference option: lb_step_adjoint and training
+                             use the default path; grids up to about 238 million nodes, 9 x the
+                             padded plane below 2^31); 0 (default) = the FP32 network: its matrix products on the tensor cores,
                              each operand split into two FP16 terms and multiplied as
                              hi.hi + hi.lo + lo.hi (about 2^-21 relative; operands scaled by
                              powers of two into FP16 range), an FP32 tanh, FP32 everything else */
@@ -159,8 +160,9 @@ LB_API void lb_default_options(lb_options* opt);
  * tau_n of Sec. 3.1. opt may be NULL (defaults). On success *out owns the memory
  * until lb_destroy. Errors: LB_ERR_ARG (dims, tau, enum values, option values),
  * LB_ERR_UNSUPPORTED (the learned collisions or MRT on a stencil other than D2Q9, KBC on
- * D3Q19, learned_tc without a learned collision or with FP64 storage, record_every with the
- * AA layout or with TRT, KBC or MRT), LB_ERR_OOM, LB_ERR_CUDA. */
+ * D3Q19, learned_tc without a learned collision, with FP64 storage or on a grid whose
+ * 9 x padded plane reaches 2^31, record_every with the AA layout or with TRT, KBC or MRT),
+ * LB_ERR_OOM, LB_ERR_CUDA. */
 LB_API lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], double tau,
                     lb_collision collision, const lb_options* opt);
 

@@ -362,6 +362,8 @@ lb_status lb_create(lb_ctx** out, lb_stencil stencil, const int64_t dims[3], dou
         return fail(LB_ERR_ARG, "nodes_per_thread must be 0, 1, 2 or 4");
     if (o.learned_tc && (!is_learned(coll) || o.storage == LB_F64))
         return fail(LB_ERR_UNSUPPORTED, "learned_tc needs a learned collision with FP32 or half storage");
+    if (o.learned_tc && 9 * ((dims[0] * dims[1] * dims[2] + 63) / 64 * 64) > (int64_t)0x7FFFFFFF)
+        return fail(LB_ERR_UNSUPPORTED, "learned_tc addresses the populations with 32-bit offsets: 9 x plane must stay below 2^31");
     const int D = stencil == LB_D2Q9 ? 2 : 3;
     for (int a = 0; a < 3; ++a)
         if (dims[a] < 1 || dims[a] > 65535) return fail(LB_ERR_ARG, "dims[%d] = %lld out of [1, 65535]", a, (long long)dims[a]);

@@ -126,189 +126,6 @@ cudaError_t learned_inputs_d2q9(const OpArgs& a)
     }
 }
 
-// ---------------------------------------------------------------- tensor-core network
-// The two hidden layers as warp-level matrix products on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation). A warp's 32 nodes are the rows
-// (two 16-row tiles); layer 1 multiplies [32 x 16] inputs (6 used) by W1^T [16 x 24],
-// layer 2 [32 x 32] activations (24 used) by W2^T [32 x 24]. The accumulator fragment of
-// layer 1 has exactly the layout of layer 2's A fragment, so the activations never leave
-// the registers; only the inputs go through shared memory. Layer 3 (24 -> 1) is an FP32
-// dot product reduced over the four lanes that share a row.
-struct NetFrag {
-    uint32_t w1[3][32];        // layer 1, n-tile t (hidden units 8t..8t+7): B register 0 per lane
-    uint32_t w2[3][2][2][32];  // layer 2, n-tile t, k-step s (k = 16s..16s+15), B register r per lane
-};
-
-static uint16_t bf16_bits(double v)
-{
-    float f = (float)v;
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
-    return (uint16_t)(u >> 16);
-}
-
-// B fragment of m16n8k16 (col-major B[k][n] = W[n][k]): lane (g = lane/4, q = lane%4)
-// holds k = 2q, 2q+1 (register 0) and 2q+8, 2q+9 (register 1) of column n = g.
-static NetFrag make_frag(const double* v)
-{
-    const double* W1 = v;
-    const double* W2 = v + kNetHidden * kNetIn + kNetHidden;
-    NetFrag fr;
-    for (int t = 0; t < 3; ++t)
-        for (int lane = 0; lane < 32; ++lane) {
-            const int g = lane >> 2, q = lane & 3, n = 8 * t + g;
-            auto w1 = [&](int k) { return k < kNetIn ? W1[n * kNetIn + k] : 0.0; };
-            fr.w1[t][lane] = (uint32_t)bf16_bits(w1(2 * q)) | ((uint32_t)bf16_bits(w1(2 * q + 1)) << 16);
-            for (int st = 0; st < 2; ++st)
-                for (int r = 0; r < 2; ++r) {
-                    const int k0 = 16 * st + 2 * q + 8 * r;
-                    auto w2 = [&](int k) { return k < kNetHidden ? W2[n * kNetHidden + k] : 0.0; };
-                    fr.w2[t][st][r][lane] = (uint32_t)bf16_bits(w2(k0)) | ((uint32_t)bf16_bits(w2(k0 + 1)) << 16);
-                }
-        }
-    return fr;
-}
-
-struct TcTable {
-    NetFrag frag;
-    float b1[kNetHidden], b2[kNetHidden], w3[kNetHidden];
-};
-
-size_t learned_tc_table_bytes() { return sizeof(TcTable); }
-
-void learned_tc_pack(const double* v, void* out)
-{
-    TcTable t;
-    t.frag = make_frag(v);
-    const double* b1 = v + kNetHidden * kNetIn;
-    const double* b2 = b1 + kNetHidden + kNetHidden * kNetHidden;
-    const double* w3 = b2 + kNetHidden;
-    for (int k = 0; k < kNetHidden; ++k) {
-        t.b1[k] = (float)b1[k];
-        t.b2[k] = (float)b2[k];
-        t.w3[k] = (float)w3[k];
-    }
-    std::memcpy(out, &t, sizeof(t));
-}
-
-LB_DEV void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-LB_DEV uint32_t pack_bf16(float lo, float hi)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *(const uint32_t*)&v;
-}
-
-// tanh of two packed BF16 values (one SFU instruction for both)
-LB_DEV uint32_t tanh_bf16x2(uint32_t x)
-{
-    uint32_t y;
-    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
-    return y;
-}
-
-LB_DEV float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
-LB_DEV float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
-
-template <class T, int MODE>
-__global__ void __launch_bounds__(128) k_learned_update_tc(const T* src, T* dst, Geom g, float omega, unsigned* status,
-                                                           const Net<float> net, const uint32_t* __restrict__ table)
-{
-    // the packed weights (fragment table, then b1, b2, W3) staged by coalesced loads
-    constexpr int kWords = (int)(sizeof(TcTable) / 4);
-    __shared__ uint32_t stab[kWords];
-    __shared__ uint32_t sx[4][32][4];  // per warp: 32 nodes x 8 BF16 inputs
-    for (int k = threadIdx.x; k < kWords; k += blockDim.x) stab[k] = table[k];
-    __syncthreads();
-    const uint32_t* sfrag = stab;
-    const float* sb = (const float*)(stab + sizeof(NetFrag) / 4);  // b1, b2, W3
-    const float* shift = net.v + kNetTheta;
-    const float* scale = shift + kNetIn;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = x < g.nx;  // every lane takes part in the warp's matrix products
-    const int y = blockIdx.y;
-    Nbr nb = make_nbr<sizeof(T)>(g, valid ? x : 0, y, 0);
-    const int n = x + g.nx * y;
-    float f[9];
-    if (valid) load_node<D2Q9, MODE>(src, g, nb, n, f);
-    else
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = 0.f;
-    LearnedNode<float> s;
-    float I[kNetIn];
-    learned_inputs(f, s, I);
-    float xin[kNetIn];
-#pragma unroll
-    for (int k = 0; k < kNetIn; ++k) xin[k] = (I[k] - shift[k]) * scale[k];
-    sx[warp][lane][0] = pack_bf16(xin[0], xin[1]);
-    sx[warp][lane][1] = pack_bf16(xin[2], xin[3]);
-    sx[warp][lane][2] = pack_bf16(xin[4], xin[5]);
-    sx[warp][lane][3] = 0u;
-    __syncwarp();
-    const int gq = lane >> 2, q = lane & 3;
-    float zp[4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        // layer 1: C[16 x 24] = X[16 x 16] W1^T + b1
-        const uint32_t a0 = sx[warp][16 * m + gq][q], a1 = sx[warp][16 * m + gq + 8][q];
-        uint32_t h1[3][2];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            float c[4];
-            c[0] = c[2] = sb[8 * t + 2 * q];
-            c[1] = c[3] = sb[8 * t + 2 * q + 1];
-            mma_bf16(c, a0, a1, 0u, 0u, sfrag[t * 32 + lane], 0u);
-            h1[t][0] = tanh_bf16x2(pack_bf16(c[0], c[1]));  // row gq
-            h1[t][1] = tanh_bf16x2(pack_bf16(c[2], c[3]));  // row gq + 8
-        }
-        // layer 2: C[16 x 24] = H1[16 x 32] W2^T + b2, H1 straight from layer 1's accumulators
-        float zr0 = 0.f, zr1 = 0.f;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            float c[4];
-            c[0] = c[2] = sb[kNetHidden + 8 * t + 2 * q];
-            c[1] = c[3] = sb[kNetHidden + 8 * t + 2 * q + 1];
-            const uint32_t* w2 = sfrag + 3 * 32 + t * 128;
-            mma_bf16(c, h1[0][0], h1[0][1], h1[1][0], h1[1][1], w2[lane], w2[32 + lane]);
-            mma_bf16(c, h1[2][0], h1[2][1], 0u, 0u, w2[64 + lane], w2[96 + lane]);
-            const uint32_t h20 = tanh_bf16x2(pack_bf16(c[0], c[1]));
-            const uint32_t h21 = tanh_bf16x2(pack_bf16(c[2], c[3]));
-            const float w3a = sb[2 * kNetHidden + 8 * t + 2 * q], w3b = sb[2 * kNetHidden + 8 * t + 2 * q + 1];
-            zr0 += w3a * bf16_lo(h20) + w3b * bf16_hi(h20);
-            zr1 += w3a * bf16_lo(h21) + w3b * bf16_hi(h21);
-        }
-        zp[2 * m] = zr0;
-        zp[2 * m + 1] = zr1;
-    }
-    // layer 3: sum the four lanes of each row, then bring row r's value to lane r
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        zp[k] += __shfl_xor_sync(0xffffffffu, zp[k], 1);
-        zp[k] += __shfl_xor_sync(0xffffffffu, zp[k], 2);
-    }
-    const int srcl = 4 * (lane & 7);
-    const float v0 = __shfl_sync(0xffffffffu, zp[0], srcl), v1 = __shfl_sync(0xffffffffu, zp[1], srcl);
-    const float v2 = __shfl_sync(0xffffffffu, zp[2], srcl), v3 = __shfl_sync(0xffffffffu, zp[3], srcl);
-    const int sel = lane >> 3;
-    const float z = (sel == 0 ? v0 : sel == 1 ? v1 : sel == 2 ? v2 : v3) + net.v[kNetTheta - 1];
-    s.z = z;
-    s.ez = expf(z);
-    s.omg = recip(s.ez + 0.5f);
-    if (!valid) return;
-    learned_post(s, s.omg, omega, f);
-    store_node<D2Q9, MODE>(dst, g, nb, n, f);
-    if (!(s.m.rho > 0.f && s.m.rho < 1e30f)) atomicOr(status, 1u);
-}
-
 // ---------------------------------------------------------------- adjoint
 constexpr int kAdjBlock = 128;
 
@@ -595,137 +412,6 @@ __global__ void __launch_bounds__(128) k_learned3_update(const T* src, T* dst, G
     if (!(s.m.rho > R(0) && s.m.rho < R(1e30))) atomicOr(status, 1u);
 }
 
-// The three-output network on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
-// accumulation), laid out like k_learned_update_tc: a warp's 32 nodes are two 16-row tiles;
-// layer 1 multiplies [32 x 16] inputs (6 used) by W1^T [16 x 56] (53 used, seven n-tiles),
-// layer 2 the tanh activations [32 x 64] (56 from layer 1's accumulators, in place as A
-// fragments) by W2^T [64 x 8] (3 used). Outputs: lanes 4g and 4g + 1 hold columns 0, 1 and
-// 2, 3 of rows g and g + 8.
-constexpr int kNet3Tiles = (kNet3Hidden + 7) / 8;  // 7
-struct Net3Frag {
-    uint32_t w1[kNet3Tiles][32];  // layer 1, n-tile t: B register 0 per lane
-    uint32_t w2[4][2][32];        // layer 2, k-step s (k = 16s..16s+15): B registers 0, 1 per lane
-    float b1[8 * kNet3Tiles];
-    float b2[8];
-};
-
-size_t learned3_tc_table_bytes() { return sizeof(Net3Frag); }
-
-void learned3_tc_pack(const double* v, void* out)
-{
-    const double* W1 = v;
-    const double* b1 = W1 + kNet3Hidden * kNetIn;
-    const double* W2 = b1 + kNet3Hidden;
-    const double* b2 = W2 + 3 * kNet3Hidden;
-    Net3Frag fr;
-    for (int lane = 0; lane < 32; ++lane) {
-        const int g = lane >> 2, q = lane & 3;
-        for (int t = 0; t < kNet3Tiles; ++t) {
-            const int n = 8 * t + g;
-            auto w1 = [&](int k) { return (n < kNet3Hidden && k < kNetIn) ? W1[n * kNetIn + k] : 0.0; };
-            fr.w1[t][lane] = (uint32_t)bf16_bits(w1(2 * q)) | ((uint32_t)bf16_bits(w1(2 * q + 1)) << 16);
-        }
-        for (int st = 0; st < 4; ++st)
-            for (int r = 0; r < 2; ++r) {
-                const int k0 = 16 * st + 2 * q + 8 * r;
-                auto w2 = [&](int k) { return (g < 3 && k < kNet3Hidden) ? W2[g * kNet3Hidden + k] : 0.0; };
-                fr.w2[st][r][lane] = (uint32_t)bf16_bits(w2(k0)) | ((uint32_t)bf16_bits(w2(k0 + 1)) << 16);
-            }
-    }
-    for (int k = 0; k < 8 * kNet3Tiles; ++k) fr.b1[k] = k < kNet3Hidden ? (float)b1[k] : 0.f;
-    for (int k = 0; k < 8; ++k) fr.b2[k] = k < 3 ? (float)b2[k] : 0.f;
-    std::memcpy(out, &fr, sizeof(fr));
-}
-
-template <class T, int MODE>
-__global__ void __launch_bounds__(128) k_learned3_update_tc(const T* src, T* dst, Geom g, float omega,
-                                                            unsigned* status, const Net3<float> net,
-                                                            const uint32_t* __restrict__ table)
-{
-    constexpr int kWords = (int)(sizeof(Net3Frag) / 4);
-    __shared__ uint32_t stab[kWords];
-    __shared__ uint32_t sx[4][32][4];  // per warp: 32 nodes x 8 BF16 inputs
-    for (int k = threadIdx.x; k < kWords; k += blockDim.x) stab[k] = table[k];
-    __syncthreads();
-    const Net3Frag& fr = *reinterpret_cast<const Net3Frag*>(stab);
-    const float* shift = net.v + kNet3Theta;
-    const float* scale = shift + kNetIn;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = x < g.nx;  // every lane takes part in the warp's matrix products
-    const int y = blockIdx.y;
-    Nbr nb = make_nbr<sizeof(T)>(g, valid ? x : 0, y, 0);
-    const int n = x + g.nx * y;
-    float f[9];
-    if (valid) load_node<D2Q9, MODE>(src, g, nb, n, f);
-    else
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = 0.f;
-    Learned3Node<float> s;
-    float I[kNetIn];
-    learned_inputs(f, s, I);
-    float xin[kNetIn];
-#pragma unroll
-    for (int k = 0; k < kNetIn; ++k) xin[k] = (I[k] - shift[k]) * scale[k];
-    sx[warp][lane][0] = pack_bf16(xin[0], xin[1]);
-    sx[warp][lane][1] = pack_bf16(xin[2], xin[3]);
-    sx[warp][lane][2] = pack_bf16(xin[4], xin[5]);
-    sx[warp][lane][3] = 0u;
-    __syncwarp();
-    const int gq = lane >> 2, q = lane & 3;
-    float zc[2][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const uint32_t a0 = sx[warp][16 * m + gq][q], a1 = sx[warp][16 * m + gq + 8][q];
-        uint32_t h[8][2];
-#pragma unroll
-        for (int t = 0; t < kNet3Tiles; ++t) {
-            float c[4];
-            c[0] = c[2] = fr.b1[8 * t + 2 * q];
-            c[1] = c[3] = fr.b1[8 * t + 2 * q + 1];
-            mma_bf16(c, a0, a1, 0u, 0u, fr.w1[t][lane], 0u);
-            h[t][0] = tanh_bf16x2(pack_bf16(c[0], c[1]));  // row gq
-            h[t][1] = tanh_bf16x2(pack_bf16(c[2], c[3]));  // row gq + 8
-        }
-        h[7][0] = h[7][1] = 0u;
-        float c[4];
-        c[0] = c[2] = fr.b2[2 * q];
-        c[1] = c[3] = fr.b2[2 * q + 1];
-#pragma unroll
-        for (int st = 0; st < 4; ++st)
-            mma_bf16(c, h[2 * st][0], h[2 * st][1], h[2 * st + 1][0], h[2 * st + 1][1], fr.w2[st][0][lane],
-                     fr.w2[st][1][lane]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) zc[m][k] = c[k];
-    }
-    // node r = lane: tile r / 16, row r % 16 (g = row % 8, upper half = row / 8); its outputs
-    // 0, 1 sit in lane 4g (c0, c1 or c2, c3) and output 2 in lane 4g + 1 (c0 or c2)
-    const int row = lane & 15, src0 = 4 * (row & 7), up = row >> 3, mt = lane >> 4;
-    float z[3];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const float v0 = __shfl_sync(0xffffffffu, zc[m][0], src0), v1 = __shfl_sync(0xffffffffu, zc[m][1], src0);
-        const float v2 = __shfl_sync(0xffffffffu, zc[m][2], src0), v3 = __shfl_sync(0xffffffffu, zc[m][3], src0);
-        const float w0 = __shfl_sync(0xffffffffu, zc[m][0], src0 + 1);
-        const float w2 = __shfl_sync(0xffffffffu, zc[m][2], src0 + 1);
-        if (m == mt) {
-            z[0] = up ? v2 : v0;
-            z[1] = up ? v3 : v1;
-            z[2] = up ? w2 : w0;
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-        const int r = net3_row(o);
-        s.ez[r] = expf(z[o]);
-        s.omg[r] = recip(s.ez[r] + 0.5f);
-    }
-    if (!valid) return;
-    learned3_post(s, s.omg, omega, f);
-    store_node<D2Q9, MODE>(dst, g, nb, n, f);
-    if (!(s.m.rho > 0.f && s.m.rho < 1e30f)) atomicOr(status, 1u);
-}
-
 // Block reduction of the parameter gradient of the three-output network. The hidden units
 // (padded to kH3Pad) form kT3Tiles register tiles of four; each tile's nodes are split into
 // kT3Parts interleaved subsets (so that the threads of a warp read distinct banks); one thread
@@ -904,19 +590,7 @@ static cudaError_t launch_learned(const OpArgs& a, const double* netv, bool tc)
     using R = typename Store<T>::Real;
     const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
     if constexpr (sizeof(R) == 4) {
-        if (!(tc && a.op == OP_UPDATE)) return run_learned_x3(a, false);
-        if (!a.tc_table) return cudaErrorInvalidValue;
-        const Net<float> net = make_net<float>(netv);
-        const uint32_t* tab = (const uint32_t*)a.tc_table;
-        const T* src = (const T*)a.src;
-        T* dst = (T*)a.dst;
-        if (a.mode == AB)
-            k_learned_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        else if (a.mode == AA_EVEN)
-            k_learned_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        else
-            k_learned_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        return cudaGetLastError();
+        return (tc && a.op == OP_UPDATE) ? run_learned_tc(a, false) : run_learned_x3(a, false);
     } else {
         const Net<R> net = make_net<R>(netv);
         if (a.op == OP_UPDATE) {
@@ -967,19 +641,7 @@ static cudaError_t launch_learned3(const OpArgs& a, const double* netv, bool tc)
     using R = typename Store<T>::Real;
     const dim3 bl(kAdjBlock, 1, 1), gr((a.g.nx + kAdjBlock - 1) / kAdjBlock, a.g.ny, 1);
     if constexpr (sizeof(R) == 4) {
-        if (!(tc && a.op == OP_UPDATE)) return run_learned_x3(a, true);
-        if (!a.tc_table) return cudaErrorInvalidValue;
-        const Net3<float> net = make_net3<float>(netv);
-        const uint32_t* tab = (const uint32_t*)a.tc_table;
-        const T* src = (const T*)a.src;
-        T* dst = (T*)a.dst;
-        if (a.mode == AB)
-            k_learned3_update_tc<T, AB><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        else if (a.mode == AA_EVEN)
-            k_learned3_update_tc<T, AA_EVEN><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        else
-            k_learned3_update_tc<T, AA_ODD><<<gr, bl, 0, a.stream>>>(src, dst, a.g, (float)a.omega, a.status, net, tab);
-        return cudaGetLastError();
+        return (tc && a.op == OP_UPDATE) ? run_learned_tc(a, true) : run_learned_x3(a, true);
     } else {
         const Net3<R> net = make_net3<R>(netv);
         if (a.op == OP_UPDATE) {

@@ -20,18 +20,19 @@ static_assert(kNet3Theta == 533, "6-53-3 network has 533 parameters");
 // forward step / adjoint step of the learned collision (a.op = OP_UPDATE or OP_ADJ_STEP);
 // net = kNetValues host doubles; a.gth = per-block parameter-gradient partials (adjoint).
 // FP64 storage runs the scalar FP64 kernels, the other storage types the tensor-core
-// kernels of the FP32 arithmetic (run_learned_x3); tc = 1: forward step with single BF16
-// operands instead (the learned_tc inference option)
+// kernels of the FP32 arithmetic (run_learned_x3); tc = 1: forward step with the network in
+// half precision instead (the learned_tc inference option, run_learned_tc)
 cudaError_t run_learned_d2q9(const OpArgs& a, const double* net, bool tc = false);
 // the same for the one-hidden-layer network with three outputs (net = kNet3Values doubles)
 cudaError_t run_learned3_d2q9(const OpArgs& a, const double* net, bool tc = false);
-// Network weights for the tensor-core path, packed once per lb_set_mlp into a device table:
-// bytes needed, and the host-side packing into `out` (learned_tc_table_bytes() bytes).
+// The learned_tc inference option (lb_learned_tc.cu): weights packed once per lb_set_mlp
+// into a device table (bytes needed, host-side packing into `out`), and the forward step
+// (a.tc_table; needs 9 x plane < 2^31).
 size_t learned_tc_table_bytes();
 void learned_tc_pack(const double* net, void* out);
-// the same for the three-output network (learned3_tc_table_bytes() bytes)
 size_t learned3_tc_table_bytes();
 void learned3_tc_pack(const double* net, void* out);
+cudaError_t run_learned_tc(const OpArgs& a, bool three);
 // out[6][N] <- the six network inputs (moment invariants) of every node of the state a.src
 cudaError_t learned_inputs_d2q9(const OpArgs& a);
 // FP32 arithmetic (FP32 / FP16 / BF16 storage): the networks on the tensor cores with

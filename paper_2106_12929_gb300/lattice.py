@@ -48,7 +48,8 @@ class Lattice:
     storage: "f64" | "f32" | "f16" | "bf16" (the half types store f_i - w_i);
     layout: "ab" (two buffers) | "aa" (in place); record_every > 0 keeps
     checkpoints for ``step_adjoint``; learned_tc runs the learned collision's network
-    on the tensor cores (BF16 operands, FP32 accumulation; forward only); graphs
+    in half precision on the tensor cores (FP16 operands and hidden-layer accumulation, the
+    hardware tanh; forward only); graphs
     replays ``step(n)`` as captured two-step CUDA graphs (off: one launch per kernel);
     nodes_per_thread forces the stream-collide launch shape (0: chosen from the grid).
     The context runs on torch's current CUDA stream at construction time.

@@ -217,11 +217,11 @@ def test_autograd_parameter_gradient_matches_oracle():
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 def test_tensor_core_option(storage, layout):
-    """The network on the tensor cores (BF16 operands, FP32 accumulation) against the FP32
-    kernel: with zero output weights both give z = the output biases (they differ by FP32
-    rounding elsewhere, which can flip an FP16 rounding); with a random network the BF16
-    activations move the rates by ~1e-2 relative."""
-    dims = (130, 40, 1)  # two blocks of 128 lanes per row, the second one ragged
+    """The network in half precision on the tensor cores (FP16 operands and hidden-layer
+    accumulation, hardware tanh) against the FP32 kernel: with zero output weights both give
+    z = the output biases (they differ by FP32 rounding elsewhere, which can flip an FP16
+    rounding); with a random network the FP16 activations move the rates by ~1e-3 relative."""
+    dims = (130, 40, 1)  # five 32-node warp tiles per row, the last one ragged
     rho, u = lbinputs.random_moments(dims, seed=7, u_amp=0.05)
     tau = 0.6
     same_tol = 1e-6 if storage == "f32" else 2e-4
