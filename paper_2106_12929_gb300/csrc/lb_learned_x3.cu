@@ -399,6 +399,39 @@ LB_DEV float to_node(const float* v, int lane)
     return sel == 0 ? v0 : sel == 1 ? v1 : sel == 2 ? v2 : v3;
 }
 
+// ---------------------------------------------------------------- asynchronous copies
+// 4-byte global -> shared copies (cp.async) that complete in the background: the adjoint
+// fetches a tile's state and cotangent while the network of the tile before it runs.
+LB_DEV void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+LB_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+LB_DEV void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The pre-collision state of the lane's node (pull: slot i of x - c_i) into pf[i][lane]; FP32
+// storage only (the copies move whole 4-byte words)
+LB_DEV void fetch_state(const float* state, const TileNode& nd, float (*pf)[32], int lane)
+{
+    if (!nd.valid) return;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cp_async4(&pf[i][lane], at(state, nd.nb, i, -c2(i, 0), -c2(i, 1), 0));
+}
+// the cotangent mu_i of the post-collision value that node x sends to x + c_i
+LB_DEV void fetch_mu(const float* lam_in, const Geom& g, const TileNode& nd, float (*pm)[32], int lane)
+{
+    if (!nd.valid) return;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        cp_async4(&pm[i][lane], lam_in + ((int64_t)i * g.plane + nd.nb.node(g, c2(i, 0), c2(i, 1), 0)));
+}
+
 // ---------------------------------------------------------------- 6-24-24-1
 // The network of row tile m: h1, h2 (accumulator layout) and the partial output sums of rows
 // g and g + 8 over the lane's columns; kxt = 2 / ln 2 / (input scale x W1 scale).
@@ -498,6 +531,8 @@ struct Adj1Smem {
     };
     float sg[kWarps][32][9];
     float acc[kWarps][36][32];  // dW2^T (24 values) and dW1^T (12) per lane
+    float pf[kWarps][9][32];    // the tile's state (FP32 storage), copied in during the tile before
+    float pm[kWarps][9][32];    // the tile's cotangent mu, copied in while its network runs
 };
 
 template <class T>
@@ -529,19 +564,42 @@ __global__ void __launch_bounds__(kThreads, 3) k_learned_adj_x3(const T* state, 
     float aW3[3][2], aB3 = 0.f;
 #pragma unroll
     for (int t = 0; t < 3; ++t) aW3[t][0] = aW3[t][1] = 0.f;
-    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += gridDim.x * kWarps) {
+    // Copies: the state of tile wt arrives during tile wt - stride (FP32 storage), its cotangent
+    // during its own network; each lane copies and reads only its own column of pf and pm, and
+    // reuses a slot only after the values read from it have been used.
+    constexpr bool kAsyncState = sizeof(T) == 4;
+    const unsigned stride = gridDim.x * kWarps;
+    if (kAsyncState && blockIdx.x * kWarps + warp < ntiles) {
+        fetch_state((const float*)state, tile_node<T>(g, blockIdx.x * kWarps + warp, ntx, lane), sm.pf[warp], lane);
+        cp_async_commit();
+    }
+    for (unsigned wt = blockIdx.x * kWarps + warp; wt < ntiles; wt += stride) {
         const TileNode nd = tile_node<T>(g, wt, ntx, lane);
         LearnedMoments<float> s;
         Scale sx_sc;
         float z;
         {
             float f[9];
-            if (nd.valid) load_node<D2Q9, AB>(state, g, nd.nb, nd.n, f);
-            else
+            cp_async_wait<0>();
+            if (nd.valid) {
+                if constexpr (kAsyncState) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = sm.pf[warp][i][lane];
+                } else {
+                    load_node<D2Q9, AB>(state, g, nd.nb, nd.n, f);
+                }
+            } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = 0.f;
+            }
+            fetch_mu(lam_in, g, nd, sm.pm[warp], lane);
+            cp_async_commit();
             float I[kNetIn];
             learned_inputs(f, s, I);
+            if (kAsyncState && wt + stride < ntiles) {
+                fetch_state((const float*)state, tile_node<T>(g, wt + stride, ntx, lane), sm.pf[warp], lane);
+                cp_async_commit();
+            }
             sx_sc = stage_inputs(I, tb.shift, tb.scale, sx[warp], lane);
             __syncwarp();
             const float kxt = sx_sc.inv * tb.iw1 * kTwoOverLn2;
@@ -564,9 +622,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_learned_adj_x3(const T* state, 
         LearnedCot<float> c;
         {
             float mu[9];
+            // the cotangent's group; the next tile's state (committed after it) may still be in flight
+            if (kAsyncState && wt + stride < ntiles) cp_async_wait<1>();
+            else cp_async_wait<0>();
             if (nd.valid)
 #pragma unroll
-                for (int i = 0; i < 9; ++i) mu[i] = lam_in[(int64_t)i * g.plane + nd.nb.node(g, c2(i, 0), c2(i, 1), 0)];
+                for (int i = 0; i < 9; ++i) mu[i] = sm.pm[warp][i][lane];
             else
 #pragma unroll
                 for (int i = 0; i < 9; ++i) mu[i] = 0.f;
