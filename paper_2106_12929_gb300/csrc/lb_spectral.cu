@@ -20,11 +20,12 @@
 // dR/dsigma, one warp per shell), columns (filter by G, inverse DFT along y; the cost R), rows
 // (inverse DFT along x: du, then the shifted BGK step of the row's nodes). lb_spectral_shift
 // writes du instead of stepping. Each DFT is an in-place radix-2 FFT of grid lines in shared
-// memory, in passes of three radix-2 stages held in registers (a padded layout keeps the
-// passes free of bank conflicts), with the twiddle table computed once per context. A row
-// block takes one grid line; a column block takes several adjacent columns, so that its loads
-// and stores of a grid row are contiguous runs of whole 32-byte sectors. Every sum runs in a
-// fixed order (deterministic).
+// memory, in passes of three radix-2 stages held in registers (three twiddle-table entries per
+// set of eight, the rest fixed rotations; a padded layout keeps the passes free of bank
+// conflicts), with the twiddle table computed once per context. A row block takes one grid
+// line; a column block takes several adjacent columns, so that its loads and stores of a grid
+// row are contiguous runs of whole 32-byte sectors. Every sum runs in a fixed order
+// (deterministic).
 #include "lb_collide.cuh"
 #include "lb_spectral.cuh"
 
@@ -64,37 +65,76 @@ LB_HD int pz(int i) { return i + (i >> 3); }
 // (one more slot per line, so that the lines of a column block start on different banks)
 LB_HD int line_stride(int n) { return n + (n >> 3) + 1; }
 
-// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 of `lines`
-// n-point lines z[l line_stride(n) ..) (bit-reversed input order): those stages only combine
-// elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads whole sets,
-// runs the RB stages in registers and stores them back (one shared-memory round trip and one
-// barrier for RB stages). Forward: twiddles exp(-i ...), INV: their conjugates; unnormalised.
+// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 (RB <= 3) of
+// `lines` n-point lines z[l line_stride(n) ..) (bit-reversed input order): those stages only
+// combine elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads whole
+// sets, runs the RB stages in registers and stores them back (one shared-memory round trip and
+// one barrier for RB stages). Element k of a set sits at position j + k h of its 2^RB h block
+// (j = its offset in the first h), so the stages' twiddles are
+//   stage s:     w1 = exp(-i pi j / h)                              for every pair,
+//   stage s + 1: w2 = exp(-i pi j / 2h), times -i for the pairs with odd k,
+//   stage s + 2: w4 = exp(-i pi j / 4h), times exp(-i pi (k mod 4) / 4),
+// three table entries per set and fixed rotations (the conjugates for INV); unnormalised.
+template <class R, bool INV>
+LB_DEV Cx<R> cmul(Cx<R> w, Cx<R> q)
+{
+    return {w.re * q.re - w.im * q.im, w.re * q.im + w.im * q.re};
+}
+// t times -i (forward) or +i (inverse)
+template <class R, bool INV>
+LB_DEV Cx<R> rot90(Cx<R> t)
+{
+    return INV ? Cx<R>{-t.im, t.re} : Cx<R>{t.im, -t.re};
+}
+template <class R>
+LB_DEV void bfly(Cx<R>& p, Cx<R>& q, Cx<R> t)  // p, q <- p + t, p - t
+{
+    const Cx<R> a = p;
+    p = {a.re + t.re, a.im + t.im};
+    q = {a.re - t.re, a.im - t.im};
+}
+
 template <class R, int RB, bool INV>
 LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s, int lines)
 {
     constexpr int RR = 1 << RB;
-    const int h = 1 << s, sets = n >> RB, ls = line_stride(n);
-    for (int t = threadIdx.x; t < lines * sets; t += blockDim.x) {
-        const int l = t / sets, q = t - l * sets;
+    const int h = 1 << s, lsets = logn - RB, ls = line_stride(n);
+    for (int t = threadIdx.x; t < (lines << lsets); t += blockDim.x) {
+        const int l = t >> lsets, q = t & ((1 << lsets) - 1);
         Cx<R>* line = z + l * ls;
         const int j = q & (h - 1);
-        const int base = (q - j) * RR + j;  // (q / h) RR h + j
+        const int base = ((q - j) << RB) + j;
         Cx<R> v[RR];
 #pragma unroll
         for (int k = 0; k < RR; ++k) v[k] = line[pz(base + k * h)];
+        auto twid = [&](int sh) {
+            Cx<R> w = tw[j << sh];
+            if (INV) w.im = -w.im;
+            return w;
+        };
+        {
+            const Cx<R> w1 = twid(logn - 1 - s);
 #pragma unroll
-        for (int lv = 0; lv < RB; ++lv) {  // stage s + lv: half H = h 2^lv, pairs (k, k + 2^lv)
+            for (int k = 0; k < RR; k += 2) bfly(v[k], v[k + 1], cmul<R, INV>(w1, v[k + 1]));
+        }
+        if constexpr (RB >= 2) {
+            const Cx<R> w2 = twid(logn - 2 - s);
 #pragma unroll
-            for (int k = 0; k < RR; ++k) {
-                if (k & (1 << lv)) continue;
-                const int m = j + (k & ((1 << lv) - 1)) * h;  // position of the pair within its half
-                Cx<R> w = tw[m << (logn - 1 - s - lv)];       // exp(-+ i pi m / H)
-                if (INV) w.im = -w.im;
-                const Cx<R> p = v[k], qv = v[k | (1 << lv)];
-                const R tr = w.re * qv.re - w.im * qv.im, ti = w.re * qv.im + w.im * qv.re;
-                v[k] = {p.re + tr, p.im + ti};
-                v[k | (1 << lv)] = {p.re - tr, p.im - ti};
+            for (int k0 = 0; k0 < RR; k0 += 4) {
+                bfly(v[k0], v[k0 + 2], cmul<R, INV>(w2, v[k0 + 2]));
+                bfly(v[k0 + 1], v[k0 + 3], rot90<R, INV>(cmul<R, INV>(w2, v[k0 + 3])));
             }
+        }
+        if constexpr (RB >= 3) {
+            const Cx<R> w4 = twid(logn - 3 - s);
+            // exp(-+ i pi / 4) = (1 -+ i) / sqrt 2
+            const R r = R(0.70710678118654752440);
+            const Cx<R> c8 = {r, INV ? r : -r};
+            const Cx<R> w4c = cmul<R, INV>(c8, w4);
+            bfly(v[0], v[4], cmul<R, INV>(w4, v[4]));
+            bfly(v[1], v[5], cmul<R, INV>(w4c, v[5]));
+            bfly(v[2], v[6], rot90<R, INV>(cmul<R, INV>(w4, v[6])));
+            bfly(v[3], v[7], rot90<R, INV>(cmul<R, INV>(w4c, v[7])));
         }
 #pragma unroll
         for (int k = 0; k < RR; ++k) line[pz(base + k * h)] = v[k];
@@ -127,6 +167,41 @@ LB_DEV int shell_of(int kx, int ky)
 
 LB_DEV int signed_k(int k, int n) { return k < n / 2 ? k : k - n; }
 
+// Population access of node x of row y with 32-bit element offsets (9 x plane < 2^31 for every
+// grid the spectral calls accept): the three columns x - 1, x, x + 1 and the three row offsets
+// (y - 1) n, y n, (y + 1) n, periodic; access modes as in lb_device.cuh.
+struct ScRows {
+    int r[3];
+};
+LB_DEV ScRows sc_rows(int y, int n)
+{
+    return {{(y == 0 ? n - 1 : y - 1) * n, y * n, (y == n - 1 ? 0 : y + 1) * n}};
+}
+template <class T, int MODE>
+LB_DEV void sc_load(const T* buf, int plane, const ScRows& rw, int x, int n, typename Store<T>::Real* f)
+{
+    const int col[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int slot = (MODE == AA_ODD) ? opp(i) : i;
+        const int sg = (MODE == AA_EVEN) ? 0 : -1;
+        f[i] = load_pop<D2Q9>(buf + (slot * plane + rw.r[1 + sg * c2(i, 1)] + col[1 + sg * c2(i, 0)]), slot);
+    }
+}
+template <class T, int MODE>
+LB_DEV void sc_store(T* buf, int plane, const ScRows& rw, int x, int n, const typename Store<T>::Real* f)
+{
+    const int col[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int slot = (MODE == AA_EVEN) ? opp(i) : i;
+        const int sg = (MODE == AA_ODD) ? 1 : 0;
+        store_pop<D2Q9>(buf + (slot * plane + rw.r[1 + sg * c2(i, 1)] + col[1 + sg * c2(i, 0)]), slot, f[i]);
+    }
+}
+
+constexpr int kRowBatch = 4;
+
 // rows, forward: moments of every node of row y, w = u_x + i u_y, DFT along x -> spec[y][kx]
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) k_sc_rows_fwd(const T* buf, Geom g, int logn,
@@ -135,17 +210,29 @@ __global__ void __launch_bounds__(256) k_sc_rows_fwd(const T* buf, Geom g, int l
 {
     using R = typename Store<T>::Real;
     extern __shared__ __align__(16) unsigned char sc_smem[];
-    const int n = g.nx, y = blockIdx.x;
+    const int n = g.nx, y = blockIdx.x, plane = (int)g.plane;
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
     Cx<R>* tws = z + line_stride(n);
     load_twiddles(tws, tw, n);
-#pragma unroll 2
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        Nbr nb = make_nbr_2d<sizeof(T)>(g, x, y);
-        R f[9], Fz[3] = {R(0), R(0), R(0)};
-        load_node<D2Q9, MODE>(buf, g, nb, x + n * y, f);
-        const NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
-        z[pz(bitrev(x, logn))] = {m.ux, m.uy};
+    const ScRows rw = sc_rows(y, n);
+    // kRowBatch nodes per thread at a time: all their loads are issued before the first
+    // shared-memory store (which the compiler would not move loads across)
+    for (int x0 = threadIdx.x; x0 < n; x0 += kRowBatch * blockDim.x) {
+        R f[kRowBatch][9];
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b) {
+            const int x = x0 + b * blockDim.x;
+            if (x < n) sc_load<T, MODE>(buf, plane, rw, x, n, f[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b) {
+            const int x = x0 + b * blockDim.x;
+            if (x < n) {
+                const R Fz[3] = {R(0), R(0), R(0)};
+                const NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f[b], Fz);
+                z[pz(bitrev(x, logn))] = {m.ux, m.uy};
+            }
+        }
     }
     __syncthreads();
     fft_lines<R, false>(z, tws, n, logn, 1);
@@ -170,8 +257,8 @@ LB_DEV int first_m(int kxs, int s, int n)
 // load the C columns kx0 .. kx0 + C - 1 of spec into lines 0 .. C - 1 (bit-reversed order along
 // y), each value times G of its shell if grad is given: thread t takes row t / C, column t % C,
 // so the threads of a warp read runs of C adjacent values of a row
-template <class R>
-LB_DEV void load_columns(Cx<R>* z, const Cx<R>* spec, int n, int logn, int kx0, int C, const double* grad)
+template <class R, int C>
+LB_DEV void load_columns(Cx<R>* z, const Cx<R>* spec, int n, int logn, int kx0, const double* grad)
 {
     const int ls = line_stride(n), K = n / 2, total = n * C;
     constexpr int U = 4;  // loads in flight per thread
@@ -202,8 +289,8 @@ LB_DEV void load_columns(Cx<R>* z, const Cx<R>* spec, int n, int logn, int kx0, 
     }
 }
 
-template <class R>
-LB_DEV void store_columns(const Cx<R>* z, Cx<R>* spec, int n, int kx0, int C)
+template <class R, int C>
+LB_DEV void store_columns(const Cx<R>* z, Cx<R>* spec, int n, int kx0)
 {
     const int ls = line_stride(n);
     for (int t = threadIdx.x; t < n * C; t += blockDim.x) {
@@ -212,27 +299,18 @@ LB_DEV void store_columns(const Cx<R>* z, Cx<R>* spec, int n, int kx0, int C)
     }
 }
 
-// columns, forward: DFT along y of the block's C columns, then the shell sums of |W|^2 / (2 N^2)
-// over those columns into partials[s][block] (per column the modes of shell s are one run of
-// |ky|, summed in order of |ky|, +ky before -ky; the columns in order)
-template <class R>
-__global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, int C, const Cx<R>* tw,
-                                                     double* partials)
+// the shell sums of |W|^2 / (2 N^2) over the block's C transformed columns (natural order)
+// into partials[s][block]: per column the modes of shell s are one run of |ky|, summed in order
+// of |ky|, +ky before -ky; the runs' sums and the columns in the arithmetic type (a few to a
+// few hundred terms; FP64 is a slow pipe on this part), scaled into FP64 once per shell
+template <class R, int C>
+LB_DEV void column_shell_sums(const Cx<R>* z, int n, int kx0, int nblk, double* partials)
 {
-    extern __shared__ __align__(16) unsigned char sc_smem[];
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n), K = n / 2, kx0 = blockIdx.x * C, nblk = gridDim.x;
-    Cx<R>* tws = z + C * ls;
-    load_twiddles(tws, tw, n);
-    load_columns<R>(z, spec, n, logn, kx0, C, nullptr);
-    __syncthreads();
-    fft_lines<R, false>(z, tws, n, logn, C);
-    store_columns<R>(z, spec, n, kx0, C);
-    // modal energies |W|^2 and the runs' sums in the arithmetic type (a few to a few hundred
-    // terms; FP64 is a slow pipe on this part), the block's total per shell in FP64
+    const int ls = line_stride(n), K = n / 2;
     const double scale = 0.5 / ((double)n * n * (double)n * n);
     for (int s = threadIdx.x; s < K; s += blockDim.x) {
-        double acc = 0.0;
+        R acc = R(0);
+#pragma unroll
         for (int c = 0; c < C; ++c) {
             const Cx<R>* line = z + c * ls;
             const int kxs = signed_k(kx0 + c, n);
@@ -246,10 +324,29 @@ __global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int log
                     run += b.re * b.re + b.im * b.im;
                 }
             }
-            acc += (double)run * scale;
+            acc += run;
         }
-        partials[(int64_t)s * nblk + blockIdx.x] = acc;
+        partials[(int64_t)s * nblk + blockIdx.x] = (double)acc * scale;
     }
+}
+
+// columns, forward: DFT along y of the block's C columns, then the shell sums of |W|^2 / (2 N^2)
+// over those columns into partials[s][block] (per column the modes of shell s are one run of
+// |ky|, summed in order of |ky|, +ky before -ky; the columns in order)
+template <class R, int C>
+__global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, const Cx<R>* tw,
+                                                     double* partials)
+{
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
+    const int ls = line_stride(n), kx0 = blockIdx.x * C, nblk = gridDim.x;
+    Cx<R>* tws = z + C * ls;
+    load_twiddles(tws, tw, n);
+    load_columns<R, C>(z, spec, n, logn, kx0, nullptr);
+    __syncthreads();
+    fft_lines<R, false>(z, tws, n, logn, C);
+    store_columns<R, C>(z, spec, n, kx0);
+    column_shell_sums<R, C>(z, n, kx0, nblk, partials);
 }
 
 // shells: sigma_s = sum over the column blocks (one warp per shell: lane l takes blocks l, l + 32,
@@ -258,12 +355,9 @@ __global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int log
 // the gradient run in the arithmetic type R (the FP64 pipe is slow on this part, and FP32
 // storage needs no more).
 template <class R>
-__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
-                                                   double c, double* sigma, double* grad, double* r2)
+LB_DEV void shell_reduce(const double* partials, int nblk, int s, int lane, const double* l0, double c,
+                         double* sigma, double* grad, double* r2)
 {
-    const int K = n / 2, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= K) return;
     const double* p = partials + (int64_t)s * nblk;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
@@ -286,6 +380,15 @@ __global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n
     }
 }
 
+template <class R>
+__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
+                                                   double c, double* sigma, double* grad, double* r2)
+{
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n / 2) return;
+    shell_reduce<R>(partials, nblk, s, threadIdx.x & 31, l0, c, sigma, grad, r2);
+}
+
 // R = sum_s r2[s] by one warp in a fixed order
 LB_DEV void sum_cost(const double* r2, int K, double* cost)
 {
@@ -301,8 +404,8 @@ __global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double*
 
 // columns, inverse: multiply by G(k), inverse DFT along y of the block's C columns; block 0's
 // first warp also totals the cost R (cost non-null)
-template <class R>
-__global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int logn, int C, const Cx<R>* tw,
+template <class R, int C>
+__global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const Cx<R>* tw,
                                                      const double* grad, const double* r2, double* cost)
 {
     if (cost && blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
@@ -311,10 +414,10 @@ __global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int log
     const int ls = line_stride(n), kx0 = blockIdx.x * C;
     Cx<R>* tws = z + C * ls;
     load_twiddles(tws, tw, n);
-    load_columns<R>(z, spec, n, logn, kx0, C, grad);
+    load_columns<R, C>(z, spec, n, logn, kx0, grad);
     __syncthreads();
     fft_lines<R, true>(z, tws, n, logn, C);
-    store_columns<R>(z, spec, n, kx0, C);
+    store_columns<R, C>(z, spec, n, kx0);
 }
 
 // rows, inverse: inverse DFT along x, du_x = scale Re(.), du_y = scale Im(.), scale = -kappa / N^2
@@ -336,16 +439,16 @@ __global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, i
     }
 }
 
-// one BGK step of node (x, y) with the equilibrium at u + du
+// one BGK step of a node from its pre-collision deviations f (loaded by the caller) with the
+// equilibrium at u + du
 template <class T, int MODE>
-LB_DEV void shifted_bgk_node(const T* src, T* dst, const Geom& g, typename Store<T>::Real omega, int x, int y,
-                             typename Store<T>::Real dux, typename Store<T>::Real duy, unsigned* status)
+LB_DEV void shifted_bgk_node(typename Store<T>::Real* f, T* dst, int plane, const ScRows& rw, int n,
+                             typename Store<T>::Real omega, int x, typename Store<T>::Real dux,
+                             typename Store<T>::Real duy, unsigned* status)
 {
     using R = typename Store<T>::Real;
-    Nbr nb = make_nbr_2d<sizeof(T)>(g, x, y);
-    const int n = x + g.nx * y;
-    R f[9], feq[9], Fz[3] = {R(0), R(0), R(0)};
-    load_node<D2Q9, MODE>(src, g, nb, n, f);
+    R feq[9];
+    const R Fz[3] = {R(0), R(0), R(0)};
     NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
     const R rho = m.rho;
     m.ux += dux;
@@ -353,7 +456,7 @@ LB_DEV void shifted_bgk_node(const T* src, T* dst, const Geom& g, typename Store
     equilibrium<D2Q9>(m, feq);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
-    store_node<D2Q9, MODE>(dst, g, nb, n, f);
+    sc_store<T, MODE>(dst, plane, rw, x, n, f);
     if (!(rho > R(0) && rho < R(1e30))) atomicOr(status, 1u);
 }
 
@@ -377,19 +480,34 @@ __global__ void __launch_bounds__(256) k_sc_rows_inv_step(const Cx<typename Stor
     for (int k = threadIdx.x; k < n; k += blockDim.x) z[pz(bitrev(k, logn))] = spec[(int64_t)y * n + k];
     __syncthreads();
     fft_lines<R, true>(z, tws, n, logn, 1);
-#pragma unroll 2
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        const Cx<R> d = z[pz(x)];
-        shifted_bgk_node<T, MODE>(src, dst, g, omega, x, y, scale * d.re, scale * d.im, status);
+    const ScRows rw = sc_rows(y, n);
+    const int plane = (int)g.plane;
+    // every node is read and written by its own thread only (AB: other buffer; AA: its own
+    // slots), so the loads of a batch may precede the stores of the nodes before it
+    for (int x0 = threadIdx.x; x0 < n; x0 += kRowBatch * blockDim.x) {
+        R f[kRowBatch][9];
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b) {
+            const int x = x0 + b * blockDim.x;
+            if (x < n) sc_load<T, MODE>(src, plane, rw, x, n, f[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b) {
+            const int x = x0 + b * blockDim.x;
+            if (x < n) {
+                const Cx<R> d = z[pz(x)];
+                shifted_bgk_node<T, MODE>(f[b], dst, plane, rw, n, omega, x, scale * d.re, scale * d.im, status);
+            }
+        }
     }
 }
 
 // threads of a block that FFTs `lines` lines of n points (passes of three stages: n / 8 sets
-// per line, one per thread up to 512)
-static int fft_threads(int n, int lines)
+// per line, one per thread, 32 to `cap`)
+static int fft_threads(int n, int lines, int cap)
 {
     const int t = lines * n / 8;
-    return t < 32 ? 32 : (t > 512 ? 512 : t);
+    return t < 32 ? 32 : (t > cap ? cap : t);
 }
 
 // columns per column block: four (whole 32-byte sectors of FP32 values, two of FP64), fewer
@@ -409,6 +527,35 @@ static cudaError_t smem_attr(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// the column passes with C columns per block: forward DFT and shell sums (inv = false), or
+// the filter by G and the inverse DFT
+template <class R, int C>
+static cudaError_t launch_columns(const SpectralArgs& s, bool inv)
+{
+    const int n = s.n, logn = s.logn, K = n / 2, nblk = n / C, th = fft_threads(n, C, 512);
+    const size_t smem = ((size_t)C * line_stride(n) + (size_t)K) * sizeof(Cx<R>);
+    Cx<R>* spec = (Cx<R>*)s.spec;
+    const Cx<R>* tw = (const Cx<R>*)s.tw;
+    cudaError_t e;
+    if (!inv) {
+        if ((e = smem_attr(k_sc_cols_fwd<R, C>, smem)) != cudaSuccess) return e;
+        k_sc_cols_fwd<R, C><<<nblk, th, smem, s.a.stream>>>(spec, n, logn, tw, s.partials);
+    } else {
+        if ((e = smem_attr(k_sc_cols_inv<R, C>, smem)) != cudaSuccess) return e;
+        k_sc_cols_inv<R, C><<<nblk, th, smem, s.a.stream>>>(spec, n, logn, tw, s.grad, s.r2, s.cost);
+    }
+    return cudaGetLastError();
+}
+template <class R>
+static cudaError_t columns(const SpectralArgs& s, bool inv)
+{
+    switch (column_block<R>(s.n)) {
+    case 4: return launch_columns<R, 4>(s, inv);
+    case 2: return launch_columns<R, 2>(s, inv);
+    default: return launch_columns<R, 1>(s, inv);
+    }
+}
+
 // step = true: the controlled step itself (a.dst, a.status, a.omega of s.a), du stays on chip
 template <class T>
 static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
@@ -416,13 +563,13 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
     using R = typename Store<T>::Real;
     const OpArgs& a = s.a;
     const int n = s.n, logn = s.logn, K = n / 2;
-    const int C = column_block<R>(n), nblk = n / C;
-    // row blocks also load and step the row's nodes: a thread per node up to 256
-    const int th_row = n < 256 ? (n < 32 ? 32 : n) : 256, th_col = fft_threads(n, C);
+    const int nblk = n / column_block<R>(n);
+    // a row block: one thread per set of the FFT passes (n / 8, 32 to 256), each loading and
+    // stepping n / threads nodes of the row
+    const int th_row = fft_threads(n, 1, 256);
     Cx<R>* spec = (Cx<R>*)s.spec;
     const Cx<R>* tw = (const Cx<R>*)s.tw;
     const size_t row_smem = ((size_t)line_stride(n) + (size_t)K) * sizeof(Cx<R>);  // one line + twiddles
-    const size_t col_smem = ((size_t)C * line_stride(n) + (size_t)K) * sizeof(Cx<R>);
     cudaError_t e;
     const T* buf = (const T*)a.src;
     if (a.mode == AB) {
@@ -435,8 +582,7 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
         if ((e = smem_attr(k_sc_rows_fwd<T, AA_ODD>, row_smem)) != cudaSuccess) return e;
         k_sc_rows_fwd<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
     }
-    if ((e = smem_attr(k_sc_cols_fwd<R>, col_smem)) != cudaSuccess) return e;
-    k_sc_cols_fwd<R><<<nblk, th_col, col_smem, a.stream>>>(spec, n, logn, C, tw, s.partials);
+    if ((e = columns<R>(s, false)) != cudaSuccess) return e;
     k_sc_shells<R><<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, nblk, s.sigma0 ? s.l0 : nullptr, s.cutoff,
                                                       s.sigma, s.grad, s.r2);
     *launches += 3;
@@ -446,8 +592,8 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
         *launches += 1;
         return cudaGetLastError();
     }
-    if ((e = smem_attr(k_sc_cols_inv<R>, col_smem)) != cudaSuccess) return e;
-    k_sc_cols_inv<R><<<nblk, th_col, col_smem, a.stream>>>(spec, n, logn, C, tw, s.grad, s.r2, s.cost);
+    if ((e = columns<R>(s, true)) != cudaSuccess) return e;
+    *launches += 1;
     const R scale = (R)(-s.kappa / ((double)n * n * (double)n * n));
     if (step) {  // inverse rows fused with the step
         const T* src = (const T*)a.src;
@@ -466,12 +612,12 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
             k_sc_rows_inv_step<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g,
                                                                              om, a.status);
         }
-        *launches += 2;
+        *launches += 1;
         return cudaGetLastError();
     }
     if ((e = smem_attr(k_sc_rows_inv<R>, row_smem)) != cudaSuccess) return e;
     k_sc_rows_inv<R><<<n, th_row, row_smem, a.stream>>>(spec, n, logn, tw, scale, (R*)s.du, a.g.plane);
-    *launches += 2;
+    *launches += 1;
     return cudaGetLastError();
 }
 
