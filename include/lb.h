@@ -388,12 +388,21 @@ LB_API lb_status lb_reduce_slab(lb_ctx* ctx, int64_t first, int64_t count, doubl
  * device (or managed) memory of the current device (checked with
  * cudaPointerGetAttributes; anything else is LB_ERR_ARG, before any launch). The first
  * call on a device looks up that array's device address (with that device current)
- * and keeps it for the life of the process; make that first call before any stream
- * capture, and do not call this entry point on a device after a cudaDeviceReset. All calls share the array: calls that
+ * and keeps it for the life of the process (do not call this entry point on a device after
+ * a cudaDeviceReset). The call synchronises its stream and copies the sums to the host, so it
+ * cannot be captured into a CUDA graph. All calls share the array: calls that
  * overlap on the GPU (other streams or threads on the same device) race, so order
  * them. Errors: LB_ERR_ARG (arguments, size), LB_ERR_CUDA. */
 LB_API lb_status lb_reduce_noalloc(lb_stencil stencil, const int64_t dims[3], const void* f, const void* F,
                                    lb_mem mem, double out[6], void* cuda_stream);
+
+/* Bandwidth reference for roofline fractions (the paper has no counterpart): copies `bytes`
+ * (a positive multiple of 16) from src to dst, both 16-byte aligned device (or managed)
+ * memory of the current device holding at least `bytes` (the caller's buffers, not checked
+ * beyond their start), as 16-byte vector loads and stores on cuda_stream (NULL = the legacy
+ * default stream). Asynchronous: returns after the launch. Errors: LB_ERR_ARG (pointers,
+ * alignment, size; before any launch), LB_ERR_CUDA. */
+LB_API lb_status lb_stream_copy(const void* src, void* dst, int64_t bytes, void* cuda_stream);
 
 /* ------------------------------------------------------------------ info ---- */
 LB_API int64_t lb_num_nodes(const lb_ctx* ctx);

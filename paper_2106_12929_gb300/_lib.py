@@ -86,6 +86,7 @@ _SIGNATURES = {
     "lb_spectrum": (_INT, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "lb_spectral_shift": (_INT, [_P, _P, _INT]),
     "lb_reduce_noalloc": (_INT, [_INT, ctypes.POINTER(_I64), _P, _P, _INT, ctypes.POINTER(_D), _P]),
+    "lb_stream_copy": (_INT, [_P, _P, _I64, _P]),
     "lb_halo_bytes": (_INT, [_P, ctypes.POINTER(_I64)]),
     "lb_halo_pack": (_INT, [_P, _INT, _P]),
     "lb_halo_unpack": (_INT, [_P, _INT, _P]),

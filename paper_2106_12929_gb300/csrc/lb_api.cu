@@ -1377,6 +1377,30 @@ lb_status lb_adam_update(float* theta, float* mm, float* v, const float* g, int6
     return LB_OK;
 }
 
+lb_status lb_stream_copy(const void* src, void* dst, int64_t bytes, void* stream)
+{
+    if (!src || !dst) return fail(LB_ERR_ARG, "lb_stream_copy: null pointer");
+    if (bytes <= 0 || bytes % 16 != 0) return fail(LB_ERR_ARG, "lb_stream_copy: bytes must be a positive multiple of 16");
+    if (((uintptr_t)src | (uintptr_t)dst) % 16 != 0)
+        return fail(LB_ERR_ARG, "lb_stream_copy: pointers must be 16-byte aligned");
+    int cur = -1, sms = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(LB_ERR_CUDA, "lb_stream_copy: no current device");
+    for (const void* p : {src, (const void*)dst}) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+            cudaGetLastError();  // clear the (non-sticky) error the failed query recorded
+            return fail(LB_ERR_ARG, "lb_stream_copy: not a CUDA pointer");
+        }
+        if (!((attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == cur))
+            return fail(LB_ERR_ARG, "lb_stream_copy: src and dst must be device (or managed) memory of the current device");
+    }
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur) != cudaSuccess)
+        return fail(LB_ERR_CUDA, "lb_stream_copy: device query failed");
+    const cudaError_t e = lb::stream_copy(src, dst, bytes, sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, "lb_stream_copy: %s", cudaGetErrorString(e));
+    return LB_OK;
+}
+
 int64_t lb_num_nodes(const lb_ctx* c) { return c ? c->N : -1; }
 int lb_q(const lb_ctx* c) { return c ? c->Q : -1; }
 int lb_d(const lb_ctx* c) { return c ? c->D : -1; }

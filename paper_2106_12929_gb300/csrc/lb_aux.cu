@@ -30,6 +30,33 @@ cudaError_t reduce_final(const double* partials, int64_t nblocks, int width, dou
     return cudaGetLastError();
 }
 
+// Bandwidth reference: dst <- src in 16-byte vectors, four loads in flight per thread before
+// their stores, over a grid-stride loop.
+__global__ void __launch_bounds__(256) k_stream_copy(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+cudaError_t stream_copy(const void* src, void* dst, int64_t bytes, int sms, cudaStream_t s)
+{
+    const int64_t n = bytes / 16;
+    int64_t blocks = (int64_t)(sms > 0 ? sms : 1) * 16;  // two rounds of resident blocks: measured best
+    const int64_t need = (n + 255) / 256;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) return cudaSuccess;
+    k_stream_copy<<<(unsigned)blocks, 256, 0, s>>>((const uint4*)src, (uint4*)dst, n);
+    return cudaGetLastError();
+}
+
 // dst[r * dst_stride + j] (+)= src[r * src_stride + j], j < n, r < rows, with
 // FP64/FP32 conversion on the way.
 __global__ void k_convert_copy(const void* src, int src_f64, void* dst, int dst_f64, int64_t n, int64_t ss,

@@ -102,6 +102,8 @@ void set_last_error(const char* msg);
 
 // stencil-independent helpers (lb_aux.cu)
 cudaError_t reduce_final(const double* partials, int64_t nblocks, int width, double* out, cudaStream_t s);
+// dst <- src, bytes a multiple of 16 with 16-byte aligned device pointers (bandwidth reference)
+cudaError_t stream_copy(const void* src, void* dst, int64_t bytes, int sms, cudaStream_t s);
 cudaError_t convert_copy(const void* src, int src_f64, void* dst, int dst_f64, int64_t n, int64_t src_stride,
                          int64_t dst_stride, int rows, int accumulate, cudaStream_t s);
 cudaError_t coarsen2(const double* rho_f, const double* u_f, int nxf, int nyf, int nzf, int d, double* rho_c,

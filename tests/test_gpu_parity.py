@@ -682,3 +682,21 @@ def test_launch_shapes_are_bit_identical(name, dims, storage, layout):
         tol = {"f64": 1e-14, "f32": 1e-6}.get(storage, 1e-4)
         for o in out[1:]:
             assert werr(o, out[0], w) <= tol, coll
+
+
+# ------------------------------------------------------------------ bandwidth reference
+def test_stream_copy_copies_bytes_and_rejects_host_memory():
+    """lb_stream_copy (the benchmark's bandwidth reference) moves every byte, including a tail
+    shorter than one four-vector round, and refuses host memory before any launch."""
+    from paper_2106_12929_gb300 import _lib
+    lib = _lib.load()
+    nbytes = 16 * (3 * 1024 * 1024 + 5)
+    src = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda")
+    dst = torch.zeros(nbytes + 16, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    assert lib.lb_stream_copy(src.data_ptr(), dst.data_ptr(), nbytes, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(dst[:nbytes], src)
+    assert int(dst[nbytes:].abs().sum()) == 0  # nothing past the end
+    host = np.zeros(1024, dtype=np.uint8)
+    assert lib.lb_stream_copy(host.ctypes.data, dst.data_ptr(), 1024, None) == 1

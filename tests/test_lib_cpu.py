@@ -140,3 +140,16 @@ def test_noalloc_sums_reject_bad_arguments_before_any_device_work(lib, stencil, 
     f = None if null_f else ctypes.cast(buf, ctypes.c_void_p)
     assert lib.lb_reduce_noalloc(stencil, d, f, None, mem, out, None) == 1
     assert lib.lb_last_error()
+
+
+def test_stream_copy_rejects_bad_arguments_before_any_device_work(lib):
+    """The bandwidth reference checks pointers, size and alignment before it touches a device."""
+    buf = (ctypes.c_uint8 * 64)()
+    base = ctypes.addressof(buf)
+    aligned = base + (-base) % 16
+    assert lib.lb_stream_copy(None, aligned, 16, None) == 1
+    assert lib.lb_stream_copy(aligned, None, 16, None) == 1
+    assert lib.lb_stream_copy(aligned, aligned + 16, 0, None) == 1
+    assert lib.lb_stream_copy(aligned, aligned + 16, 24, None) == 1        # not a multiple of 16
+    assert lib.lb_stream_copy(aligned + 4, aligned + 16, 16, None) == 1    # misaligned source
+    assert b"16" in lib.lb_last_error()
