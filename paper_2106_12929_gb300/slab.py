@@ -83,6 +83,13 @@ class DistTransport:
             req.wait()
 
     def allreduce_sum(self, t):
+        """Sum of t over the ranks. NCCL reduces device tensors only: a host tensor goes through
+        the rank's current CUDA device and comes back."""
+        if t.device.type == "cpu" and self.dist.get_backend(self.group) == "nccl":
+            d = t.to(torch.device("cuda", torch.cuda.current_device()))
+            self.dist.all_reduce(d, op=self.dist.ReduceOp.SUM, group=self.group)
+            t.copy_(d.cpu())
+            return t
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
         return t
 

@@ -87,3 +87,39 @@ def test_halo_calls_reject_what_they_do_not_support():
     assert lat._lib.lb_halo_pack(lat.handle, 1, buf.data_ptr()) == 6  # LB_ERR_UNSUPPORTED
     assert lat._lib.lb_halo_pack(lat.handle, 2, buf.data_ptr()) == 1
     lat.close()
+
+
+def test_one_rank_over_nccl():
+    """The torch.distributed transport on an NCCL group of one rank: the exchange (a local copy)
+    keeps the slab equal to the whole grid, and the all-reduce of host sums goes through the
+    device, as NCCL needs."""
+    import os
+    import socket
+
+    import torch.distributed as dist
+    from paper_2106_12929_gb300 import Lattice
+    from paper_2106_12929_gb300.slab import DistTransport, SlabLattice
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        t = DistTransport()
+        host = torch.tensor([1.0, 2.5, -3.0], dtype=torch.float64)
+        assert t.allreduce_sum(host).tolist() == [1.0, 2.5, -3.0]
+        dims = (24, 16, 20)
+        rho, u = lbinputs.random_moments(dims, seed=6, u_amp=0.05)
+        whole = Lattice("D3Q19", dims, 0.6, "bgk", storage="f32", nodes_per_thread=1, graphs=False)
+        whole.init_from_moments(rho, u)
+        slab = SlabLattice("D3Q19", dims, 0.6, "bgk", t, storage="f32", nodes_per_thread=1)
+        slab.init_from_moments(rho, u)
+        whole.step(5)
+        slab.step(5)
+        np.testing.assert_array_equal(slab.get_populations(torch.float64, "cpu").numpy(),
+                                      whole.get_populations(torch.float64, "cpu").numpy())
+        np.testing.assert_allclose(slab.reduce(), whole.reduce(), rtol=1e-12, atol=1e-13)
+        slab.close()
+        whole.close()
+    finally:
+        dist.destroy_process_group()
