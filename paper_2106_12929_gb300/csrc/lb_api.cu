@@ -97,7 +97,7 @@ struct lb_ctx {
     bool sc_on = false;
     int sc_logn = 0;
     double sc_cutoff = 2e-5, sc_kappa = 5e-5;
-    void* sc_spec = nullptr;     // [n][n] complex values of the arithmetic type, then the twiddles [n/2]
+    void* sc_spec = nullptr;     // [n][n] complex values of the arithmetic type, then the tables (spectral_layout)
     double* sc_small = nullptr;  // partials [n/2][<= n], sigma, grad, r2 [n/2 each], cost [1], sigma0, l0 [n/2 each]
     void* sc_du = nullptr;       // [2][plane] arithmetic type
 
@@ -181,7 +181,25 @@ lb::OpArgs base_args(lb_ctx* c, int op)
     return a;
 }
 
-// spectral-control scratch views of c->sc_small
+// Byte offsets in c->sc_spec of the spectral-control tables after the complex field [n][n]:
+// level twiddles, the shell of every mode [n][n] int16, the first |ky| of every shell per
+// column [n/2 + 1][n/2 + 1] int16 (each 256-byte aligned); *total = the allocation's size.
+struct SpectralLayout {
+    size_t tw, shell, first, total;
+};
+static SpectralLayout spectral_layout(int64_t n, int storage)
+{
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t cx = 2 * real_bytes(storage), K = (size_t)n / 2;
+    SpectralLayout l;
+    l.tw = up((size_t)n * n * cx);
+    l.shell = l.tw + up(lb::spectral_twiddle_count((int)n) * cx);
+    l.first = l.shell + up((size_t)n * n * 2);
+    l.total = l.first + up((K + 1) * (K + 1) * 2);
+    return l;
+}
+
+// spectral-control scratch views of c->sc_spec and c->sc_small
 lb::SpectralArgs spectral_args(lb_ctx* c, const lb::OpArgs& a)
 {
     lb::SpectralArgs s;
@@ -189,7 +207,12 @@ lb::SpectralArgs spectral_args(lb_ctx* c, const lb::OpArgs& a)
     s.n = (int)c->dims[0];
     s.logn = c->sc_logn;
     s.spec = c->sc_spec;
-    s.tw = c->sc_spec ? (const char*)c->sc_spec + (int64_t)s.n * s.n * 2 * real_bytes(c->opt.storage) : nullptr;
+    if (c->sc_spec) {
+        const SpectralLayout l = spectral_layout(s.n, c->opt.storage);
+        s.tw = (const char*)c->sc_spec + l.tw;
+        s.shell = (const char*)c->sc_spec + l.shell;
+        s.first = (const char*)c->sc_spec + l.first;
+    }
     const int64_t K = s.n / 2;
     s.partials = c->sc_small;
     s.sigma = s.partials + (int64_t)s.n * K;
@@ -677,12 +700,15 @@ static lb_status spectral_alloc(lb_ctx* c)
     const int64_t n = c->dims[0], K = n / 2;
     lb_status s;
     if (!c->sc_spec) {
-        // the complex field [n][n], then the twiddle table [n/2] (computed here, once)
-        if ((s = alloc(c, &c->sc_spec, (n * n + K) * 2 * real_bytes(c->opt.storage), "spectrum")) != LB_OK) return s;
-        LB_CUDA(c, lb::spectral_twiddles((char*)c->sc_spec + n * n * 2 * real_bytes(c->opt.storage), (int)n,
-                                         c->opt.storage, c->stream),
-                "twiddle table");
-        c->launches += 1;
+        // the complex field [n][n], then the tables of the line transforms (computed here, once)
+        const SpectralLayout l = spectral_layout(n, c->opt.storage);
+        if ((s = alloc(c, &c->sc_spec, l.total, "spectrum")) != LB_OK) return s;
+        char* base = (char*)c->sc_spec;
+        int nl = 0;
+        LB_CUDA(c, lb::spectral_tables(base + l.tw, base + l.shell, base + l.first, (int)n, c->opt.storage, c->stream,
+                                       &nl),
+                "spectral tables");
+        c->launches += nl;
     }
     if (!c->sc_small && (s = alloc(c, (void**)&c->sc_small, (n * K + 5 * K + 1) * 8, "spectral sums")) != LB_OK)
         return s;

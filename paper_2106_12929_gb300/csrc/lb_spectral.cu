@@ -15,142 +15,40 @@
 // G is real and even, so the inverse transform of G W has the real part grad_u_x R N^2 and
 // the imaginary part grad_u_y R N^2. One complex 2D FFT each way instead of two.
 //
-// A controlled step is five launches: rows (moments + forward DFT along x), columns (forward
-// DFT along y and the shell sums of |W|^2 over the block's columns), shells (sigma and
-// dR/dsigma, one warp per shell), columns (filter by G, inverse DFT along y; the cost R), rows
-// (inverse DFT along x: du, then the shifted BGK step of the row's nodes). lb_spectral_shift
-// writes du instead of stepping. Each DFT is an in-place radix-2 FFT of grid lines in shared
-// memory, in passes of three radix-2 stages held in registers (three twiddle-table entries per
-// set of eight, the rest fixed rotations; a padded layout keeps the passes free of bank
-// conflicts), with the twiddle table computed once per context. A row block takes one grid
-// line; a column block takes several adjacent columns, so that its loads and stores of a grid
-// row are contiguous runs of whole 32-byte sectors. Every sum runs in a fixed order
-// (deterministic).
-#include "lb_collide.cuh"
-#include "lb_spectral.cuh"
+// A controlled step is five launches: rows (moments + forward DFT along x, lb_spectral_fft.cuh),
+// columns (forward DFT along y and the shell sums of |W|^2 over the block's columns), shells
+// (sigma and dR/dsigma, one warp per shell), columns (filter by G, inverse DFT along y), rows
+// (inverse DFT along x: du, then the shifted BGK step of the row's nodes, and the cost R).
+// lb_spectral_shift writes du instead of stepping. The line transforms hold their values in
+// registers (lb_spectral_fft.cuh); the tables they use (twiddle factors per level, the shell of
+// every mode, the first |ky| of every shell per column) are computed once per context. A
+// column block takes several adjacent columns, so that its loads and stores of a grid row are
+// whole 32-byte sectors. Every sum runs in a fixed order (deterministic).
+#include "lb_spectral_fft.cuh"
 
 namespace lb {
+namespace sc {
 
-template <class R>
-struct Cx {
-    R re, im;
-};
-
-LB_DEV void sincos_pi(float x, float* s, float* c) { sincospif(x, s, c); }
 LB_DEV void sincos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
 
-LB_DEV int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
-
-// twiddle table tw[k] = exp(-i 2 pi k / n), k < n/2
+// Level twiddles exp(-2 pi i m r / (Ns R)) in the layout of Plan<L> (level 1: Ns = P, radix R1;
+// level 2: Ns = P R1, radix R2), computed in FP64 and rounded once
 template <class R>
-__global__ void k_sc_twiddles(Cx<R>* tw, int n)
+__global__ void k_sc_twiddles(Cx<R>* tw, int P, int R1, int R2, int nlev)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n / 2) return;
-    R s, c;
-    sincos_pi(R(-2 * k) / R(n), &s, &c);
-    tw[k] = {c, s};
-}
-
-// the table into shared memory (block-wide; the caller syncs)
-template <class R>
-LB_DEV void load_twiddles(Cx<R>* tws, const Cx<R>* tw, int n)
-{
-    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) tws[k] = tw[k];
-}
-
-// Shared-memory position of element i of a line: one spare slot after every eight elements, so
-// that the threads of a half-warp reading the sets of the first passes hit distinct banks.
-LB_HD int pz(int i) { return i + (i >> 3); }
-// (one more slot per line, so that the lines of a column block start on different banks)
-LB_HD int line_stride(int n) { return n + (n >> 3) + 1; }
-
-// One pass of the in-place decimation-in-time FFT over the stages s .. s + RB - 1 (RB <= 3) of
-// `lines` n-point lines z[l line_stride(n) ..) (bit-reversed input order): those stages only
-// combine elements within the sets {base + k h : k < 2^RB}, h = 2^s, so each thread loads whole
-// sets, runs the RB stages in registers and stores them back (one shared-memory round trip and
-// one barrier for RB stages). Element k of a set sits at position j + k h of its 2^RB h block
-// (j = its offset in the first h), so the stages' twiddles are
-//   stage s:     w1 = exp(-i pi j / h)                              for every pair,
-//   stage s + 1: w2 = exp(-i pi j / 2h), times -i for the pairs with odd k,
-//   stage s + 2: w4 = exp(-i pi j / 4h), times exp(-i pi (k mod 4) / 4),
-// three table entries per set and fixed rotations (the conjugates for INV); unnormalised.
-template <class R, bool INV>
-LB_DEV Cx<R> cmul(Cx<R> w, Cx<R> q)
-{
-    return {w.re * q.re - w.im * q.im, w.re * q.im + w.im * q.re};
-}
-// t times -i (forward) or +i (inverse)
-template <class R, bool INV>
-LB_DEV Cx<R> rot90(Cx<R> t)
-{
-    return INV ? Cx<R>{-t.im, t.re} : Cx<R>{t.im, -t.re};
-}
-template <class R>
-LB_DEV void bfly(Cx<R>& p, Cx<R>& q, Cx<R> t)  // p, q <- p + t, p - t
-{
-    const Cx<R> a = p;
-    p = {a.re + t.re, a.im + t.im};
-    q = {a.re - t.re, a.im - t.im};
-}
-
-template <class R, int RB, bool INV>
-LB_DEV void fft_pass(Cx<R>* z, const Cx<R>* tw, int n, int logn, int s, int lines)
-{
-    constexpr int RR = 1 << RB;
-    const int h = 1 << s, lsets = logn - RB, ls = line_stride(n);
-    for (int t = threadIdx.x; t < (lines << lsets); t += blockDim.x) {
-        const int l = t >> lsets, q = t & ((1 << lsets) - 1);
-        Cx<R>* line = z + l * ls;
-        const int j = q & (h - 1);
-        const int base = ((q - j) << RB) + j;
-        Cx<R> v[RR];
-#pragma unroll
-        for (int k = 0; k < RR; ++k) v[k] = line[pz(base + k * h)];
-        auto twid = [&](int sh) {
-            Cx<R> w = tw[j << sh];
-            if (INV) w.im = -w.im;
-            return w;
-        };
-        {
-            const Cx<R> w1 = twid(logn - 1 - s);
-#pragma unroll
-            for (int k = 0; k < RR; k += 2) bfly(v[k], v[k + 1], cmul<R, INV>(w1, v[k + 1]));
-        }
-        if constexpr (RB >= 2) {
-            const Cx<R> w2 = twid(logn - 2 - s);
-#pragma unroll
-            for (int k0 = 0; k0 < RR; k0 += 4) {
-                bfly(v[k0], v[k0 + 2], cmul<R, INV>(w2, v[k0 + 2]));
-                bfly(v[k0 + 1], v[k0 + 3], rot90<R, INV>(cmul<R, INV>(w2, v[k0 + 3])));
-            }
-        }
-        if constexpr (RB >= 3) {
-            const Cx<R> w4 = twid(logn - 3 - s);
-            // exp(-+ i pi / 4) = (1 -+ i) / sqrt 2
-            const R r = R(0.70710678118654752440);
-            const Cx<R> c8 = {r, INV ? r : -r};
-            const Cx<R> w4c = cmul<R, INV>(c8, w4);
-            bfly(v[0], v[4], cmul<R, INV>(w4, v[4]));
-            bfly(v[1], v[5], cmul<R, INV>(w4c, v[5]));
-            bfly(v[2], v[6], rot90<R, INV>(cmul<R, INV>(w4, v[6])));
-            bfly(v[3], v[7], rot90<R, INV>(cmul<R, INV>(w4c, v[7])));
-        }
-#pragma unroll
-        for (int k = 0; k < RR; ++k) line[pz(base + k * h)] = v[k];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tw2 = nlev >= 2 ? (R1 - 1) * P : 0;
+    const int twn = tw2 + (nlev == 3 ? (R2 - 1) * P * R1 : 0);
+    if (e >= twn) return;
+    int ns, rad, r, m;
+    if (e < tw2) {
+        ns = P, rad = R1, r = e / P + 1, m = e % P;
+    } else {
+        ns = P * R1, rad = R2, r = (e - tw2) / ns + 1, m = (e - tw2) % ns;
     }
-    __syncthreads();
-}
-
-// FFT of `lines` lines (bit-reversed input order, loaded and synchronised by the caller):
-// passes of three stages, the last one of one or two.
-template <class R, bool INV>
-LB_DEV void fft_lines(Cx<R>* z, const Cx<R>* tw, int n, int logn, int lines)
-{
-    int s = 0;
-    for (; s + 3 <= logn; s += 3) fft_pass<R, 3, INV>(z, tw, n, logn, s, lines);
-    if (logn - s == 2) fft_pass<R, 2, INV>(z, tw, n, logn, s, lines);
-    else if (logn - s == 1) fft_pass<R, 1, INV>(z, tw, n, logn, s, lines);
+    double s, c;
+    sincos_pi(-2.0 * (double)m * r / ((double)ns * rad), &s, &c);
+    tw[e] = {(R)c, (R)s};
 }
 
 // round(|k|) of the mode (kx, ky) (signed wavenumbers), in exact integer arithmetic: an FP32
@@ -167,76 +65,15 @@ LB_DEV int shell_of(int kx, int ky)
 
 LB_DEV int signed_k(int k, int n) { return k < n / 2 ? k : k - n; }
 
-// Population access of node x of row y with 32-bit element offsets (9 x plane < 2^31 for every
-// grid the spectral calls accept): the three columns x - 1, x, x + 1 and the three row offsets
-// (y - 1) n, y n, (y + 1) n, periodic; access modes as in lb_device.cuh.
-struct ScRows {
-    int r[3];
-};
-LB_DEV ScRows sc_rows(int y, int n)
+// round(|k|) of every mode, in the order the column transforms load them: entry
+// (kx M + t) P + r is the mode (kx, ky = t + r M) of thread t of column kx (P values per
+// thread, M threads per column), so that a thread reads its P entries in one or two vectors
+__global__ void k_sc_shell_table(short* shell, int n, int P)
 {
-    return {{(y == 0 ? n - 1 : y - 1) * n, y * n, (y == n - 1 ? 0 : y + 1) * n}};
-}
-template <class T, int MODE>
-LB_DEV void sc_load(const T* buf, int plane, const ScRows& rw, int x, int n, typename Store<T>::Real* f)
-{
-    const int col[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int slot = (MODE == AA_ODD) ? opp(i) : i;
-        const int sg = (MODE == AA_EVEN) ? 0 : -1;
-        f[i] = load_pop<D2Q9>(buf + (slot * plane + rw.r[1 + sg * c2(i, 1)] + col[1 + sg * c2(i, 0)]), slot);
-    }
-}
-template <class T, int MODE>
-LB_DEV void sc_store(T* buf, int plane, const ScRows& rw, int x, int n, const typename Store<T>::Real* f)
-{
-    const int col[3] = {x == 0 ? n - 1 : x - 1, x, x == n - 1 ? 0 : x + 1};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int slot = (MODE == AA_EVEN) ? opp(i) : i;
-        const int sg = (MODE == AA_ODD) ? 1 : 0;
-        store_pop<D2Q9>(buf + (slot * plane + rw.r[1 + sg * c2(i, 1)] + col[1 + sg * c2(i, 0)]), slot, f[i]);
-    }
-}
-
-constexpr int kRowBatch = 4;
-
-// rows, forward: moments of every node of row y, w = u_x + i u_y, DFT along x -> spec[y][kx]
-template <class T, int MODE>
-__global__ void __launch_bounds__(256) k_sc_rows_fwd(const T* buf, Geom g, int logn,
-                                                     const Cx<typename Store<T>::Real>* tw,
-                                                     Cx<typename Store<T>::Real>* spec)
-{
-    using R = typename Store<T>::Real;
-    extern __shared__ __align__(16) unsigned char sc_smem[];
-    const int n = g.nx, y = blockIdx.x, plane = (int)g.plane;
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tws = z + line_stride(n);
-    load_twiddles(tws, tw, n);
-    const ScRows rw = sc_rows(y, n);
-    // kRowBatch nodes per thread at a time: all their loads are issued before the first
-    // shared-memory store (which the compiler would not move loads across)
-    for (int x0 = threadIdx.x; x0 < n; x0 += kRowBatch * blockDim.x) {
-        R f[kRowBatch][9];
-#pragma unroll
-        for (int b = 0; b < kRowBatch; ++b) {
-            const int x = x0 + b * blockDim.x;
-            if (x < n) sc_load<T, MODE>(buf, plane, rw, x, n, f[b]);
-        }
-#pragma unroll
-        for (int b = 0; b < kRowBatch; ++b) {
-            const int x = x0 + b * blockDim.x;
-            if (x < n) {
-                const R Fz[3] = {R(0), R(0), R(0)};
-                const NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f[b], Fz);
-                z[pz(bitrev(x, logn))] = {m.ux, m.uy};
-            }
-        }
-    }
-    __syncthreads();
-    fft_lines<R, false>(z, tws, n, logn, 1);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) spec[(int64_t)y * n + k] = z[pz(k)];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * n) return;
+    const int kx = (int)(i / n), rem = (int)(i % n), t = rem / P, r = rem % P, M = n / P;
+    shell[i] = (short)shell_of(signed_k(kx, n), signed_k(t + r * M, n));
 }
 
 // first |ky| in [0, n/2 + 1] whose mode (kx, ky) lies in shell s or above (the shell grows
@@ -254,99 +91,171 @@ LB_DEV int first_m(int kxs, int s, int n)
     return ky < n / 2 + 1 ? ky : n / 2 + 1;
 }
 
-// load the C columns kx0 .. kx0 + C - 1 of spec into lines 0 .. C - 1 (bit-reversed order along
-// y), each value times G of its shell if grad is given: thread t takes row t / C, column t % C,
-// so the threads of a warp read runs of C adjacent values of a row
-template <class R, int C>
-LB_DEV void load_columns(Cx<R>* z, const Cx<R>* spec, int n, int logn, int kx0, const double* grad)
+// first[a][s] = first_m(a, s) for |kx| = a in [0, n/2] and s in [0, n/2]: in a column the modes
+// of shell s are the |ky| in [first[a][s], first[a][s + 1])
+__global__ void k_sc_first_table(short* first, int n)
 {
-    const int ls = line_stride(n), K = n / 2, total = n * C;
-    constexpr int U = 4;  // loads in flight per thread
-    for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
-        Cx<R> v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + u * blockDim.x;
-            if (t < total) {
-                const int y = t / C, c = t - y * C;
-                v[u] = spec[(int64_t)y * n + kx0 + c];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + u * blockDim.x;
-            if (t < total) {
-                const int y = t / C, c = t - y * C;
-                if (grad) {
-                    const int sh = shell_of(signed_k(kx0 + c, n), signed_k(y, n));
-                    const R G = sh < K ? (R)__ldg(grad + sh) : R(0);
-                    v[u].re *= G;
-                    v[u].im *= G;
-                }
-                z[c * ls + pz(bitrev(y, logn))] = v[u];
-            }
-        }
-    }
+    const int K = n / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)(K + 1) * (K + 1)) return;
+    const int a = (int)(i / (K + 1)), s = (int)(i % (K + 1));
+    first[i] = (short)first_m(a, s, n);
 }
 
-template <class R, int C>
-LB_DEV void store_columns(const Cx<R>* z, Cx<R>* spec, int n, int kx0)
+// columns per block: 32-byte runs of a grid row (four FP32 or two FP64 complex values), at most
+// 512 threads per block
+constexpr int col_c(int L, int rbytes)
 {
-    const int ls = line_stride(n);
-    for (int t = threadIdx.x; t < n * C; t += blockDim.x) {
-        const int y = t / C, c = t - y * C;
-        spec[(int64_t)y * n + kx0 + c] = z[c * ls + pz(y)];
-    }
+    const int c0 = rbytes == 4 ? 4 : 2, m = (1 << L) / Plan_P(L);
+    return c0 * m <= 512 ? c0 : 512 / m;
 }
+template <class R, int L>
+struct ColShape {
+    static constexpr int C = col_c(L, (int)sizeof(R));
+};
+template <class R, int L>
+constexpr int col_threads() { return ColShape<R, L>::C * Plan<L>::M; }
 
-// the shell sums of |W|^2 / (2 N^2) over the block's C transformed columns (natural order)
-// into partials[s][block]: per column the modes of shell s are one run of |ky|, summed in order
-// of |ky|, +ky before -ky; the runs' sums and the columns in the arithmetic type (a few to a
-// few hundred terms; FP64 is a slow pipe on this part), scaled into FP64 once per shell
-template <class R, int C>
-LB_DEV void column_shell_sums(const Cx<R>* z, int n, int kx0, int nblk, double* partials)
+// columns, forward: DFT along y of the block's C columns, then the shell sums of
+// |W|^2 / (2 N^2) over those columns into partials[s][block] (per column the modes of shell s
+// are one run of |ky|, summed in order of |ky|, +ky before -ky; the columns in order; the
+// sums in the arithmetic type, scaled into FP64 once per shell)
+template <class R, int L>
+__global__ void __launch_bounds__(col_threads<R, L>()) k_sc_cols_fwd(Cx<R>* spec, const Cx<R>* __restrict__ tw,
+                                                     const short* __restrict__ first, double* partials)
 {
-    const int ls = line_stride(n), K = n / 2;
+    using PL = Plan<L>;
+    constexpr int C = ColShape<R, L>::C, n = PL::N, K = n / 2;
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    Cx<R>* zs = reinterpret_cast<Cx<R>*>(sc_smem);
+    const int c = threadIdx.x % C, t = threadIdx.x / C, kx = blockIdx.x * C + c;
+    // after the lines: the twiddles, then the shell runs of the block's columns,
+    // first[|kx|][0 .. K] (read after the barriers below)
+    Cx<R>* tws = zs + C * PL::LS;
+    stage_twiddles<R, L>(tws, tw);
+    short* fs = reinterpret_cast<short*>(tws + PL::TWN);
+    for (int i = threadIdx.x; i < C * (K + 1); i += blockDim.x) {
+        const int cc = i / (K + 1), kxc = blockIdx.x * C + cc;
+        fs[i] = first[(kxc <= K ? kxc : n - kxc) * (K + 1) + i % (K + 1)];
+    }
+    Cx<R> a[PL::P];
+#pragma unroll
+    for (int r = 0; r < PL::P; ++r) a[r] = spec[(t + r * PL::M) * n + kx];
+    line_fft<R, L, false>(a, zs + c * PL::LS, tws, t);
+#pragma unroll
+    for (int s = 0; s < PL::SUBL; ++s)
+#pragma unroll
+        for (int k = 0; k < PL::RL; ++k) spec[PL::out_index(t, s, k) * n + kx] = a[s * PL::RL + k];
+    __syncthreads();  // the shared lines are free again
+    R* e = reinterpret_cast<R*>(zs + c * PL::LS);
+#pragma unroll
+    for (int s = 0; s < PL::SUBL; ++s)
+#pragma unroll
+        for (int k = 0; k < PL::RL; ++k) {
+            const Cx<R> v = a[s * PL::RL + k];
+            e[PL::out_index(t, s, k)] = v.re * v.re + v.im * v.im;
+        }
+    __syncthreads();
     const double scale = 0.5 / ((double)n * n * (double)n * n);
-    for (int s = threadIdx.x; s < K; s += blockDim.x) {
+    for (int sh = threadIdx.x; sh < K; sh += blockDim.x) {
         R acc = R(0);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const Cx<R>* line = z + c * ls;
-            const int kxs = signed_k(kx0 + c, n);
-            const int m0 = first_m(kxs, s, n), m1 = first_m(kxs, s + 1, n);
+        for (int cc = 0; cc < C; ++cc) {
+            const R* ec = reinterpret_cast<const R*>(zs + cc * PL::LS);
+            const short* fr = fs + cc * (K + 1);
+            const int m0 = fr[sh], m1 = fr[sh + 1];
             R run = R(0);
             for (int m = m0; m < m1; ++m) {
-                const Cx<R> a = line[pz(m)];
-                run += a.re * a.re + a.im * a.im;
-                if (m > 0 && m < n / 2) {
-                    const Cx<R> b = line[pz(n - m)];
-                    run += b.re * b.re + b.im * b.im;
-                }
+                run += ec[m];
+                if (m > 0 && m < K) run += ec[n - m];
             }
             acc += run;
         }
-        partials[(int64_t)s * nblk + blockIdx.x] = (double)acc * scale;
+        partials[(int64_t)sh * gridDim.x + blockIdx.x] = (double)acc * scale;
     }
 }
 
-// columns, forward: DFT along y of the block's C columns, then the shell sums of |W|^2 / (2 N^2)
-// over those columns into partials[s][block] (per column the modes of shell s are one run of
-// |ky|, summed in order of |ky|, +ky before -ky; the columns in order)
-template <class R, int C>
-__global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int logn, const Cx<R>* tw,
-                                                     double* partials)
+// columns, inverse: multiply by G(k) of the mode's shell, inverse DFT along y of the block's
+// C columns (the twiddles and G of every kept shell staged in shared memory after the lines)
+template <class R, int L>
+__global__ void __launch_bounds__(col_threads<R, L>()) k_sc_cols_inv(Cx<R>* spec, const Cx<R>* __restrict__ tw,
+                                                     const short* __restrict__ shell, const double* __restrict__ grad)
 {
+    using PL = Plan<L>;
+    constexpr int C = ColShape<R, L>::C, n = PL::N, K = n / 2;
     extern __shared__ __align__(16) unsigned char sc_smem[];
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n), kx0 = blockIdx.x * C, nblk = gridDim.x;
-    Cx<R>* tws = z + C * ls;
-    load_twiddles(tws, tw, n);
-    load_columns<R, C>(z, spec, n, logn, kx0, nullptr);
-    __syncthreads();
-    fft_lines<R, false>(z, tws, n, logn, C);
-    store_columns<R, C>(z, spec, n, kx0);
-    column_shell_sums<R, C>(z, n, kx0, nblk, partials);
+    Cx<R>* zs = reinterpret_cast<Cx<R>*>(sc_smem);
+    Cx<R>* tws = zs + C * PL::LS;
+    R* gs = reinterpret_cast<R*>(tws + PL::TWN);
+    stage_twiddles<R, L>(tws, tw);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) gs[i] = (R)grad[i];
+    const int c = threadIdx.x % C, t = threadIdx.x / C, kx = blockIdx.x * C + c;
+    // the thread's P shell indices are contiguous (k_sc_shell_table's order)
+    short shv[PL::P];
+    const short* sp = shell + (kx * PL::M + t) * PL::P;
+    if constexpr (PL::P % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < PL::P / 8; ++q) {
+            const uint4 v = reinterpret_cast<const uint4*>(sp)[q];
+            const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                shv[8 * q + 2 * e] = (short)(w[e] & 0xffffu);
+                shv[8 * q + 2 * e + 1] = (short)(w[e] >> 16);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < PL::P; ++r) shv[r] = sp[r];
+    }
+    Cx<R> a[PL::P];
+#pragma unroll
+    for (int r = 0; r < PL::P; ++r) a[r] = spec[(t + r * PL::M) * n + kx];
+    __syncthreads();  // G staged
+#pragma unroll
+    for (int r = 0; r < PL::P; ++r) {
+        const R G = shv[r] < K ? gs[shv[r]] : R(0);
+        a[r] = {G * a[r].re, G * a[r].im};
+    }
+    line_fft<R, L, true>(a, zs + c * PL::LS, tws, t);
+#pragma unroll
+    for (int s = 0; s < PL::SUBL; ++s)
+#pragma unroll
+        for (int k = 0; k < PL::RL; ++k) spec[PL::out_index(t, s, k) * n + kx] = a[s * PL::RL + k];
+}
+
+// rows, inverse: inverse DFT along x, du_x = scale Re(.), du_y = scale Im(.), scale = -kappa / N^2,
+// written by the transform's threads; the first warp of block 0 also totals the cost R
+template <class R, int L>
+__global__ void __launch_bounds__(RowShape<L>::THREADS) k_sc_rows_inv(const Cx<R>* __restrict__ spec,
+                                                                      const Cx<R>* __restrict__ tw, R scale, R* du,
+                                                                      int plane, const double* r2, double* cost)
+{
+    using PL = Plan<L>;
+    using RS = RowShape<L>;
+    constexpr int n = PL::N;
+    if (blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    Cx<R>* tws = reinterpret_cast<Cx<R>*>(sc_smem) + RS::LPB * PL::LS;
+    stage_twiddles<R, L>(tws, tw);
+    const int l = threadIdx.x / PL::M, t = threadIdx.x % PL::M, y = blockIdx.x * RS::LPB + l;
+    const bool act = threadIdx.x < RS::FFT_T && y < n;
+    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem) + (act ? l : 0) * PL::LS;
+    Cx<R> a[PL::P];
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < PL::P; ++r) a[r] = spec[y * n + t + r * PL::M];
+    }
+    line_fft<R, L, true>(a, z, tws, t, act);
+    if (!act) return;
+#pragma unroll
+    for (int s = 0; s < PL::SUBL; ++s)
+#pragma unroll
+        for (int k = 0; k < PL::RL; ++k) {
+            const int x = PL::out_index(t, s, k);
+            du[y * n + x] = scale * a[s * PL::RL + k].re;
+            du[plane + y * n + x] = scale * a[s * PL::RL + k].im;
+        }
 }
 
 // shells: sigma_s = sum over the column blocks (one warp per shell: lane l takes blocks l, l + 32,
@@ -355,9 +264,12 @@ __global__ void __launch_bounds__(512) k_sc_cols_fwd(Cx<R>* spec, int n, int log
 // the gradient run in the arithmetic type R (the FP64 pipe is slow on this part, and FP32
 // storage needs no more).
 template <class R>
-LB_DEV void shell_reduce(const double* partials, int nblk, int s, int lane, const double* l0, double c,
-                         double* sigma, double* grad, double* r2)
+__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
+                                                   double c, double* sigma, double* grad, double* r2)
 {
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n / 2) return;
+    const int lane = threadIdx.x & 31;
     const double* p = partials + (int64_t)s * nblk;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
@@ -380,209 +292,109 @@ LB_DEV void shell_reduce(const double* partials, int nblk, int s, int lane, cons
     }
 }
 
-template <class R>
-__global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
-                                                   double c, double* sigma, double* grad, double* r2)
-{
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= n / 2) return;
-    shell_reduce<R>(partials, nblk, s, threadIdx.x & 31, l0, c, sigma, grad, r2);
-}
-
-// R = sum_s r2[s] by one warp in a fixed order
-LB_DEV void sum_cost(const double* r2, int K, double* cost)
-{
-    double acc = 0.0;
-    for (int s = threadIdx.x; s < K; s += 32) acc += r2[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) cost[0] = acc;
-}
-
 // cost R = sum_s r2[s] (one warp, fixed order)
 __global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost) { sum_cost(r2, K, cost); }
 
-// columns, inverse: multiply by G(k), inverse DFT along y of the block's C columns; block 0's
-// first warp also totals the cost R (cost non-null)
-template <class R, int C>
-__global__ void __launch_bounds__(512) k_sc_cols_inv(Cx<R>* spec, int n, int logn, const Cx<R>* tw,
-                                                     const double* grad, const double* r2, double* cost)
+template <class R, int L>
+static size_t col_smem_bytes()  // the lines, the twiddles, then G (inverse) or the shell runs (forward)
 {
-    if (cost && blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
-    extern __shared__ __align__(16) unsigned char sc_smem[];
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int ls = line_stride(n), kx0 = blockIdx.x * C;
-    Cx<R>* tws = z + C * ls;
-    load_twiddles(tws, tw, n);
-    load_columns<R, C>(z, spec, n, logn, kx0, grad);
-    __syncthreads();
-    fft_lines<R, true>(z, tws, n, logn, C);
-    store_columns<R, C>(z, spec, n, kx0);
+    constexpr int C = ColShape<R, L>::C, K = Plan<L>::N / 2;
+    const size_t g = (size_t)K * sizeof(R), f = (size_t)C * (K + 1) * sizeof(short);
+    return ((size_t)C * Plan<L>::LS + Plan<L>::TWN) * sizeof(Cx<R>) + (g > f ? g : f);
 }
 
-// rows, inverse: inverse DFT along x, du_x = scale Re(.), du_y = scale Im(.), scale = -kappa / N^2
-template <class R>
-__global__ void __launch_bounds__(256) k_sc_rows_inv(const Cx<R>* spec, int n, int logn, const Cx<R>* tw, R scale,
-                                                     R* du, int64_t plane)
+// the column passes of grid edge 2^L: forward DFT and shell sums (inv = false), or the filter
+// by G and the inverse DFT
+template <class R, int L>
+static cudaError_t cols_sized(const SpectralArgs& s, bool inv)
 {
-    extern __shared__ __align__(16) unsigned char sc_smem[];
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    Cx<R>* tws = z + line_stride(n);
-    const int y = blockIdx.x;
-    load_twiddles(tws, tw, n);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) z[pz(bitrev(k, logn))] = spec[(int64_t)y * n + k];
-    __syncthreads();
-    fft_lines<R, true>(z, tws, n, logn, 1);
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        du[(int64_t)y * n + x] = scale * z[pz(x)].re;
-        du[plane + (int64_t)y * n + x] = scale * z[pz(x)].im;
-    }
-}
-
-// one BGK step of a node from its pre-collision deviations f (loaded by the caller) with the
-// equilibrium at u + du
-template <class T, int MODE>
-LB_DEV void shifted_bgk_node(typename Store<T>::Real* f, T* dst, int plane, const ScRows& rw, int n,
-                             typename Store<T>::Real omega, int x, typename Store<T>::Real dux,
-                             typename Store<T>::Real duy, unsigned* status)
-{
-    using R = typename Store<T>::Real;
-    R feq[9];
-    const R Fz[3] = {R(0), R(0), R(0)};
-    NodeMoments<D2Q9, R> m = node_moments<D2Q9, false>(f, Fz);
-    const R rho = m.rho;
-    m.ux += dux;
-    m.uy += duy;
-    equilibrium<D2Q9>(m, feq);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
-    sc_store<T, MODE>(dst, plane, rw, x, n, f);
-    if (!(rho > R(0) && rho < R(1e30))) atomicOr(status, 1u);
-}
-
-// rows, inverse, fused with the step: the inverse DFT of row y gives du of the row in shared
-// memory, and the block then steps the row's nodes (the step reads only the pre-step state,
-// which no kernel of this step writes; every node is stepped by exactly one thread, as in the
-// one-kernel AA update)
-template <class T, int MODE>
-__global__ void __launch_bounds__(256) k_sc_rows_inv_step(const Cx<typename Store<T>::Real>* spec, int logn,
-                                                          const Cx<typename Store<T>::Real>* tw,
-                                                          typename Store<T>::Real scale, const T* src, T* dst,
-                                                          Geom g, typename Store<T>::Real omega, unsigned* status)
-{
-    using R = typename Store<T>::Real;
-    extern __shared__ __align__(16) unsigned char sc_smem[];
-    Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem);
-    const int n = g.nx;
-    Cx<R>* tws = z + line_stride(n);
-    const int y = blockIdx.x;
-    load_twiddles(tws, tw, n);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) z[pz(bitrev(k, logn))] = spec[(int64_t)y * n + k];
-    __syncthreads();
-    fft_lines<R, true>(z, tws, n, logn, 1);
-    const ScRows rw = sc_rows(y, n);
-    const int plane = (int)g.plane;
-    // every node is read and written by its own thread only (AB: other buffer; AA: its own
-    // slots), so the loads of a batch may precede the stores of the nodes before it
-    for (int x0 = threadIdx.x; x0 < n; x0 += kRowBatch * blockDim.x) {
-        R f[kRowBatch][9];
-#pragma unroll
-        for (int b = 0; b < kRowBatch; ++b) {
-            const int x = x0 + b * blockDim.x;
-            if (x < n) sc_load<T, MODE>(src, plane, rw, x, n, f[b]);
-        }
-#pragma unroll
-        for (int b = 0; b < kRowBatch; ++b) {
-            const int x = x0 + b * blockDim.x;
-            if (x < n) {
-                const Cx<R> d = z[pz(x)];
-                shifted_bgk_node<T, MODE>(f[b], dst, plane, rw, n, omega, x, scale * d.re, scale * d.im, status);
-            }
-        }
-    }
-}
-
-// threads of a block that FFTs `lines` lines of n points (passes of three stages: n / 8 sets
-// per line, one per thread, 32 to `cap`)
-static int fft_threads(int n, int lines, int cap)
-{
-    const int t = lines * n / 8;
-    return t < 32 ? 32 : (t > cap ? cap : t);
-}
-
-// columns per column block: four (whole 32-byte sectors of FP32 values, two of FP64), fewer
-// where four lines would not fit in shared memory
-template <class R>
-static int column_block(int n)
-{
-    int C = 4;
-    while (C > 1 && (size_t)C * line_stride(n) * sizeof(Cx<R>) > 160 * 1024) C >>= 1;
-    return C < n ? C : n;
-}
-
-template <class K>
-static cudaError_t smem_attr(K kernel, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// the column passes with C columns per block: forward DFT and shell sums (inv = false), or
-// the filter by G and the inverse DFT
-template <class R, int C>
-static cudaError_t launch_columns(const SpectralArgs& s, bool inv)
-{
-    const int n = s.n, logn = s.logn, K = n / 2, nblk = n / C, th = fft_threads(n, C, 512);
-    const size_t smem = ((size_t)C * line_stride(n) + (size_t)K) * sizeof(Cx<R>);
+    const int nblk = Plan<L>::N / ColShape<R, L>::C, th = col_threads<R, L>();
+    const size_t smem = col_smem_bytes<R, L>();
     Cx<R>* spec = (Cx<R>*)s.spec;
     const Cx<R>* tw = (const Cx<R>*)s.tw;
     cudaError_t e;
     if (!inv) {
-        if ((e = smem_attr(k_sc_cols_fwd<R, C>, smem)) != cudaSuccess) return e;
-        k_sc_cols_fwd<R, C><<<nblk, th, smem, s.a.stream>>>(spec, n, logn, tw, s.partials);
+        if ((e = sc_smem_attr(k_sc_cols_fwd<R, L>, smem)) != cudaSuccess) return e;
+        k_sc_cols_fwd<R, L><<<nblk, th, smem, s.a.stream>>>(spec, tw, (const short*)s.first, s.partials);
     } else {
-        if ((e = smem_attr(k_sc_cols_inv<R, C>, smem)) != cudaSuccess) return e;
-        k_sc_cols_inv<R, C><<<nblk, th, smem, s.a.stream>>>(spec, n, logn, tw, s.grad, s.r2, s.cost);
+        if ((e = sc_smem_attr(k_sc_cols_inv<R, L>, smem)) != cudaSuccess) return e;
+        k_sc_cols_inv<R, L><<<nblk, th, smem, s.a.stream>>>(spec, tw, (const short*)s.shell, s.grad);
     }
     return cudaGetLastError();
 }
-template <class R>
-static cudaError_t columns(const SpectralArgs& s, bool inv)
+
+// inverse rows writing du (no step)
+template <class R, int L>
+static cudaError_t rows_inv_sized(const SpectralArgs& s)
 {
-    switch (column_block<R>(s.n)) {
-    case 4: return launch_columns<R, 4>(s, inv);
-    case 2: return launch_columns<R, 2>(s, inv);
-    default: return launch_columns<R, 1>(s, inv);
+    const int blocks = (Plan<L>::N + RowShape<L>::LPB - 1) / RowShape<L>::LPB;
+    const size_t smem = row_smem_bytes<R, L>();
+    const R scale = (R)(-s.kappa / ((double)s.n * s.n * (double)s.n * s.n));
+    cudaError_t e;
+    if ((e = sc_smem_attr(k_sc_rows_inv<R, L>, smem)) != cudaSuccess) return e;
+    k_sc_rows_inv<R, L><<<blocks, RowShape<L>::THREADS, smem, s.a.stream>>>(
+        (const Cx<R>*)s.spec, (const Cx<R>*)s.tw, scale, (R*)s.du, (int)s.a.g.plane, s.r2, s.cost);
+    return cudaGetLastError();
+}
+
+template <class R>
+static cudaError_t cols(const SpectralArgs& s, bool inv)
+{
+    switch (s.logn) {
+    case 2: return cols_sized<R, 2>(s, inv);
+    case 3: return cols_sized<R, 3>(s, inv);
+    case 4: return cols_sized<R, 4>(s, inv);
+    case 5: return cols_sized<R, 5>(s, inv);
+    case 6: return cols_sized<R, 6>(s, inv);
+    case 7: return cols_sized<R, 7>(s, inv);
+    case 8: return cols_sized<R, 8>(s, inv);
+    case 9: return cols_sized<R, 9>(s, inv);
+    case 10: return cols_sized<R, 10>(s, inv);
+    case 11: return cols_sized<R, 11>(s, inv);
+    case 12: return cols_sized<R, 12>(s, inv);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class R>
+static cudaError_t rows_inv(const SpectralArgs& s)
+{
+    switch (s.logn) {
+    case 2: return rows_inv_sized<R, 2>(s);
+    case 3: return rows_inv_sized<R, 3>(s);
+    case 4: return rows_inv_sized<R, 4>(s);
+    case 5: return rows_inv_sized<R, 5>(s);
+    case 6: return rows_inv_sized<R, 6>(s);
+    case 7: return rows_inv_sized<R, 7>(s);
+    case 8: return rows_inv_sized<R, 8>(s);
+    case 9: return rows_inv_sized<R, 9>(s);
+    case 10: return rows_inv_sized<R, 10>(s);
+    case 11: return rows_inv_sized<R, 11>(s);
+    case 12: return rows_inv_sized<R, 12>(s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t rows(const SpectralArgs& s, bool step)
+{
+    switch (s.a.storage) {
+    case S_F64: return spectral_rows_f64(s, step);
+    case S_F32: return spectral_rows_f32(s, step);
+    case S_F16: return spectral_rows_f16(s, step);
+    case S_BF16: return spectral_rows_bf16(s, step);
+    default: return cudaErrorInvalidValue;
     }
 }
 
 // step = true: the controlled step itself (a.dst, a.status, a.omega of s.a), du stays on chip
-template <class T>
+template <class R>
 static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
 {
-    using R = typename Store<T>::Real;
     const OpArgs& a = s.a;
-    const int n = s.n, logn = s.logn, K = n / 2;
-    const int nblk = n / column_block<R>(n);
-    // a row block: one thread per set of the FFT passes (n / 8, 32 to 256), each loading and
-    // stepping n / threads nodes of the row
-    const int th_row = fft_threads(n, 1, 256);
-    Cx<R>* spec = (Cx<R>*)s.spec;
-    const Cx<R>* tw = (const Cx<R>*)s.tw;
-    const size_t row_smem = ((size_t)line_stride(n) + (size_t)K) * sizeof(Cx<R>);  // one line + twiddles
+    const int n = s.n, K = n / 2, nblk = n / col_c(s.logn, (int)sizeof(R));
     cudaError_t e;
-    const T* buf = (const T*)a.src;
-    if (a.mode == AB) {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AB>, row_smem)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AB><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
-    } else if (a.mode == AA_EVEN) {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AA_EVEN>, row_smem)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AA_EVEN><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
-    } else {
-        if ((e = smem_attr(k_sc_rows_fwd<T, AA_ODD>, row_smem)) != cudaSuccess) return e;
-        k_sc_rows_fwd<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(buf, a.g, logn, tw, spec);
-    }
-    if ((e = columns<R>(s, false)) != cudaSuccess) return e;
+    if ((e = rows(s, false)) != cudaSuccess) return e;
+    if ((e = cols<R>(s, false)) != cudaSuccess) return e;
     k_sc_shells<R><<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, nblk, s.sigma0 ? s.l0 : nullptr, s.cutoff,
                                                       s.sigma, s.grad, s.r2);
     *launches += 3;
@@ -592,33 +404,10 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
         *launches += 1;
         return cudaGetLastError();
     }
-    if ((e = columns<R>(s, true)) != cudaSuccess) return e;
-    *launches += 1;
-    const R scale = (R)(-s.kappa / ((double)n * n * (double)n * n));
-    if (step) {  // inverse rows fused with the step
-        const T* src = (const T*)a.src;
-        T* dst = (T*)a.dst;
-        const R om = (R)a.omega;
-        if (a.mode == AB) {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AB>, row_smem)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AB><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g, om,
-                                                                         a.status);
-        } else if (a.mode == AA_EVEN) {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_EVEN>, row_smem)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AA_EVEN><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g,
-                                                                              om, a.status);
-        } else {
-            if ((e = smem_attr(k_sc_rows_inv_step<T, AA_ODD>, row_smem)) != cudaSuccess) return e;
-            k_sc_rows_inv_step<T, AA_ODD><<<n, th_row, row_smem, a.stream>>>(spec, logn, tw, scale, src, dst, a.g,
-                                                                             om, a.status);
-        }
-        *launches += 1;
-        return cudaGetLastError();
-    }
-    if ((e = smem_attr(k_sc_rows_inv<R>, row_smem)) != cudaSuccess) return e;
-    k_sc_rows_inv<R><<<n, th_row, row_smem, a.stream>>>(spec, n, logn, tw, scale, (R*)s.du, a.g.plane);
-    *launches += 1;
-    return cudaGetLastError();
+    if ((e = cols<R>(s, true)) != cudaSuccess) return e;
+    e = step ? rows(s, true) : rows_inv<R>(s);
+    *launches += 2;
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 static cudaError_t shift_or_step(const SpectralArgs& s, int* launches, bool step)
@@ -626,26 +415,71 @@ static cudaError_t shift_or_step(const SpectralArgs& s, int* launches, bool step
     if (s.a.g.nx != s.n || s.a.g.ny != s.n || s.a.g.nz != 1 || s.n < 4 || s.n > kSpecMaxN || (1 << s.logn) != s.n)
         return cudaErrorInvalidValue;
     if (step && !s.sigma0) return cudaErrorInvalidValue;
-    if (!s.tw) return cudaErrorInvalidValue;
-    switch (s.a.storage) {
-    case S_F64: return shift_typed<double>(s, launches, step);
-    case S_F32: return shift_typed<float>(s, launches, step);
-    case S_F16: return shift_typed<__half>(s, launches, step);
-    case S_BF16: return shift_typed<__nv_bfloat16>(s, launches, step);
-    default: return cudaErrorInvalidValue;
+    if (!s.tw || !s.shell || !s.first) return cudaErrorInvalidValue;
+    return s.a.storage == S_F64 ? shift_typed<double>(s, launches, step) : shift_typed<float>(s, launches, step);
+}
+
+template <int L>
+static void plan_of(int* P, int* R1, int* R2, int* nlev)
+{
+    *P = Plan<L>::P;
+    *R1 = Plan<L>::R1;
+    *R2 = Plan<L>::R2;
+    *nlev = Plan<L>::NLEV;
+}
+
+}  // namespace sc
+
+cudaError_t spectral_shift(const SpectralArgs& s, int* launches) { return sc::shift_or_step(s, launches, false); }
+
+cudaError_t spectral_step(const SpectralArgs& s, int* launches) { return sc::shift_or_step(s, launches, true); }
+
+size_t spectral_twiddle_count(int n)
+{
+    switch (n) {
+    case 4: return sc::Plan<2>::TWN;
+    case 8: return sc::Plan<3>::TWN;
+    case 16: return sc::Plan<4>::TWN;
+    case 32: return sc::Plan<5>::TWN;
+    case 64: return sc::Plan<6>::TWN;
+    case 128: return sc::Plan<7>::TWN;
+    case 256: return sc::Plan<8>::TWN;
+    case 512: return sc::Plan<9>::TWN;
+    case 1024: return sc::Plan<10>::TWN;
+    case 2048: return sc::Plan<11>::TWN;
+    case 4096: return sc::Plan<12>::TWN;
+    default: return 0;
     }
 }
 
-cudaError_t spectral_shift(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, false); }
-
-cudaError_t spectral_step(const SpectralArgs& s, int* launches) { return shift_or_step(s, launches, true); }
-
-cudaError_t spectral_twiddles(void* tw, int n, int storage, cudaStream_t st)
+cudaError_t spectral_tables(void* tw, void* shell, void* first, int n, int storage, cudaStream_t st, int* launches)
 {
-    if (n < 4 || n > kSpecMaxN) return cudaErrorInvalidValue;
-    const int blocks = (n / 2 + 127) / 128;
-    if (storage == S_F64) k_sc_twiddles<double><<<blocks, 128, 0, st>>>((Cx<double>*)tw, n);
-    else k_sc_twiddles<float><<<blocks, 128, 0, st>>>((Cx<float>*)tw, n);
+    if (n < 4 || n > kSpecMaxN || (n & (n - 1))) return cudaErrorInvalidValue;
+    int P = 0, R1 = 0, R2 = 0, nlev = 0;
+    switch (n) {
+    case 4: sc::plan_of<2>(&P, &R1, &R2, &nlev); break;
+    case 8: sc::plan_of<3>(&P, &R1, &R2, &nlev); break;
+    case 16: sc::plan_of<4>(&P, &R1, &R2, &nlev); break;
+    case 32: sc::plan_of<5>(&P, &R1, &R2, &nlev); break;
+    case 64: sc::plan_of<6>(&P, &R1, &R2, &nlev); break;
+    case 128: sc::plan_of<7>(&P, &R1, &R2, &nlev); break;
+    case 256: sc::plan_of<8>(&P, &R1, &R2, &nlev); break;
+    case 512: sc::plan_of<9>(&P, &R1, &R2, &nlev); break;
+    case 1024: sc::plan_of<10>(&P, &R1, &R2, &nlev); break;
+    case 2048: sc::plan_of<11>(&P, &R1, &R2, &nlev); break;
+    default: sc::plan_of<12>(&P, &R1, &R2, &nlev); break;
+    }
+    const int twn = (int)spectral_twiddle_count(n);
+    if (twn > 0) {
+        const int blocks = (twn + 127) / 128;
+        if (storage == S_F64) sc::k_sc_twiddles<double><<<blocks, 128, 0, st>>>((sc::Cx<double>*)tw, P, R1, R2, nlev);
+        else sc::k_sc_twiddles<float><<<blocks, 128, 0, st>>>((sc::Cx<float>*)tw, P, R1, R2, nlev);
+        *launches += 1;
+    }
+    const int64_t nn = (int64_t)n * n, K = n / 2, nf = (K + 1) * (K + 1);
+    sc::k_sc_shell_table<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>((short*)shell, n, P);
+    sc::k_sc_first_table<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>((short*)first, n);
+    *launches += 2;
     return cudaGetLastError();
 }
 

@@ -49,8 +49,10 @@ def flow(n, seed=2000, k0=None, u0=0.1 / math.sqrt(3.0), re=2000.0):
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-6)])
-@pytest.mark.parametrize("n", [4, 16, 128, 2048, 4096])
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
 def test_spectrum_and_cost_match_oracle(storage, tol, n):
+    """Every grid edge the calls accept: one-level line transforms (n <= 16), two levels
+    (32 ... 256) and three (512 ... 4096)."""
     dims, tau, rho, u = flow(n, k0=max(1.0, n / 16.0))
     f0 = oracle.init_eq(NAME, dims, rho, u)
     lat = L(NAME, dims, tau, "bgk", storage=storage)
@@ -68,8 +70,8 @@ def test_spectrum_and_cost_match_oracle(storage, tol, n):
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-4)])
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_velocity_shift_matches_oracle(storage, tol, layout):
-    n = 64
+@pytest.mark.parametrize("n", [16, 64, 512])
+def test_velocity_shift_matches_oracle(storage, tol, layout, n):
     dims, tau, rho, u = flow(n)
     f0 = oracle.init_eq(NAME, dims, rho, u)
     f1 = oracle.step(NAME, dims, tau, "bgk", f0, nsteps=3)  # away from equilibrium, and an odd AA step
@@ -87,8 +89,8 @@ def test_velocity_shift_matches_oracle(storage, tol, layout):
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
-def test_controlled_run_fp64_matches_oracle(layout):
-    n = 32
+@pytest.mark.parametrize("n", [32, 256, 1024])
+def test_controlled_run_fp64_matches_oracle(layout, n):
     dims, tau, rho, u = flow(n, seed=7)
     f0 = oracle.init_eq(NAME, dims, rho, u)
     s0 = spectral.spectrum(u, n) * 1.5  # a target above the current spectrum: the control pumps
