@@ -106,7 +106,12 @@ typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16_SHIFTED = 2, LB_BF16_SHIFTED = 3 }
  *               (half the memory of AB, the same bytes moved per step). */
 typedef enum { LB_LAYOUT_AB = 0, LB_LAYOUT_AA = 1 } lb_layout;
 
-/* Element type and location of an array argument. */
+/* Element type and location of an array argument. A host array in page-locked memory (pinned
+ * or registered with CUDA) is read, or written, in place by the call's kernels through its
+ * device address (over NVLink-C2C on Grace-Blackwell); a pageable host array, and an output
+ * that a call accumulates into (grad_F, grad_theta), go through a stream-ordered temporary
+ * device buffer and a copy. Either way a call returns its host outputs complete; host inputs
+ * must stay unchanged until the stream has run the call's work. */
 typedef enum { LB_HOST_F64 = 0, LB_DEVICE_F64 = 1, LB_HOST_F32 = 2, LB_DEVICE_F32 = 3 } lb_mem;
 
 typedef enum {

@@ -255,6 +255,7 @@ struct Staged {
     lb_ctx* c = nullptr;
     void* dev = nullptr;
     void* tmp = nullptr;
+    bool direct = false;  // a page-locked host array the kernels use in place
     int64_t bytes = 0;
     ~Staged()
     {
@@ -262,12 +263,30 @@ struct Staged {
     }
 };
 
+// The device address of a page-locked (pinned or registered) host array, or null for pageable
+// memory. Kernels read and write such arrays in place (over the host link: NVLink-C2C on
+// Grace-Blackwell), which saves the staging buffer and its copy; pageable arrays are staged.
+static void* host_direct(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 lb_status stage_in(lb_ctx* c, Staged& s, const void* p, int64_t count, lb_mem m, const char* what)
 {
     s.c = c;
     s.bytes = count * (mem_f64(m) ? 8 : 4);
     if (!mem_host(m)) {
         s.dev = const_cast<void*>(p);
+        return LB_OK;
+    }
+    if (void* d = host_direct(p)) {  // read once by the call's kernels
+        s.dev = d;
+        s.direct = true;
         return LB_OK;
     }
     cudaError_t e = cudaMallocAsync(&s.tmp, (size_t)s.bytes, c->stream);
@@ -289,6 +308,13 @@ lb_status stage_out_alloc(lb_ctx* c, Staged& s, void* p, int64_t count, lb_mem m
         s.dev = p;
         return LB_OK;
     }
+    // a pure output (written once per element) goes straight to page-locked host memory; an
+    // accumulator (copy_in) is staged, since its kernels add to it on every step
+    if (void* d = copy_in ? nullptr : host_direct(p)) {
+        s.dev = d;
+        s.direct = true;
+        return LB_OK;
+    }
     cudaError_t e = cudaMallocAsync(&s.tmp, (size_t)s.bytes, c->stream);
     if (e != cudaSuccess) {
         s.tmp = nullptr;
@@ -302,6 +328,10 @@ lb_status stage_out_alloc(lb_ctx* c, Staged& s, void* p, int64_t count, lb_mem m
 
 lb_status stage_out_finish(lb_ctx* c, Staged& s, void* p, const char* what)
 {
+    if (s.direct) {  // written in place: ready once the stream has run
+        LB_CUDA(c, cudaStreamSynchronize(c->stream), what);
+        return LB_OK;
+    }
     if (!s.tmp) return LB_OK;
     LB_CUDA(c, cudaMemcpyAsync(p, s.tmp, (size_t)s.bytes, cudaMemcpyDeviceToHost, c->stream), what);
     LB_CUDA(c, cudaStreamSynchronize(c->stream), what);

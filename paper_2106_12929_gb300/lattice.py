@@ -208,9 +208,17 @@ class Lattice:
         _lib.check(self._lib.lb_get_populations(self._h, out.data_ptr(), _mem_code(out)), "lb_get_populations")
         return out
 
-    def moments(self, dtype=torch.float64, device=None):
-        rho = self._out((self.N,), dtype, device)
-        u = self._out((self.D, self.N), dtype, device)
+    def moments(self, dtype=torch.float64, device=None, out=None):
+        """(rho[N], u[D][N]) of the pre-collision state; out = (rho, u): contiguous tensors of one
+        dtype to fill instead (e.g. page-locked host buffers kept across calls)."""
+        if out is None:
+            rho = self._out((self.N,), dtype, device)
+            u = self._out((self.D, self.N), dtype, device)
+        else:
+            rho, u = out
+            if (rho.numel() != self.N or u.numel() != self.D * self.N or rho.dtype != u.dtype
+                    or rho.device != u.device or not (rho.is_contiguous() and u.is_contiguous())):
+                raise ValueError("out must be contiguous (rho[N], u[D][N]) of one dtype and device")
         _lib.check(self._lib.lb_moments(self._h, rho.data_ptr(), u.data_ptr(), _mem_code(rho)), "lb_moments")
         return rho, u
 
