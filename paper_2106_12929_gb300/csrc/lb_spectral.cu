@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(col_threads<R, L>()) k_sc_cols_fwd(Cx<R>* spec
         const int cc = i / (K + 1), kxc = blockIdx.x * C + cc;
         fs[i] = first[(kxc <= K ? kxc : n - kxc) * (K + 1) + i % (K + 1)];
     }
+    pdl_wait();  // the row transforms of the previous launch
+    pdl_trigger();
     Cx<R> a[PL::P];
 #pragma unroll
     for (int r = 0; r < PL::P; ++r) a[r] = spec[(t + r * PL::M) * n + kx];
@@ -188,7 +190,6 @@ __global__ void __launch_bounds__(col_threads<R, L>()) k_sc_cols_inv(Cx<R>* spec
     Cx<R>* tws = zs + C * PL::LS;
     R* gs = reinterpret_cast<R*>(tws + PL::TWN);
     stage_twiddles<R, L>(tws, tw);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) gs[i] = (R)grad[i];
     const int c = threadIdx.x % C, t = threadIdx.x / C, kx = blockIdx.x * C + c;
     // the thread's P shell indices are contiguous (k_sc_shell_table's order)
     short shv[PL::P];
@@ -208,6 +209,9 @@ __global__ void __launch_bounds__(col_threads<R, L>()) k_sc_cols_inv(Cx<R>* spec
 #pragma unroll
         for (int r = 0; r < PL::P; ++r) shv[r] = sp[r];
     }
+    pdl_wait();  // dR/dsigma of the previous launch (and the columns of the one before)
+    pdl_trigger();
+    for (int i = threadIdx.x; i < K; i += blockDim.x) gs[i] = (R)grad[i];
     Cx<R> a[PL::P];
 #pragma unroll
     for (int r = 0; r < PL::P; ++r) a[r] = spec[(t + r * PL::M) * n + kx];
@@ -234,10 +238,12 @@ __global__ void __launch_bounds__(RowShape<L>::THREADS) k_sc_rows_inv(const Cx<R
     using PL = Plan<L>;
     using RS = RowShape<L>;
     constexpr int n = PL::N;
-    if (blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
     extern __shared__ __align__(16) unsigned char sc_smem[];
     Cx<R>* tws = reinterpret_cast<Cx<R>*>(sc_smem) + RS::LPB * PL::LS;
     stage_twiddles<R, L>(tws, tw);
+    pdl_wait();
+    pdl_trigger();
+    if (blockIdx.x == 0 && threadIdx.x < 32) sum_cost(r2, n / 2, cost);
     const int l = threadIdx.x / PL::M, t = threadIdx.x % PL::M, y = blockIdx.x * RS::LPB + l;
     const bool act = threadIdx.x < RS::FFT_T && y < n;
     Cx<R>* z = reinterpret_cast<Cx<R>*>(sc_smem) + (act ? l : 0) * PL::LS;
@@ -267,6 +273,8 @@ template <class R>
 __global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n, int nblk, const double* l0,
                                                    double c, double* sigma, double* grad, double* r2)
 {
+    pdl_wait();  // the column blocks' partial sums
+    pdl_trigger();
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= n / 2) return;
     const int lane = threadIdx.x & 31;
@@ -293,7 +301,12 @@ __global__ void __launch_bounds__(256) k_sc_shells(const double* partials, int n
 }
 
 // cost R = sum_s r2[s] (one warp, fixed order)
-__global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost) { sum_cost(r2, K, cost); }
+__global__ void __launch_bounds__(32) k_sc_cost(const double* r2, int K, double* cost)
+{
+    pdl_wait();
+    pdl_trigger();
+    sum_cost(r2, K, cost);
+}
 
 template <class R, int L>
 static size_t col_smem_bytes()  // the lines, the twiddles, then G (inverse) or the shell runs (forward)
@@ -315,12 +328,12 @@ static cudaError_t cols_sized(const SpectralArgs& s, bool inv)
     cudaError_t e;
     if (!inv) {
         if ((e = sc_smem_attr(k_sc_cols_fwd<R, L>, smem)) != cudaSuccess) return e;
-        k_sc_cols_fwd<R, L><<<nblk, th, smem, s.a.stream>>>(spec, tw, (const short*)s.first, s.partials);
+        return launch_pdl(s.n <= kPdlMaxN, k_sc_cols_fwd<R, L>, nblk, th, smem, s.a.stream, spec, tw, (const short*)s.first, s.partials);
     } else {
         if ((e = sc_smem_attr(k_sc_cols_inv<R, L>, smem)) != cudaSuccess) return e;
-        k_sc_cols_inv<R, L><<<nblk, th, smem, s.a.stream>>>(spec, tw, (const short*)s.shell, s.grad);
+        return launch_pdl(s.n <= kPdlMaxN, k_sc_cols_inv<R, L>, nblk, th, smem, s.a.stream, spec, tw, (const short*)s.shell,
+                          (const double*)s.grad);
     }
-    return cudaGetLastError();
 }
 
 // inverse rows writing du (no step)
@@ -332,9 +345,8 @@ static cudaError_t rows_inv_sized(const SpectralArgs& s)
     const R scale = (R)(-s.kappa / ((double)s.n * s.n * (double)s.n * s.n));
     cudaError_t e;
     if ((e = sc_smem_attr(k_sc_rows_inv<R, L>, smem)) != cudaSuccess) return e;
-    k_sc_rows_inv<R, L><<<blocks, RowShape<L>::THREADS, smem, s.a.stream>>>(
-        (const Cx<R>*)s.spec, (const Cx<R>*)s.tw, scale, (R*)s.du, (int)s.a.g.plane, s.r2, s.cost);
-    return cudaGetLastError();
+    return launch_pdl(s.n <= kPdlMaxN, k_sc_rows_inv<R, L>, blocks, RowShape<L>::THREADS, smem, s.a.stream, (const Cx<R>*)s.spec,
+                      (const Cx<R>*)s.tw, scale, (R*)s.du, (int)s.a.g.plane, (const double*)s.r2, s.cost);
 }
 
 template <class R>
@@ -395,12 +407,13 @@ static cudaError_t shift_typed(const SpectralArgs& s, int* launches, bool step)
     cudaError_t e;
     if ((e = rows(s, false)) != cudaSuccess) return e;
     if ((e = cols<R>(s, false)) != cudaSuccess) return e;
-    k_sc_shells<R><<<(K + 7) / 8, 256, 0, a.stream>>>(s.partials, n, nblk, s.sigma0 ? s.l0 : nullptr, s.cutoff,
-                                                      s.sigma, s.grad, s.r2);
+    if ((e = launch_pdl(n <= kPdlMaxN, k_sc_shells<R>, (K + 7) / 8, 256, 0, a.stream, (const double*)s.partials, n, nblk,
+                        s.sigma0 ? s.l0 : nullptr, s.cutoff, s.sigma, s.grad, s.r2)) != cudaSuccess)
+        return e;
     *launches += 3;
     if (!s.sigma0) return cudaGetLastError();
     if (!s.du && !step) {
-        k_sc_cost<<<1, 32, 0, a.stream>>>(s.r2, K, s.cost);
+        if ((e = launch_pdl(n <= kPdlMaxN, k_sc_cost, 1, 32, 0, a.stream, (const double*)s.r2, K, s.cost)) != cudaSuccess) return e;
         *launches += 1;
         return cudaGetLastError();
     }
