@@ -1,8 +1,7 @@
 """Parity of the training helpers of Sec. 3.1, each on its own: the 2 x 2 coarse-graining of a
 fine state (lb_coarsen_into), the Eq. 6 vorticity (lb_vorticity), the network's six inputs
 (lb_learned_inputs) against the oracle, and one Adam update (lb_adam_update) against its
-definition. The training driver runs all four; its tests check the resulting gain. This file is
-collected after every other GPU test."""
+definition. The training driver runs all four; its tests check the resulting gain."""
 import numpy as np
 import pytest
 import torch
