@@ -64,33 +64,6 @@ LB_DEV NodeMoments<St, R> node_moments(const R* d, const R* F)
     return {rho, jx * inv, jy * inv, jz * inv, rho1};
 }
 
-// The same moments from the opposite pairs (i, i + 1 = opp(i), i odd): ps = f_i + f_opp(i) and
-// pd = f_i - f_opp(i) (deviations), which the regularized collision reuses for its second
-// moments; rho - 1 = delta_0 + sum ps, j = sum over the pairs of c_i pd
-template <class St, bool FORCE, class R>
-LB_DEV NodeMoments<St, R> pair_moments(const R* d, const R* F, R* ps, R* pd)
-{
-    R rho1 = d[0], jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-    for (int p = 0; p < St::Q / 2; ++p) {
-        const int i = 2 * p + 1;
-        ps[p] = d[i] + d[i + 1];
-        pd[p] = d[i] - d[i + 1];
-        rho1 += ps[p];
-        if (St::c(i, 0)) jx += St::c(i, 0) > 0 ? pd[p] : -pd[p];
-        if (St::c(i, 1)) jy += St::c(i, 1) > 0 ? pd[p] : -pd[p];
-        if (St::D == 3 && St::c(i, 2)) jz += St::c(i, 2) > 0 ? pd[p] : -pd[p];
-    }
-    if constexpr (FORCE) {
-        jx += R(0.5) * F[0];
-        jy += R(0.5) * F[1];
-        if (St::D == 3) jz += R(0.5) * F[2];
-    }
-    const R rho = R(1) + rho1;
-    const R inv = recip(rho);
-    return {rho, jx * inv, jy * inv, jz * inv, rho1};
-}
-
 template <class St, class R>
 LB_DEV R cdotu(int i, R ux, R uy, R uz)
 {
@@ -135,10 +108,7 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
         return true;
     } else {
         const R omega = rx.omega;
-        R ps[St::Q / 2], pd[St::Q / 2];  // opposite-pair sums and differences (regularized only)
-        NodeMoments<St, R> m;
-        if constexpr (COLL == REG) m = pair_moments<St, FORCE>(f, F, ps, pd);
-        else m = node_moments<St, FORCE>(f, F);
+        NodeMoments<St, R> m = node_moments<St, FORCE>(f, F);
         R feq[St::Q];
         const R pre = R(1) - R(0.5) * omega;
         if constexpr (COLL == TRT) {
@@ -296,8 +266,7 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
             // REG: keep only the Hermite order <= 2 projection of f - f^eq. Opposite velocities
             // i, i + 1 share the even parts, which halves the work per pair: f^eq = w (a +- b)
             // with a = (rho - 1) + rho (4.5 (c.u)^2 - 1.5 u.u) and b = 3 rho c.u; the second
-            // moments of f - f^eq take the pair sums (f_i + f_opp) - 2 w a, the force term the
-            // pair differences (f_i - f_opp) - 2 w b; the correction (c c - I/3):Pi is even in c.
+            // moments of f - f^eq take the pair sums; the correction (c c - I/3):Pi is even in c.
             const R uu15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
             const R a0 = m.rho1 - m.rho * uu15, rho45 = R(4.5) * m.rho, rho3 = R(3) * m.rho;
             feq[0] = R(St::w(0)) * a0;
@@ -309,7 +278,8 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
                 const R a = a0 + rho45 * cu * cu, b = rho3 * cu;
                 feq[i] = R(St::w(i)) * (a + b);
                 feq[i + 1] = R(St::w(i)) * (a - b);
-                const R sp = ps[i / 2] - R(2 * St::w(i)) * a;
+                const R di = f[i] - feq[i], dj = f[i + 1] - feq[i + 1];
+                const R sp = di + dj;
                 const int cx = St::c(i, 0), cy = St::c(i, 1), cz = St::c(i, 2);
                 if (cx) pxx += sp;
                 if (cy) pyy += sp;
@@ -318,7 +288,7 @@ LB_DEV bool collide(R* f, const R* F, const Relax<R>& rx)
                 if (St::D == 3 && cx && cz) pxz += (cx == cz) ? sp : -sp;
                 if (St::D == 3 && cy && cz) pyz += (cy == cz) ? sp : -sp;
                 if constexpr (FORCE) {
-                    const R sm = pd[i / 2] - R(2 * St::w(i)) * b;
+                    const R sm = di - dj;
                     if (cx) ax += cx > 0 ? sm : -sm;
                     if (cy) ay += cy > 0 ? sm : -sm;
                     if (St::D == 3 && cz) az += cz > 0 ? sm : -sm;
