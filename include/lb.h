@@ -263,7 +263,11 @@ LB_API int64_t lb_steps_taken(const lb_ctx* ctx);
  * shells; this is its reading). The paper's constants are c = 2e-5 and kappa = 5e-5.
  * grad_u R is the exact gradient of R (a spectral filter of u), computed each step on the
  * GPU by FFTs of the grid lines. D2Q9 only, on a square grid of n = 2^k nodes per side,
- * 4 <= n <= 4096, any storage and layout. */
+ * 4 <= n <= 4096, any storage and layout. The first spectral call on a context allocates its
+ * scratch, kept until lb_destroy: the complex field (n^2 values of the arithmetic type), the
+ * line transforms' tables (the twiddles, the shell of every mode as int16, the first |ky| of
+ * every shell per column as int16: about 2.5 n^2 bytes), the shell sums and, with the control
+ * on, du[2][N]. */
 
 /* Turn the control on (sigma0[K] in host memory, K = n/2 shells, copied; cutoff c > 0,
  * kappa >= 0) or off (sigma0 NULL). From the next lb_step every step computes du from the
