@@ -687,7 +687,8 @@ REFERENCE_LU_BUDGET = 6e9  # lattice updates the reference arm may spend (~200 s
 
 def reference_grid(steps: int, warmup: int) -> int:
     """Edge of the grid the reference arm times: the 256^3 workload itself when its K + W
-    steps fit the budget (the driver's short runs), else the largest of 128^3, 64^3 that does."""
+    steps fit the budget (short runs such as 20 timed after 5 warm-up steps), else the largest of
+    128^3, 64^3 that does."""
     for n in (N_GRID, 128, 64):
         if (steps + warmup) * n ** 3 <= REFERENCE_LU_BUDGET:
             return n
