@@ -190,7 +190,7 @@ def test_timed_region_repeats_and_is_taken_once_more_after_a_rejected_clock_reco
 def test_reference_arm_grid_fits_its_budget():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.reference_grid(20, 5) == bench.N_GRID  # the driver's short run times the 256^3 grid itself
+    assert bench.reference_grid(20, 5) == bench.N_GRID  # a 20 + 5 step run times the 256^3 grid itself
     assert bench.reference_grid(2000, 10) == 128
     assert bench.reference_grid(20000, 10) == 64
     for k in (1, 20, 200, 2000, 20000):
